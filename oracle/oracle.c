@@ -12,7 +12,7 @@
  *   - symbolic structure: row-by-row closure of the up-looking
  *     elimination, fixed before any numeric work                       (Sec. 2.1, 2.2)
  *   - supernodes: runs of consecutive rows with identical U structure (Sec. 2.2)
- *   - padded storage pattern (dense supernode blocks, full-width
+ *   - padded storage pattern (dense supernode diagonal blocks, full-width
  *     supernode segments in L) -- a reading, the paper gives no detail (Sec. 2.2)
  *   - symbolic flop count                                              (Sec. 2.1)
  *   - up-looking (transposed left-looking) numeric LU, row by row,
@@ -229,10 +229,10 @@ int or_supernodes(or_ctx *c, int sn_max) {
  * the hybrid numerical kernels in a common way"):
  *   (i)   a supernode's diagonal block is stored dense;
  *   (ii)  a row that holds any L entry in a column of supernode S holds all
- *         columns of S;
- *   (iii) all rows of one supernode hold the same L columns (their union).
- * U structure is left as it is.  Also computes both flop counts (Sec. 2.1):
- * every L(i,k) costs one division and two flops per off-diagonal U(k,:) entry. */
+ *         columns of S.
+ * Each row keeps its own L columns; U structure is left as it is.  Also
+ * computes both flop counts (Sec. 2.1): every L(i,k) costs one division and
+ * two flops per off-diagonal U(k,:) entry. */
 int or_pad(or_ctx *c) {
     int n = c->n;
     char *in = (char *)calloc((size_t)n, 1);
@@ -248,28 +248,25 @@ int or_pad(or_ctx *c) {
     }
     for (int s = 0; s < c->nsn; ++s) {
         int r = c->sn_start[s], e = c->sn_start[s + 1] - 1;
-        int64_t nl = 0;
         for (int i = r; i <= e; ++i) {
+            int64_t nl = 0;
             for (int64_t q = c->f_rp[i]; q < c->f_rp[i + 1]; ++q) {
                 int k = c->f_ci[q];
                 if (k >= r) break;                          /* only columns before the block */
                 int S = c->sn_of[k];
                 for (int t = c->sn_start[S]; t < c->sn_start[S + 1]; ++t)   /* rule (ii) */
-                    if (!in[t]) { in[t] = 1; lst[nl++] = t; }               /* rule (iii): union */
+                    if (!in[t]) { in[t] = 1; lst[nl++] = t; }
             }
-        }
-        qsort(lst, (size_t)nl, sizeof(int32_t), cmp_i32);
-        for (int i = r; i <= e; ++i) {
+            qsort(lst, (size_t)nl, sizeof(int32_t), cmp_i32);
             int64_t d = diag_index(c->f_rp, c->f_ci, i);
             int64_t need = nl + (e - r + 1) + (c->f_rp[i + 1] - d);
             if (nnz + need > cap) { while (nnz + need > cap) cap *= 2; c->p_ci = (int32_t *)realloc(c->p_ci, sizeof(int32_t) * cap); }
-            for (int64_t t = 0; t < nl; ++t) c->p_ci[nnz++] = lst[t];
+            for (int64_t t = 0; t < nl; ++t) { c->p_ci[nnz++] = lst[t]; in[lst[t]] = 0; }
             for (int t = r; t <= e; ++t) c->p_ci[nnz++] = t;               /* rule (i) */
             for (int64_t q = d; q < c->f_rp[i + 1]; ++q)
                 if (c->f_ci[q] > e) c->p_ci[nnz++] = c->f_ci[q];          /* tail of U */
             c->p_rp[i + 1] = nnz;
         }
-        for (int64_t t = 0; t < nl; ++t) in[lst[t]] = 0;
     }
     /* flop counts */
     double fu = 0.0, fp = 0.0;
