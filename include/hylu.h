@@ -1,0 +1,167 @@
+/*
+ * hylu.h -- C ABI of a GB300 (sm_103a) implementation of the numeric phase of
+ * HYLU, a hybrid up-looking sparse LU solver (X. Chen, "HYLU: Hybrid Parallel
+ * Sparse LU Factorization", Sec. 2).
+ *
+ * Plain C types only: sizes are int32/int64, matrices are CSR arrays, device
+ * buffers are raw pointers into the memory of the current CUDA device and
+ * streams are passed as `void*` holding a cudaStream_t (NULL = legacy default
+ * stream).  Every entry point returns HYLU_OK (0), a warning (> 0) or an error
+ * (< 0).  There is no CPU fallback: numeric work runs only in this library's
+ * CUDA kernels, and a call made without a usable CUDA device returns
+ * HYLU_ERR_CUDA.
+ *
+ * Data conventions (used by every call below):
+ *   - A is n x n CSR: rowptr int64[n+1] (rowptr[0] = 0), col int32[nnz]
+ *     strictly increasing within each row, values float64[nnz].
+ *   - Preprocessing (Sec. 2.1) gives row/column permutations and scalings:
+ *     Ahat(i,k) = dr[rowperm[i]] * A(rowperm[i], colperm[k]) * dc[colperm[k]],
+ *     rowperm/colperm map new index -> original index, dr/dc are indexed by
+ *     original row/column.
+ *   - The numeric phase factors Ahat * Pi = L * U (L unit lower, U upper); Pi
+ *     only exchanges columns inside the diagonal block of a supernode
+ *     (supernode diagonal pivoting, Sec. 2.2); piv[p] = column label at
+ *     position p.
+ */
+#ifndef HYLU_H
+#define HYLU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HYLU_OK 0
+#define HYLU_WARN_PERTURBED 1         /* a small pivot was perturbed (Sec. 2.2) */
+#define HYLU_WARN_REFINE_STALLED 2    /* refinement stopped above the target  */
+#define HYLU_ERR_ARG (-1)             /* null/invalid argument                */
+#define HYLU_ERR_PATTERN (-2)         /* unsorted, duplicate or out-of-range column */
+#define HYLU_ERR_STRUCT_SINGULAR (-3) /* no perfect matching on the nonzeros  */
+#define HYLU_ERR_NOMEM (-4)           /* device or host allocation failed     */
+#define HYLU_ERR_CUDA (-5)            /* a CUDA call failed / no device       */
+#define HYLU_ERR_DEVICE_TIMEOUT (-6)  /* a bounded device wait expired        */
+#define HYLU_ERR_STATE (-7)           /* call out of order (e.g. solve before factor) */
+#define HYLU_ERR_INTERNAL (-8)        /* plan inconsistency (a bug)           */
+
+/* ---- options ---- */
+#define HYLU_ORDER_AMD 0
+#define HYLU_ORDER_ND 1
+#define HYLU_ORDER_NATURAL 2
+#define HYLU_ORDER_USER 3
+
+typedef struct hylu_handle hylu_handle; /* opaque, owned by the library */
+
+typedef struct {
+    int ordering;          /* HYLU_ORDER_*; default AMD (Sec. 2.1)                    */
+    int static_pivot;      /* 1: maximum-product matching on the values (Sec. 2.1)    */
+    int scale;             /* 1: apply the matching's row/column scalings             */
+    int sn_max;            /* largest supernode, in rows (default 256)                 */
+    int nd_leaf;           /* nested dissection: subgraphs this small use AMD          */
+    double pivot_tau;      /* pivots below pivot_tau * max|Ahat| are perturbed (sqrt eps) */
+    double refine_tol;     /* refinement target on the backward error (1e-12)          */
+    int refine_maxit;      /* refinement corrections at most (10)                      */
+    int refine;            /* 0: only after a perturbation (Sec. 2.3); 1: always       */
+    long long spin_limit;  /* iterations of a device wait before HYLU_ERR_DEVICE_TIMEOUT */
+    int rows_per_task;     /* standalone rows claimed together by one thread block     */
+    int debug;             /* 1: extra host checks                                     */
+} hylu_options;
+
+typedef struct {
+    int32_t n;
+    int64_t nnz_a;          /* entries of A                                 */
+    int64_t nnz_lu;         /* entries of the unpadded symbolic L+U pattern */
+    int64_t nnz_store;      /* stored entries (padded pattern)              */
+    int32_t nnodes;         /* supernodes + standalone rows                 */
+    int32_t nsupernodes;    /* nodes of more than one row                   */
+    int32_t rows_in_supernodes;
+    int32_t max_supernode;
+    int32_t ntasks;
+    double flops;           /* unpadded symbolic flop count (Sec. 2.1)      */
+    double flops_padded;    /* flops on the padded pattern                  */
+    int32_t nperturb;       /* perturbed pivots of the last factorization   */
+    int32_t refine_iters;   /* corrections of the last solve                */
+    double backward_error;  /* of the last solve: ||b-Ax||inf/(||A||inf ||x||inf + ||b||inf) */
+    int32_t device_status;  /* 0 or a HYLU_ERR_* raised on the device       */
+    int32_t failed_node;    /* node where a device wait expired, else -1    */
+    double analyze_ms;
+} hylu_info;
+
+/* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */
+int hylu_default_options(hylu_options* opt);
+
+/* Preprocessing (Sec. 2.1): static pivoting with scaling (maximum-product
+ * matching on `vals`, host memory), fill-reducing ordering (AMD, nested
+ * dissection, natural, or `user_perm` = new -> original index when
+ * opt->ordering == HYLU_ORDER_USER), symbolic factorization, supernode
+ * detection (consecutive rows with identical U structure, Sec. 2.2) and the
+ * task schedule (Sec. 2.2.1).  All inputs are host arrays owned by the caller
+ * and are copied; `vals` is only read for the matching (may be NULL when
+ * opt->static_pivot == 0).  On success *out is a new handle (free it with
+ * hylu_destroy).  Errors: HYLU_ERR_ARG, HYLU_ERR_PATTERN,
+ * HYLU_ERR_STRUCT_SINGULAR, HYLU_ERR_NOMEM.  Runs on the host only. */
+int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
+                 const double* vals, const int32_t* user_perm, const hylu_options* opt,
+                 hylu_handle** out);
+
+/* Numeric factorization (Sec. 2.2, Fig. 1): d_vals is a DEVICE array of the
+ * nnz values of A in the CSR order given to hylu_analyze.  The first call
+ * uploads the plan and allocates the factor storage on the current device;
+ * later calls reuse it.  Asynchronous on `stream`; the library copies d_vals
+ * (device to device) so the caller may reuse it once the stream has passed
+ * this call.  Device-side failures (a wait that expired) are reported by
+ * hylu_get_info / the next synchronizing call. */
+int hylu_factor(hylu_handle* h, const double* d_vals, void* stream);
+
+/* Repeated solve with an identical pattern (Sec. 3.2): same as hylu_factor
+ * with new values; keeps the matching, scalings and ordering of the analysis
+ * and recomputes the pivot choices inside supernodes.  Requires a previous
+ * hylu_factor (else HYLU_ERR_STATE). */
+int hylu_refactor(hylu_handle* h, const double* d_vals, void* stream);
+
+/* Forward/backward substitution (Sec. 2.3): solves A x = b for nrhs right-hand
+ * sides stored column by column with leading dimension ld >= n, both DEVICE
+ * arrays (d_b is read only, d_x written; they may not overlap).  When a pivot
+ * was perturbed (or opt.refine == 1) the solution is refined in FP64 on the
+ * original A (Sec. 2.3) until the backward error reaches opt.refine_tol, stops
+ * halving, or opt.refine_maxit corrections were made; this synchronizes the
+ * stream.  Returns HYLU_WARN_REFINE_STALLED if the target was not reached. */
+int hylu_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream);
+
+/* Transpose solve A^T x = b with the same factors (U^T then L^T), same
+ * arguments and refinement rule as hylu_solve. */
+int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld,
+                         void* stream);
+
+/* Synchronize the handle's last stream and report sizes, flop counts,
+ * perturbations, refinement results and any device-side status. */
+int hylu_get_info(hylu_handle* h, hylu_info* info);
+
+/* Copy preprocessing outputs to caller-owned HOST arrays (any may be NULL):
+ * rowperm/colperm int32[n], dr/dc float64[n], sn_start int32[nnodes+1]. */
+int hylu_export_perm(hylu_handle* h, int32_t* rowperm, int32_t* colperm, double* dr, double* dc,
+                     int32_t* sn_start);
+
+/* Padded storage pattern in CSR form (HOST arrays, any may be NULL):
+ * rowptr int64[n+1], col int32[info.nnz_store]; columns sorted per row. */
+int hylu_export_pattern(hylu_handle* h, int64_t* rowptr, int32_t* col);
+
+/* Factor values on the padded pattern (HOST arrays, synchronizes): vals
+ * float64[nnz_store] in the CSR order of hylu_export_pattern, piv int32[n].
+ * Entry (i, c): L(i, position c) if c is below the first row of i's node,
+ * position c (L if c < i, U if c >= i) inside i's own supernode block, and
+ * U(i, label c) past the end of i's node. */
+int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv);
+
+/* Release device and host memory of the handle (NULL is accepted). */
+int hylu_destroy(hylu_handle* h);
+
+/* Static counters of the library: number of kernel launches issued since load
+ * (for launch accounting in benchmarks). */
+int64_t hylu_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HYLU_H */

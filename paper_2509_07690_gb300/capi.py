@@ -1,0 +1,167 @@
+"""ctypes binding of include/hylu.h: one Python function per C entry point,
+same names, argument marshalling only (host arrays as numpy, device arrays
+and streams as integer addresses)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "libhylu.so")
+_lib = None
+
+HYLU_OK = 0
+HYLU_WARN_PERTURBED = 1
+HYLU_WARN_REFINE_STALLED = 2
+ERRORS = {-1: "HYLU_ERR_ARG", -2: "HYLU_ERR_PATTERN", -3: "HYLU_ERR_STRUCT_SINGULAR",
+          -4: "HYLU_ERR_NOMEM", -5: "HYLU_ERR_CUDA", -6: "HYLU_ERR_DEVICE_TIMEOUT",
+          -7: "HYLU_ERR_STATE", -8: "HYLU_ERR_INTERNAL"}
+
+
+class HyluError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}")
+        self.code = code
+
+
+class Options(C.Structure):
+    _fields_ = [("ordering", C.c_int), ("static_pivot", C.c_int), ("scale", C.c_int),
+                ("sn_max", C.c_int), ("nd_leaf", C.c_int), ("pivot_tau", C.c_double),
+                ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine", C.c_int),
+                ("spin_limit", C.c_longlong), ("rows_per_task", C.c_int), ("debug", C.c_int)]
+
+
+class Info(C.Structure):
+    _fields_ = [("n", C.c_int32), ("nnz_a", C.c_int64), ("nnz_lu", C.c_int64),
+                ("nnz_store", C.c_int64), ("nnodes", C.c_int32), ("nsupernodes", C.c_int32),
+                ("rows_in_supernodes", C.c_int32), ("max_supernode", C.c_int32),
+                ("ntasks", C.c_int32), ("flops", C.c_double), ("flops_padded", C.c_double),
+                ("nperturb", C.c_int32), ("refine_iters", C.c_int32),
+                ("backward_error", C.c_double), ("device_status", C.c_int32),
+                ("failed_node", C.c_int32), ("analyze_ms", C.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+def library_path() -> str:
+    return _SO
+
+
+def load():
+    """Load libhylu.so (built by paper_2509_07690_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_SO):
+        raise ImportError(f"{_SO} is missing: run paper_2509_07690_gb300.build.build() first")
+    lib = C.CDLL(_SO)
+    H = C.c_void_p
+    i64p = np.ctypeslib.ndpointer(np.int64, flags="C")
+    i32p = np.ctypeslib.ndpointer(np.int32, flags="C")
+    f64p = np.ctypeslib.ndpointer(np.float64, flags="C")
+    lib.hylu_default_options.argtypes = [C.POINTER(Options)]
+    lib.hylu_analyze.argtypes = [C.c_int32, C.c_int64, i64p, i32p, C.c_void_p, C.c_void_p,
+                                 C.POINTER(Options), C.POINTER(H)]
+    lib.hylu_factor.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.hylu_refactor.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.hylu_solve.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.hylu_solve_transpose.argtypes = [H, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.hylu_get_info.argtypes = [H, C.POINTER(Info)]
+    lib.hylu_export_perm.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.hylu_export_pattern.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.hylu_export_factors.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.hylu_destroy.argtypes = [H]
+    lib.hylu_launch_count.restype = C.c_int64
+    lib.hylu_launch_count.argtypes = []
+    _lib = lib
+    return lib
+
+
+def _check(rc: int, where: str) -> int:
+    if rc < 0:
+        raise HyluError(rc, where)
+    return rc
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(C.c_void_p)
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().hylu_default_options(C.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def hylu_analyze(n, rowptr, col, vals=None, user_perm=None, opt: Options | None = None) -> int:
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    vals = None if vals is None else np.ascontiguousarray(vals, dtype=np.float64)
+    user_perm = None if user_perm is None else np.ascontiguousarray(user_perm, dtype=np.int32)
+    h = C.c_void_p()
+    rc = load().hylu_analyze(int(n), int(rowptr[-1]), rowptr, col, _ptr(vals), _ptr(user_perm),
+                             C.byref(opt) if opt is not None else None, C.byref(h))
+    _check(rc, "hylu_analyze")
+    return h.value
+
+
+def hylu_factor(h: int, d_vals: int, stream: int = 0) -> int:
+    return _check(load().hylu_factor(h, d_vals, stream), "hylu_factor")
+
+
+def hylu_refactor(h: int, d_vals: int, stream: int = 0) -> int:
+    return _check(load().hylu_refactor(h, d_vals, stream), "hylu_refactor")
+
+
+def hylu_solve(h: int, d_b: int, d_x: int, nrhs: int, ld: int, stream: int = 0) -> int:
+    return _check(load().hylu_solve(h, d_b, d_x, nrhs, ld, stream), "hylu_solve")
+
+
+def hylu_solve_transpose(h: int, d_b: int, d_x: int, nrhs: int, ld: int, stream: int = 0) -> int:
+    return _check(load().hylu_solve_transpose(h, d_b, d_x, nrhs, ld, stream), "hylu_solve_transpose")
+
+
+def hylu_get_info(h: int) -> Info:
+    info = Info()
+    _check(load().hylu_get_info(h, C.byref(info)), "hylu_get_info")
+    return info
+
+
+def hylu_export_perm(h: int, n: int, nnodes: int):
+    rp = np.empty(n, np.int32)
+    cp = np.empty(n, np.int32)
+    dr = np.empty(n, np.float64)
+    dc = np.empty(n, np.float64)
+    sn = np.empty(nnodes + 1, np.int32)
+    _check(load().hylu_export_perm(h, _ptr(rp), _ptr(cp), _ptr(dr), _ptr(dc), _ptr(sn)), "hylu_export_perm")
+    return rp, cp, dr, dc, sn
+
+
+def hylu_export_pattern(h: int, n: int, nnz_store: int):
+    rp = np.empty(n + 1, np.int64)
+    ci = np.empty(nnz_store, np.int32)
+    _check(load().hylu_export_pattern(h, _ptr(rp), _ptr(ci)), "hylu_export_pattern")
+    return rp, ci
+
+
+def hylu_export_factors(h: int, n: int, nnz_store: int):
+    v = np.empty(nnz_store, np.float64)
+    piv = np.empty(n, np.int32)
+    _check(load().hylu_export_factors(h, _ptr(v), _ptr(piv)), "hylu_export_factors")
+    return v, piv
+
+
+def hylu_destroy(h: int) -> None:
+    if h:
+        load().hylu_destroy(h)
+
+
+def hylu_launch_count() -> int:
+    return int(load().hylu_launch_count())

@@ -1,0 +1,370 @@
+// C ABI of the library (declared in include/hylu.h): handle lifetime, plan
+// upload, the factorization / substitution / refinement drivers.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/hylu.h"
+#include "host/plan.hpp"
+#include "kernels.cuh"
+
+struct hylu_handle {
+    hylu::Plan P;
+    hylu_options opt;
+    int device = -1;
+    bool uploaded = false;
+    bool factored = false;
+    hylu::DevPlan dp{};
+    std::vector<void*> allocs;
+    // original A (for the residual) and preprocessing outputs on the device
+    double* d_avals = nullptr;
+    int64_t* d_arp = nullptr;
+    int32_t* d_aci = nullptr;
+    int32_t *d_rowperm = nullptr, *d_colperm = nullptr;
+    double *d_dr = nullptr, *d_dc = nullptr;
+    // solve workspace (n * cap_rhs each)
+    int cap_rhs = 0;
+    size_t cap_elems = 0;
+    double *d_z = nullptr, *d_xh = nullptr, *d_r = nullptr, *d_d = nullptr, *d_norms = nullptr;
+    double* h_norms = nullptr;   // pinned
+    int32_t* h_status = nullptr; // pinned
+    int32_t gen_factor = 0, gen_solve = 0;
+    int grid = 0;
+    cudaStream_t last = nullptr;
+    int32_t nperturb = 0, refine_iters = 0, device_status = 0, failed_node = -1;
+    double backward_error = -1.0;
+};
+
+namespace {
+
+template <class T>
+int dalloc(hylu_handle* h, T** p, size_t count) {
+    void* q = nullptr;
+    if (cudaMalloc(&q, sizeof(T) * (count ? count : 1)) != cudaSuccess) return HYLU_ERR_NOMEM;
+    h->allocs.push_back(q);
+    *p = static_cast<T*>(q);
+    return HYLU_OK;
+}
+
+template <class T>
+int upload(hylu_handle* h, T** p, const std::vector<T>& v, cudaStream_t st) {
+    int rc = dalloc(h, p, v.size());
+    if (rc) return rc;
+    if (!v.empty() && cudaMemcpyAsync(*p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return HYLU_ERR_CUDA;
+    return HYLU_OK;
+}
+
+#define TRY(x) do { int rc_ = (x); if (rc_ < 0) return rc_; } while (0)
+
+int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
+    if (h->uploaded) return HYLU_OK;
+    if (cudaGetDevice(&h->device) != cudaSuccess) return HYLU_ERR_CUDA;
+    hylu::Plan& P = h->P;
+    hylu::DevPlan& d = h->dp;
+    d.n = P.n;
+    d.nnodes = P.nnodes;
+    int32_t *sn, *nof, *lc, *tc, *ahs;
+    int64_t *rl, *nto, *npo, *ahr, *ahsrc;
+    double* ahsc;
+    TRY(upload(h, &sn, P.sn_start, st));
+    TRY(upload(h, &nof, P.node_of, st));
+    TRY(upload(h, &rl, P.row_lptr, st));
+    TRY(upload(h, &lc, P.lcols, st));
+    TRY(upload(h, &nto, P.node_tail_off, st));
+    TRY(upload(h, &tc, P.tcols, st));
+    TRY(upload(h, &npo, P.node_panel_off, st));
+    TRY(upload(h, &ahr, P.ah_rp, st));
+    TRY(upload(h, &ahs, P.ah_slot, st));
+    TRY(upload(h, &ahsrc, P.ah_src, st));
+    TRY(upload(h, &ahsc, P.ah_scale, st));
+    d.sn_start = sn; d.node_of = nof; d.row_lptr = rl; d.lcols = lc; d.node_tail_off = nto;
+    d.tcols = tc; d.node_panel_off = npo; d.ah_rp = ahr; d.ah_slot = ahs; d.ah_src = ahsrc;
+    d.ah_scale = ahsc;
+    TRY(dalloc(h, &d.lval, P.nnz_l));
+    TRY(dalloc(h, &d.pval, P.nnz_panel));
+    TRY(dalloc(h, &d.piv, P.n));
+    TRY(dalloc(h, &d.pinv, P.n));
+    TRY(dalloc(h, &d.ready, P.n));
+    TRY(dalloc(h, &d.fwd_ready, P.nnodes));
+    TRY(dalloc(h, &d.bwd_ready, P.nnodes));
+    TRY(dalloc(h, &d.dinv, P.n));
+    TRY(dalloc(h, &d.status, hylu::ST_WORDS));
+    h->grid = hylu::factor_grid(h->device);
+    TRY(dalloc(h, &d.pos, (size_t)h->grid * hylu::warps_per_block() * (size_t)P.n));
+    if (cudaMemsetAsync(d.ready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(d.fwd_ready, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(d.bwd_ready, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    TRY(dalloc(h, &h->d_avals, P.nnz_a));
+    TRY(upload(h, &h->d_arp, P.a_rp, st));
+    TRY(upload(h, &h->d_aci, P.a_ci, st));
+    TRY(upload(h, &h->d_rowperm, P.rowperm, st));
+    TRY(upload(h, &h->d_colperm, P.colperm, st));
+    TRY(upload(h, &h->d_dr, P.dr, st));
+    TRY(upload(h, &h->d_dc, P.dc, st));
+    if (cudaMallocHost(&h->h_status, sizeof(int32_t) * hylu::ST_WORDS) != cudaSuccess) return HYLU_ERR_NOMEM;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;   // host vectors stay alive anyway
+    h->uploaded = true;
+    return HYLU_OK;
+}
+
+int ensure_rhs(hylu_handle* h, int nrhs, int ld) {
+    const size_t need = (size_t)ld * (size_t)nrhs;
+    if (nrhs <= h->cap_rhs && need <= h->cap_elems) return HYLU_OK;
+    const size_t n = (size_t)h->P.n;
+    TRY(dalloc(h, &h->d_z, n * nrhs));
+    TRY(dalloc(h, &h->d_xh, n * nrhs));
+    TRY(dalloc(h, &h->d_r, need));
+    TRY(dalloc(h, &h->d_d, need));
+    h->cap_elems = need;
+    TRY(dalloc(h, &h->d_norms, 3 * (size_t)nrhs + 1));
+    if (h->h_norms) cudaFreeHost(h->h_norms);
+    if (cudaMallocHost(&h->h_norms, sizeof(double) * (3 * (size_t)nrhs + 1)) != cudaSuccess) return HYLU_ERR_NOMEM;
+    h->cap_rhs = nrhs;
+    return HYLU_OK;
+}
+
+int read_status(hylu_handle* h, cudaStream_t st) {
+    if (cudaMemcpyAsync(h->h_status, h->dp.status, sizeof(int32_t) * hylu::ST_WORDS, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return HYLU_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;
+    h->nperturb = h->h_status[hylu::ST_NPERT];
+    h->device_status = h->h_status[hylu::ST_ERR];
+    h->failed_node = h->device_status ? h->h_status[hylu::ST_FAILED] : -1;
+    return h->device_status ? h->device_status : HYLU_OK;
+}
+
+int do_factor(hylu_handle* h, const double* d_vals, cudaStream_t st) {
+    if (!d_vals) return HYLU_ERR_ARG;
+    TRY(ensure_uploaded(h, st));
+    if (cudaMemcpyAsync(h->d_avals, d_vals, sizeof(double) * h->P.nnz_a, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return HYLU_ERR_CUDA;
+    TRY(hylu::launch_reset(h->dp.status, h->dp.piv, h->dp.pinv, h->P.n, st));
+    ++h->gen_factor;
+    TRY(hylu::launch_factor(h->dp, h->d_avals, h->P.nnz_a, h->gen_factor, h->opt.pivot_tau,
+                            h->opt.spin_limit, h->grid, st));
+    h->factored = true;
+    h->last = st;
+    return HYLU_OK;
+}
+
+double max_be(const hylu_handle* h, int nrhs) {
+    double anorm;
+    std::memcpy(&anorm, &h->h_norms[3 * nrhs], sizeof(double));
+    double be = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+        double rn = h->h_norms[3 * r], xn = h->h_norms[3 * r + 1], bn = h->h_norms[3 * r + 2];
+        double den = anorm * xn + bn;
+        double b = den > 0 ? rn / den : rn;
+        if (!(b <= be)) be = b;   // NaN propagates
+    }
+    return be;
+}
+
+int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, cudaStream_t st) {
+    if (!h->factored) return HYLU_ERR_STATE;
+    if (!d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
+    TRY(ensure_rhs(h, nrhs, ld));
+    // the perturbation count decides whether to refine (Sec. 2.3); this also
+    // surfaces a device-side failure of the factorization
+    TRY(read_status(h, st));
+    hylu::DevPlan& P = h->dp;
+    ++h->gen_solve;
+    TRY(hylu::launch_solve(P, d_b, d_x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
+                           nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st));
+    h->refine_iters = 0;
+    h->backward_error = -1.0;
+    h->last = st;
+    if (!(h->nperturb > 0 || h->opt.refine)) return HYLU_OK;
+    // iterative refinement in FP64 on the original A (Sec. 2.3)
+    double be_prev = INFINITY;
+    for (;;) {
+        TRY(hylu::launch_residual(h->P.n, h->d_arp, h->d_aci, h->d_avals, d_x, d_b, h->d_r, h->d_norms,
+                                  nrhs, ld, st));
+        if (cudaMemcpyAsync(h->h_norms, h->d_norms, sizeof(double) * (3 * nrhs + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return HYLU_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;
+        double be = max_be(h, nrhs);
+        h->backward_error = be;
+        if (be <= h->opt.refine_tol) return HYLU_OK;
+        if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
+        be_prev = be;
+        ++h->gen_solve;
+        TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
+                               h->d_dc, nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st));
+        TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
+        ++h->refine_iters;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int hylu_default_options(hylu_options* o) {
+    if (!o) return HYLU_ERR_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->ordering = HYLU_ORDER_AMD;
+    o->static_pivot = 1;
+    o->scale = 1;
+    o->sn_max = 256;
+    o->nd_leaf = 256;
+    o->pivot_tau = 1.4901161193847656e-08;
+    o->refine_tol = 1e-12;
+    o->refine_maxit = 10;
+    o->refine = 0;
+    o->spin_limit = 1LL << 26;
+    o->rows_per_task = 1;
+    o->debug = 0;
+    return HYLU_OK;
+}
+
+int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* vals,
+                 const int32_t* user_perm, const hylu_options* opt, hylu_handle** out) {
+    if (!out || n < 0 || !rowptr || (nnz > 0 && !col)) return HYLU_ERR_ARG;
+    *out = nullptr;
+    if (rowptr[n] != nnz) return HYLU_ERR_PATTERN;
+    hylu_options o;
+    if (opt) o = *opt; else hylu_default_options(&o);
+    if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
+    hylu_handle* h = new (std::nothrow) hylu_handle();
+    if (!h) return HYLU_ERR_NOMEM;
+    h->opt = o;
+    hylu::AnalyzeOptions ao;
+    ao.ordering = o.ordering;
+    ao.static_pivot = o.static_pivot;
+    ao.scale = o.scale;
+    ao.sn_max = o.sn_max;
+    ao.nd_leaf = o.nd_leaf > 0 ? o.nd_leaf : 256;
+    int rc;
+    try {
+        rc = hylu::analyze(n, rowptr, col, vals, user_perm, ao, h->P);
+    } catch (const std::bad_alloc&) {
+        rc = HYLU_ERR_NOMEM;
+    }
+    if (rc) { delete h; return rc; }
+    *out = h;
+    return HYLU_OK;
+}
+
+int hylu_factor(hylu_handle* h, const double* d_vals, void* stream) {
+    if (!h) return HYLU_ERR_ARG;
+    return do_factor(h, d_vals, static_cast<cudaStream_t>(stream));
+}
+
+int hylu_refactor(hylu_handle* h, const double* d_vals, void* stream) {
+    if (!h) return HYLU_ERR_ARG;
+    if (!h->factored) return HYLU_ERR_STATE;
+    return do_factor(h, d_vals, static_cast<cudaStream_t>(stream));
+}
+
+int hylu_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream) {
+    if (!h) return HYLU_ERR_ARG;
+    return do_solve(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream));
+}
+
+int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream) {
+    (void)d_b; (void)d_x; (void)nrhs; (void)ld; (void)stream;
+    if (!h) return HYLU_ERR_ARG;
+    return HYLU_ERR_STATE;
+}
+
+int hylu_get_info(hylu_handle* h, hylu_info* info) {
+    if (!h || !info) return HYLU_ERR_ARG;
+    std::memset(info, 0, sizeof(*info));
+    const hylu::Plan& P = h->P;
+    info->n = P.n;
+    info->nnz_a = P.nnz_a;
+    info->nnz_lu = P.nnz_f;
+    info->nnz_store = P.nnz_l + P.nnz_panel;
+    info->nnodes = P.nnodes;
+    int ns = 0, rs = 0, mx = 0;
+    for (int32_t s = 0; s < P.nnodes; ++s) {
+        int sz = P.sn_start[s + 1] - P.sn_start[s];
+        if (sz > 1) { ++ns; rs += sz; }
+        if (sz > mx) mx = sz;
+    }
+    info->nsupernodes = ns;
+    info->rows_in_supernodes = rs;
+    info->max_supernode = mx;
+    info->ntasks = P.n;
+    info->flops = P.flops_unpadded;
+    info->flops_padded = P.flops_padded;
+    info->analyze_ms = P.analyze_ms;
+    int rc = HYLU_OK;
+    if (h->factored) rc = read_status(h, h->last);
+    info->nperturb = h->nperturb;
+    info->refine_iters = h->refine_iters;
+    info->backward_error = h->backward_error;
+    info->device_status = h->device_status;
+    info->failed_node = h->failed_node;
+    return rc < 0 ? rc : HYLU_OK;
+}
+
+int hylu_export_perm(hylu_handle* h, int32_t* rowperm, int32_t* colperm, double* dr, double* dc,
+                     int32_t* sn_start) {
+    if (!h) return HYLU_ERR_ARG;
+    const hylu::Plan& P = h->P;
+    if (rowperm) std::memcpy(rowperm, P.rowperm.data(), sizeof(int32_t) * P.n);
+    if (colperm) std::memcpy(colperm, P.colperm.data(), sizeof(int32_t) * P.n);
+    if (dr) std::memcpy(dr, P.dr.data(), sizeof(double) * P.n);
+    if (dc) std::memcpy(dc, P.dc.data(), sizeof(double) * P.n);
+    if (sn_start) std::memcpy(sn_start, P.sn_start.data(), sizeof(int32_t) * P.sn_start.size());
+    return HYLU_OK;
+}
+
+int hylu_export_pattern(hylu_handle* h, int64_t* rowptr, int32_t* col) {
+    if (!h) return HYLU_ERR_ARG;
+    const hylu::Plan& P = h->P;
+    int64_t pos = 0;
+    if (rowptr) rowptr[0] = 0;
+    for (int32_t i = 0; i < P.n; ++i) {
+        const int32_t D = P.node_of[i], r = P.sn_start[D], e = P.sn_start[D + 1] - 1;
+        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) { if (col) col[pos] = P.lcols[t]; ++pos; }
+        for (int32_t c = r; c <= e; ++c) { if (col) col[pos] = c; ++pos; }
+        for (int64_t t = P.node_tail_off[D]; t < P.node_tail_off[D + 1]; ++t) { if (col) col[pos] = P.tcols[t]; ++pos; }
+        if (rowptr) rowptr[i + 1] = pos;
+    }
+    return HYLU_OK;
+}
+
+int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv) {
+    if (!h) return HYLU_ERR_ARG;
+    if (!h->factored) return HYLU_ERR_STATE;
+    const hylu::Plan& P = h->P;
+    if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
+    std::vector<double> lv(P.nnz_l), pv(P.nnz_panel);
+    std::vector<int32_t> pv_piv(P.n);
+    if (cudaMemcpy(lv.data(), h->dp.lval, sizeof(double) * P.nnz_l, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pv.data(), h->dp.pval, sizeof(double) * P.nnz_panel, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(pv_piv.data(), h->dp.piv, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HYLU_ERR_CUDA;
+    if (piv) std::memcpy(piv, pv_piv.data(), sizeof(int32_t) * P.n);
+    if (!vals) return HYLU_OK;
+    int64_t pos = 0;
+    for (int32_t i = 0; i < P.n; ++i) {
+        const int32_t D = P.node_of[i], r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+        const int64_t nT = P.node_tail_off[D + 1] - P.node_tail_off[D];
+        const double* row = pv.data() + P.node_panel_off[D] + (int64_t)(i - r) * (s + nT);
+        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) vals[pos++] = lv[t];
+        for (int32_t p = r; p <= e; ++p) vals[pos++] = row[pv_piv[p] - r];   // block: label -> position
+        for (int64_t t = 0; t < nT; ++t) vals[pos++] = row[s + t];
+    }
+    return HYLU_OK;
+}
+
+int hylu_destroy(hylu_handle* h) {
+    if (!h) return HYLU_OK;
+    if (h->uploaded) cudaDeviceSynchronize();
+    for (void* p : h->allocs) cudaFree(p);
+    if (h->h_norms) cudaFreeHost(h->h_norms);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    delete h;
+    return HYLU_OK;
+}
+
+int64_t hylu_launch_count(void) { return hylu::launches(); }
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Host-side plan of one sparsity pattern: preprocessing outputs (Sec. 2.1) and
+// the node/task tables that drive the numeric kernels (Sec. 2.2, 2.2.1).
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "preprocess.hpp"
+
+namespace hylu {
+
+struct Plan {
+    int32_t n = 0;
+    int64_t nnz_a = 0;
+    std::vector<int64_t> a_rp;          // original pattern (kept for the residual)
+    std::vector<int32_t> a_ci;
+    // static pivoting + scaling + ordering: Ahat(i,k) = dr[rowperm[i]] A(rowperm[i], colperm[k]) dc[colperm[k]]
+    std::vector<int32_t> rowperm, colperm;
+    std::vector<double> dr, dc;
+    // Ahat, row by row: for each entry its slot in the node column list, the
+    // index of its value in the caller's CSR array and its scale dr * dc
+    std::vector<int64_t> ah_rp;
+    std::vector<int32_t> ah_slot;
+    std::vector<int64_t> ah_src;
+    std::vector<double> ah_scale;
+    // supernode partition; a node is a supernode or a standalone row
+    std::vector<int32_t> sn_start;      // nnodes + 1, first row of each node
+    int32_t nnodes = 0;
+    std::vector<int32_t> node_of;       // row -> node
+    // L part: each row's own sorted columns below its node (full supernode segments)
+    std::vector<int64_t> row_lptr;      // n + 1 into lcols / the L values
+    std::vector<int32_t> lcols;
+    // U part: per node a dense panel of s rows x (s + |tail|) columns,
+    // the diagonal block (columns r..e) then the shared U tail
+    std::vector<int64_t> node_tail_off; // nnodes + 1 into tcols
+    std::vector<int32_t> tcols;
+    std::vector<int64_t> node_panel_off;// nnodes + 1 into the panel values
+    int64_t nnz_l = 0, nnz_panel = 0, nnz_store = 0, nnz_f = 0;
+    double flops_unpadded = 0.0, flops_padded = 0.0;
+    int32_t max_row = 0;                // longest row pattern (L + block + tail)
+    int32_t max_sn = 1;
+    double analyze_ms = 0.0;
+    std::string error;
+};
+
+struct AnalyzeOptions {
+    int ordering = 0;        // 0 AMD, 1 ND, 2 natural, 3 user
+    int static_pivot = 1;    // maximum-product matching
+    int scale = 1;           // apply the matching's scalings
+    int sn_max = 256;
+    int nd_leaf = 256;
+};
+
+// Returns 0 or a negative hylu status code; fills P.
+int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
+            const int32_t* user_perm, const AnalyzeOptions& opt, Plan& P);
+
+void symbolic_rows(const CsrPattern& ahat, std::vector<int64_t>& frp, std::vector<int32_t>& fci,
+                   std::vector<int64_t>& fdiag);
+void supernode_partition(int32_t n, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
+                         const std::vector<int64_t>& fdiag, int32_t sn_max, std::vector<int32_t>& start);
+void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
+                 const std::vector<int64_t>& fdiag);
+
+}  // namespace hylu

@@ -1,0 +1,151 @@
+// Symbolic factorization, supernode detection, padded storage pattern and
+// the node/task tables of the numeric phase (HYLU Sec. 2.1 and Sec. 2.2).
+//
+// Row structure (up-looking): row i holds Ahat(i,:), i, and for every k < i it
+// holds, U(k, >k).  Rows are found by depth-first search over the graph of U
+// from the lower entries of Ahat(i,:).  The search follows a pruned adjacency
+// (Eisenstat and Liu): once a row p with L(p,k) != 0 and U(k,p) != 0 has been
+// built, U(k, >p) is contained in U(p,:), so the search from k may stop at p.
+// This gives the same sets as the plain closure in far less time.
+#include <algorithm>
+#include <cstdint>
+#include <cstring>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace hylu {
+
+void symbolic_rows(const CsrPattern& ahat, std::vector<int64_t>& frp, std::vector<int32_t>& fci,
+                   std::vector<int64_t>& fdiag) {
+    const int32_t n = ahat.n;
+    frp.assign(n + 1, 0);
+    fci.clear();
+    fci.reserve((size_t)ahat.rp[n] * 4 + n);
+    fdiag.assign(n, 0);
+    std::vector<int64_t> prune_end(n, -1);     // end (exclusive) of the traversed part of U(k,:)
+    std::vector<int32_t> mark(n, -1);
+    std::vector<int32_t> lset, uset;
+    std::vector<std::pair<int32_t, int64_t>> stack;
+    for (int32_t i = 0; i < n; ++i) {
+        lset.clear(); uset.clear();
+        mark[i] = i; uset.push_back(i);
+        for (int64_t q = ahat.rp[i]; q < ahat.rp[i + 1]; ++q) {
+            int32_t c = ahat.ci[q];
+            if (mark[c] == i) continue;
+            mark[c] = i;
+            if (c > i) { uset.push_back(c); continue; }
+            // DFS from c over the pruned U graph, collecting nodes < i
+            lset.push_back(c);
+            stack.clear();
+            stack.push_back({c, fdiag[c] + 1});
+            while (!stack.empty()) {
+                int32_t k = stack.back().first;
+                int64_t& it = stack.back().second;
+                int64_t end = prune_end[k] >= 0 ? prune_end[k] : frp[k + 1];
+                bool pushed = false;
+                while (it < end) {
+                    int32_t j = fci[it++];
+                    if (mark[j] == i) continue;
+                    mark[j] = i;
+                    if (j < i) { lset.push_back(j); stack.push_back({j, fdiag[j] + 1}); pushed = true; break; }
+                    uset.push_back(j);
+                }
+                if (!pushed) stack.pop_back();
+            }
+        }
+        std::sort(lset.begin(), lset.end());
+        std::sort(uset.begin(), uset.end());
+        fci.insert(fci.end(), lset.begin(), lset.end());
+        fdiag[i] = (int64_t)fci.size();
+        fci.insert(fci.end(), uset.begin(), uset.end());
+        frp[i + 1] = (int64_t)fci.size();
+        // symmetric pruning of the sources of row i
+        for (int32_t k : lset) {
+            if (prune_end[k] >= 0) continue;
+            const int32_t* b = fci.data() + fdiag[k] + 1;
+            const int32_t* e = fci.data() + frp[k + 1];
+            const int32_t* f = std::lower_bound(b, e, i);
+            if (f != e && *f == i) prune_end[k] = (int64_t)(f - fci.data()) + 1;
+        }
+    }
+}
+
+void supernode_partition(int32_t n, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
+                         const std::vector<int64_t>& fdiag, int32_t sn_max, std::vector<int32_t>& start) {
+    start.clear();
+    start.push_back(0);
+    int32_t cur = 0;
+    for (int32_t r = 0; r + 1 < n; ++r) {
+        int64_t lr = frp[r + 1] - fdiag[r], ln = frp[r + 2] - fdiag[r + 1];
+        bool same = (lr - 1 == ln) &&
+                    std::memcmp(fci.data() + fdiag[r] + 1, fci.data() + fdiag[r + 1], sizeof(int32_t) * ln) == 0;
+        if (!same || (r + 1 - cur) >= sn_max) { cur = r + 1; start.push_back(r + 1); }
+    }
+    start.push_back(n);
+}
+
+// Padded pattern (Sec. 2.2 storage, read as): each row keeps its own L
+// columns, widened to whole source supernodes; every node stores its rows'
+// diagonal block densely together with the shared U tail.
+void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
+                 const std::vector<int64_t>& fdiag) {
+    const int32_t n = P.n;
+    const int32_t nn = (int32_t)P.sn_start.size() - 1;
+    P.nnodes = nn;
+    P.node_of.assign(n, 0);
+    for (int32_t s = 0; s < nn; ++s)
+        for (int32_t i = P.sn_start[s]; i < P.sn_start[s + 1]; ++i) P.node_of[i] = s;
+    P.row_lptr.assign(n + 1, 0);
+    P.lcols.clear();
+    P.node_tail_off.assign(nn + 1, 0);
+    P.node_panel_off.assign(nn + 1, 0);
+    P.tcols.clear();
+    std::vector<char> in(n, 0);
+    std::vector<int32_t> lst;
+    int64_t poff = 0;
+    P.max_row = 0;
+    for (int32_t s = 0; s < nn; ++s) {
+        int32_t r = P.sn_start[s], e = P.sn_start[s + 1] - 1, sz = e - r + 1;
+        for (int64_t q = fdiag[e] + 1; q < frp[e + 1]; ++q) P.tcols.push_back(fci[q]);
+        P.node_tail_off[s + 1] = (int64_t)P.tcols.size();
+        int64_t w = sz + (P.node_tail_off[s + 1] - P.node_tail_off[s]);
+        P.node_panel_off[s] = poff;
+        poff += w * sz;
+        P.node_panel_off[s + 1] = poff;
+        for (int32_t i = r; i <= e; ++i) {
+            lst.clear();
+            for (int64_t q = frp[i]; q < fdiag[i]; ++q) {
+                int32_t k = fci[q];
+                if (k >= r) break;
+                if (in[k]) continue;
+                int32_t S = P.node_of[k];
+                for (int32_t t = P.sn_start[S]; t < P.sn_start[S + 1]; ++t)
+                    if (!in[t]) { in[t] = 1; lst.push_back(t); }
+            }
+            std::sort(lst.begin(), lst.end());
+            for (int32_t t : lst) in[t] = 0;
+            P.lcols.insert(P.lcols.end(), lst.begin(), lst.end());
+            P.row_lptr[i + 1] = (int64_t)P.lcols.size();
+            P.max_row = std::max<int32_t>(P.max_row, (int32_t)(lst.size() + w));
+        }
+    }
+    P.nnz_l = (int64_t)P.lcols.size();
+    P.nnz_panel = poff;
+    P.nnz_store = P.nnz_l + P.nnz_panel;
+    // flop counts (Sec. 2.1): one division per L(i,k) plus two per U(k, >k) entry
+    double fu = 0.0, fp = 0.0;
+    std::vector<int64_t> ulen(n);
+    for (int32_t i = 0; i < n; ++i) ulen[i] = frp[i + 1] - fdiag[i];
+    for (int32_t i = 0; i < n; ++i)
+        for (int64_t q = frp[i]; q < fdiag[i]; ++q) fu += 1.0 + 2.0 * (double)(ulen[fci[q]] - 1);
+    for (int32_t i = 0; i < n; ++i) {
+        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) fp += 1.0 + 2.0 * (double)(ulen[P.lcols[t]] - 1);
+        for (int32_t k = P.sn_start[P.node_of[i]]; k < i; ++k) fp += 1.0 + 2.0 * (double)(ulen[k] - 1);
+    }
+    P.flops_unpadded = fu;
+    P.flops_padded = fp;
+    P.nnz_f = frp[n];
+}
+
+}  // namespace hylu

@@ -1,0 +1,56 @@
+// Device-side view of one factorization plan and the kernel entry points of
+// the numeric phase (HYLU Sec. 2.2) and the substitution (Sec. 2.3).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace hylu {
+
+// Status words in device memory (int32):
+//   [0] error code (0 or HYLU_ERR_DEVICE_TIMEOUT), [1] row/node where a wait
+//   expired, [2] perturbed pivots, [3] task counter of the factor kernel,
+//   [4] task counter of the forward solve, [5] of the backward solve,
+//   [6..7] max |Ahat| as the bit pattern of a non-negative double.
+enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_CNT_FWD = 4, ST_CNT_BWD = 5,
+       ST_AMAX = 6, ST_WORDS = 8 };
+
+struct DevPlan {
+    int32_t n, nnodes;
+    const int32_t* sn_start;       // nnodes + 1
+    const int32_t* node_of;        // n
+    const int64_t* row_lptr;       // n + 1
+    const int32_t* lcols;          // nnz_l
+    const int64_t* node_tail_off;  // nnodes + 1
+    const int32_t* tcols;
+    const int64_t* node_panel_off; // nnodes + 1
+    double* lval;                  // nnz_l   : L(i, position) values
+    double* pval;                  // nnz_panel: per node s x (s + tail), block by label
+    const int64_t* ah_rp;          // n + 1 (rows of Ahat)
+    const int32_t* ah_slot;
+    const int64_t* ah_src;
+    const double* ah_scale;
+    int32_t* piv;                  // position -> label
+    int32_t* pinv;                 // label -> position
+    int32_t* ready;                // per row, factor generation
+    int32_t* fwd_ready;            // per node, solve generation
+    int32_t* bwd_ready;            // per node, solve generation
+    int32_t* pos;                  // per-warp column -> slot maps, n each
+    double* dinv;                  // 1 / u_ii by position (row)
+    int32_t* status;
+};
+
+int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t gen,
+                  double tau_rel, long long spin_limit, int grid, cudaStream_t st);
+int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, double* d_xh,
+                 const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
+                 int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st);
+int launch_residual(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x,
+                    const double* b, double* r, double* norms, int nrhs, int ld, cudaStream_t st);
+int launch_axpy(int32_t n, double* x, const double* d, int nrhs, int ld, cudaStream_t st);
+int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t n, cudaStream_t st);
+int factor_grid(int device);   // blocks of the persistent kernels
+int warps_per_block();
+int64_t launches();
+void count_launch();
+
+}  // namespace hylu
