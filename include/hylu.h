@@ -64,8 +64,10 @@ typedef struct {
     int refine_maxit;      /* refinement corrections at most (10)                      */
     int refine;            /* 0: only after a perturbation (Sec. 2.3); 1: always       */
     long long spin_limit;  /* iterations of a device wait before HYLU_ERR_DEVICE_TIMEOUT */
-    int rows_per_task;     /* standalone rows claimed together by one thread block     */
+    int rows_per_task;     /* reserved (rows are claimed one per warp)                 */
     int debug;             /* 1: extra host checks                                     */
+    double amd_dense;      /* AMD: rows denser than max(16, amd_dense*sqrt(n)) go last (2) */
+    int timing;            /* 1: time the factor and solve kernels with CUDA events     */
 } hylu_options;
 
 typedef struct {
@@ -86,6 +88,8 @@ typedef struct {
     int32_t device_status;  /* 0 or a HYLU_ERR_* raised on the device       */
     int32_t failed_node;    /* node where a device wait expired, else -1    */
     double analyze_ms;
+    double factor_kernel_ms; /* last factorization kernel (opt.timing = 1), else -1 */
+    double solve_kernel_ms;  /* last substitution kernels (opt.timing = 1), else -1  */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */
@@ -157,9 +161,14 @@ int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv);
 /* Release device and host memory of the handle (NULL is accepted). */
 int hylu_destroy(hylu_handle* h);
 
-/* Static counters of the library: number of kernel launches issued since load
- * (for launch accounting in benchmarks). */
+/* Number of kernel launches this library has issued since it was loaded. */
 int64_t hylu_launch_count(void);
+
+/* Measure the FP64 fused multiply-add throughput of the current device (the
+ * roofline of the FP64 numeric kernels: the factorization is bound by the
+ * FP64 pipe on GB300).  Runs a short register-resident DFMA kernel on
+ * `stream` and synchronizes it; *gflops receives FLOP/s / 1e9 (2 per FMA). */
+int hylu_measure_fp64_peak(double* gflops, void* stream);
 
 #ifdef __cplusplus
 }

@@ -30,7 +30,8 @@ class Options(C.Structure):
     _fields_ = [("ordering", C.c_int), ("static_pivot", C.c_int), ("scale", C.c_int),
                 ("sn_max", C.c_int), ("nd_leaf", C.c_int), ("pivot_tau", C.c_double),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine", C.c_int),
-                ("spin_limit", C.c_longlong), ("rows_per_task", C.c_int), ("debug", C.c_int)]
+                ("spin_limit", C.c_longlong), ("rows_per_task", C.c_int), ("debug", C.c_int),
+                ("amd_dense", C.c_double), ("timing", C.c_int)]
 
 
 class Info(C.Structure):
@@ -40,7 +41,8 @@ class Info(C.Structure):
                 ("ntasks", C.c_int32), ("flops", C.c_double), ("flops_padded", C.c_double),
                 ("nperturb", C.c_int32), ("refine_iters", C.c_int32),
                 ("backward_error", C.c_double), ("device_status", C.c_int32),
-                ("failed_node", C.c_int32), ("analyze_ms", C.c_double)]
+                ("failed_node", C.c_int32), ("analyze_ms", C.c_double),
+                ("factor_kernel_ms", C.c_double), ("solve_kernel_ms", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -76,6 +78,7 @@ def load():
     lib.hylu_destroy.argtypes = [H]
     lib.hylu_launch_count.restype = C.c_int64
     lib.hylu_launch_count.argtypes = []
+    lib.hylu_measure_fp64_peak.argtypes = [C.POINTER(C.c_double), C.c_void_p]
     _lib = lib
     return lib
 
@@ -165,3 +168,9 @@ def hylu_destroy(h: int) -> None:
 
 def hylu_launch_count() -> int:
     return int(load().hylu_launch_count())
+
+
+def hylu_measure_fp64_peak(stream: int = 0) -> float:
+    g = C.c_double()
+    _check(load().hylu_measure_fp64_peak(C.byref(g), stream), "hylu_measure_fp64_peak")
+    return g.value

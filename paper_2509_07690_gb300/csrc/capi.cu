@@ -35,6 +35,8 @@ struct hylu_handle {
     cudaStream_t last = nullptr;
     int32_t nperturb = 0, refine_iters = 0, device_status = 0, failed_node = -1;
     double backward_error = -1.0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool timed_factor = false, timed_solve = false;
 };
 
 namespace {
@@ -90,6 +92,8 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     TRY(dalloc(h, &d.ready, P.n));
     TRY(dalloc(h, &d.fwd_ready, P.nnodes));
     TRY(dalloc(h, &d.bwd_ready, P.nnodes));
+    TRY(dalloc(h, &d.fwd_row, P.n));
+    TRY(dalloc(h, &d.bwd_row, P.n));
     TRY(dalloc(h, &d.dinv, P.n));
     TRY(dalloc(h, &d.status, hylu::ST_WORDS));
     h->grid = hylu::factor_grid(h->device);
@@ -97,6 +101,8 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     if (cudaMemsetAsync(d.ready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.fwd_ready, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.bwd_ready, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(d.fwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(d.bwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     TRY(dalloc(h, &h->d_avals, P.nnz_a));
     TRY(upload(h, &h->d_arp, P.a_rp, st));
     TRY(upload(h, &h->d_aci, P.a_ci, st));
@@ -105,6 +111,8 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     TRY(upload(h, &h->d_dr, P.dr, st));
     TRY(upload(h, &h->d_dc, P.dc, st));
     if (cudaMallocHost(&h->h_status, sizeof(int32_t) * hylu::ST_WORDS) != cudaSuccess) return HYLU_ERR_NOMEM;
+    for (int q = 0; q < 4; ++q)
+        if (cudaEventCreate(&h->ev[q]) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;   // host vectors stay alive anyway
     h->uploaded = true;
     return HYLU_OK;
@@ -144,7 +152,9 @@ int do_factor(hylu_handle* h, const double* d_vals, cudaStream_t st) {
     TRY(hylu::launch_reset(h->dp.status, h->dp.piv, h->dp.pinv, h->P.n, st));
     ++h->gen_factor;
     TRY(hylu::launch_factor(h->dp, h->d_avals, h->P.nnz_a, h->gen_factor, h->opt.pivot_tau,
-                            h->opt.spin_limit, h->grid, st));
+                            h->opt.spin_limit, h->grid, st, h->opt.timing ? h->ev[0] : nullptr,
+                            h->opt.timing ? h->ev[1] : nullptr));
+    if (h->opt.timing) h->timed_factor = true;
     h->factored = true;
     h->last = st;
     return HYLU_OK;
@@ -173,7 +183,9 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
     hylu::DevPlan& P = h->dp;
     ++h->gen_solve;
     TRY(hylu::launch_solve(P, d_b, d_x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
-                           nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st));
+                           nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st,
+                           h->opt.timing ? h->ev[2] : nullptr, h->opt.timing ? h->ev[3] : nullptr));
+    if (h->opt.timing) h->timed_solve = true;
     h->refine_iters = 0;
     h->backward_error = -1.0;
     h->last = st;
@@ -218,6 +230,8 @@ int hylu_default_options(hylu_options* o) {
     o->spin_limit = 1LL << 26;
     o->rows_per_task = 1;
     o->debug = 0;
+    o->amd_dense = 2.0;
+    o->timing = 0;
     return HYLU_OK;
 }
 
@@ -238,6 +252,7 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
     ao.scale = o.scale;
     ao.sn_max = o.sn_max;
     ao.nd_leaf = o.nd_leaf > 0 ? o.nd_leaf : 256;
+    ao.amd_dense = o.amd_dense > 0 ? o.amd_dense : 2.0;
     int rc;
     try {
         rc = hylu::analyze(n, rowptr, col, vals, user_perm, ao, h->P);
@@ -300,6 +315,11 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->backward_error = h->backward_error;
     info->device_status = h->device_status;
     info->failed_node = h->failed_node;
+    info->factor_kernel_ms = -1.0;
+    info->solve_kernel_ms = -1.0;
+    float ms = 0.f;
+    if (h->timed_factor && cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]) == cudaSuccess) info->factor_kernel_ms = ms;
+    if (h->timed_solve && cudaEventElapsedTime(&ms, h->ev[2], h->ev[3]) == cudaSuccess) info->solve_kernel_ms = ms;
     return rc < 0 ? rc : HYLU_OK;
 }
 
@@ -359,6 +379,7 @@ int hylu_destroy(hylu_handle* h) {
     if (!h) return HYLU_OK;
     if (h->uploaded) cudaDeviceSynchronize();
     for (void* p : h->allocs) cudaFree(p);
+    for (int q = 0; q < 4; ++q) if (h->ev[q]) cudaEventDestroy(h->ev[q]);
     if (h->h_norms) cudaFreeHost(h->h_norms);
     if (h->h_status) cudaFreeHost(h->h_status);
     delete h;
@@ -366,5 +387,10 @@ int hylu_destroy(hylu_handle* h) {
 }
 
 int64_t hylu_launch_count(void) { return hylu::launches(); }
+
+int hylu_measure_fp64_peak(double* gflops, void* stream) {
+    if (!gflops) return HYLU_ERR_ARG;
+    return hylu::measure_fp64_peak(gflops, static_cast<cudaStream_t>(stream));
+}
 
 }  // extern "C"

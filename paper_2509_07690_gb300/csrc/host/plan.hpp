@@ -49,6 +49,7 @@ struct AnalyzeOptions {
     int scale = 1;           // apply the matching's scalings
     int sn_max = 256;
     int nd_leaf = 256;
+    double amd_dense = 2.0;
 };
 
 // Returns 0 or a negative hylu status code; fills P.

@@ -138,56 +138,100 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
             *slot_ptr(xl, xu, nL, sl) = vals[P.ah_src[q]] * P.ah_scale[q];
         }
         __syncwarp();
-        // ---- updates from earlier nodes, ascending
+        // ---- updates from earlier nodes, ascending.  The metadata and ready
+        //      flags of the next 32 L entries are fetched at once (one lane
+        //      each); a source found ready then needs no further wait.
         int t = 0;
         while (t < nL) {
-            const int k = lc[t];
-            const int S = P.node_of[k];
-            const int rS = P.sn_start[S], eS = P.sn_start[S + 1] - 1, sS = eS - rS + 1;
-            if (!warp_wait(P.ready + eS, gen, P.status, eS, limit)) return;
-            const int64_t tS = P.node_tail_off[S];
-            const int nTS = (int)(P.node_tail_off[S + 1] - tS);
-            const int wS = sS + nTS;
-            const double* U = P.pval + P.node_panel_off[S];
-            const int32_t* tcS = P.tcols + tS;
-            if (sS == 1) {
-                // row-row: l = x_k / u_kk, x[U(k, >k)] -= l * U(k, >k)
-                const double l = xl[t] * dinv[k];
-                for (int j = lane; j < nTS; j += 32) {
-                    const int sl = pos[tcS[j]];
-                    *slot_ptr(xl, xu, nL, sl) -= l * U[1 + j];
-                }
-                __syncwarp();
-                if (lane == 0) xl[t] = l;
-                __syncwarp();
-                t += 1;
-            } else {
-                // sup-row: l * U_SS = x_S (by position), x[T_S] -= l * U_S,T_S
-                for (int p = lane; p < sS; p += 32) {
-                    const int lab = P.piv[rS + p] - rS;
-                    pb[p] = lab;
-                    lb[p] = xl[t + lab];
-                }
-                __syncwarp();
-                for (int p = 0; p < sS; ++p) {
-                    const double* Up = U + (int64_t)p * wS;
-                    const double lp = lb[p] * dinv[rS + p];
-                    __syncwarp();
-                    for (int q = p + 1 + lane; q < sS; q += 32) lb[q] -= lp * Up[pb[q]];
-                    if (lane == 0) lb[p] = lp;
-                    __syncwarp();
-                }
-                for (int j = lane; j < nTS; j += 32) {
-                    const double* Uj = U + sS + j;
-                    double acc = 0.0;
-                    for (int p = 0; p < sS; ++p) acc = fma(lb[p], Uj[(int64_t)p * wS], acc);
-                    const int sl = pos[tcS[j]];
-                    *slot_ptr(xl, xu, nL, sl) -= acc;
-                }
-                for (int p = lane; p < sS; p += 32) xl[t + p] = lb[p];
-                __syncwarp();
-                t += sS;
+            const int tq = t + lane;
+            int kq = 0, eq = 0, sq = 1, nTq = 0, okq = 1;
+            int64_t tq0 = 0, pq0 = 0;
+            if (tq < nL) {
+                kq = lc[tq];
+                const int Sq = P.node_of[kq];
+                const int rq = P.sn_start[Sq];
+                eq = P.sn_start[Sq + 1] - 1;
+                sq = eq - rq + 1;
+                tq0 = P.node_tail_off[Sq];
+                nTq = (int)(P.node_tail_off[Sq + 1] - tq0);
+                pq0 = P.node_panel_off[Sq];
+                okq = (ld_acquire(P.ready + eq) == gen);
             }
+            const unsigned rmask = __ballot_sync(FULL, okq);
+            const int cend = min(32, nL - t);
+            int q = 0;
+            while (q < cend) {
+                const int k = __shfl_sync(FULL, kq, q);
+                const int eS = __shfl_sync(FULL, eq, q);
+                const int sS = __shfl_sync(FULL, sq, q);
+                const int nTS = __shfl_sync(FULL, nTq, q);
+                const int64_t tS = __shfl_sync(FULL, tq0, q);
+                const int64_t pS = __shfl_sync(FULL, pq0, q);
+                if (!((rmask >> q) & 1u))
+                    if (!warp_wait(P.ready + eS, gen, P.status, eS, limit)) return;
+                const int tt = t + q;
+                const int wS = sS + nTS;
+                const double* __restrict__ U = P.pval + pS;
+                const int32_t* __restrict__ tcS = P.tcols + tS;
+                if (sS == 1) {
+                    // row-row: l = x_k / u_kk, x[U(k, >k)] -= l * U(k, >k)
+                    const double l = xl[tt] * dinv[k];
+                    for (int j0 = 0; j0 < nTS; j0 += 128) {
+                        int c[4];
+                        double u[4], xv[4];
+                        double* px[4];
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) {
+                            const int j = j0 + m * 32 + lane;
+                            c[m] = (j < nTS) ? tcS[j] : -1;
+                            u[m] = (j < nTS) ? U[1 + j] : 0.0;
+                        }
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) px[m] = (c[m] >= 0) ? slot_ptr(xl, xu, nL, pos[c[m]]) : nullptr;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) xv[m] = px[m] ? *px[m] : 0.0;
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) if (px[m]) *px[m] = xv[m] - l * u[m];
+                    }
+                    __syncwarp();
+                    if (lane == 0) xl[tt] = l;
+                    __syncwarp();
+                    q += 1;
+                } else {
+                    // sup-row: l * U_SS = x_S (by position), x[T_S] -= l * U_S,T_S
+                    const int rS = eS - sS + 1;
+                    for (int p = lane; p < sS; p += 32) {
+                        const int lab = P.piv[rS + p] - rS;
+                        pb[p] = lab;
+                        lb[p] = xl[tt + lab];
+                    }
+                    __syncwarp();
+                    for (int p = 0; p < sS; ++p) {
+                        const double* Up = U + (int64_t)p * wS;
+                        const double lp = lb[p] * dinv[rS + p];
+                        __syncwarp();
+                        for (int qq = p + 1 + lane; qq < sS; qq += 32) lb[qq] -= lp * Up[pb[qq]];
+                        if (lane == 0) lb[p] = lp;
+                        __syncwarp();
+                    }
+                    for (int j = lane; j < nTS; j += 32) {
+                        const double* Uj = U + sS + j;
+                        const int sl = pos[tcS[j]];
+                        double acc0 = 0.0, acc1 = 0.0;
+                        int p = 0;
+                        for (; p + 1 < sS; p += 2) {
+                            acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
+                            acc1 = fma(lb[p + 1], Uj[(int64_t)(p + 1) * wS], acc1);
+                        }
+                        if (p < sS) acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
+                        *slot_ptr(xl, xu, nL, sl) -= acc0 + acc1;
+                    }
+                    for (int p = lane; p < sS; p += 32) xl[tt + p] = lb[p];
+                    __syncwarp();
+                    q += sS;
+                }
+            }
+            t += q;
         }
         if (s > 1) {
             // ---- earlier rows of the own supernode, each as soon as it is ready
@@ -199,7 +243,20 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
                 const double l = xu[lab] * dinv[k];
                 for (int c = lane; c < s; c += 32)
                     if (c != lab && ld_relaxed(P.pinv + r + c) > k) xu[c] -= l * Uk[c];
-                for (int j = lane; j < nT; j += 32) xu[s + j] -= l * Uk[s + j];
+                for (int j0 = s; j0 < w; j0 += 128) {
+                    double u[4], xv[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int j = j0 + m * 32 + lane;
+                        u[m] = (j < w) ? Uk[j] : 0.0;
+                        xv[m] = (j < w) ? xu[j] : 0.0;
+                    }
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) {
+                        const int j = j0 + m * 32 + lane;
+                        if (j < w) xu[j] = xv[m] - l * u[m];
+                    }
+                }
                 __syncwarp();
                 if (lane == 0) xu[lab] = l;
                 __syncwarp();
@@ -265,70 +322,79 @@ __global__ void permute_out_kernel(int32_t n, const int32_t* __restrict__ colper
     }
 }
 
-// Forward substitution L z = bhat (unit L, by position), one node per warp in
-// ascending order; z holds bhat on entry.  Right-hand sides are columns of z
-// with stride n.
+// Bounded wait of the calling lanes on flag == gen; false on expiry/error.
+__device__ __forceinline__ bool lane_wait(const int* flag, int gen, int* status, int who, long long limit) {
+    if (ld_acquire(flag) == gen) return true;
+    long long it = 0;
+    while (ld_acquire(flag) != gen) {
+        if (++it > limit) {
+            if (atomicCAS(status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0) status[ST_FAILED] = who;
+            return false;
+        }
+        if ((it & 255) == 0 && ld_relaxed(status + ST_ERR) != 0) return false;
+    }
+    return true;
+}
+
+// Forward substitution L z = bhat (unit L, by position); z holds bhat on
+// entry.  Every warp claims the next row: it subtracts the row's L list
+// (waiting for each source node), and the warp of the LAST row of a
+// supernode then solves the unit lower block once all rows of the supernode
+// have their external part.  Right-hand sides are columns of z (stride n).
 __global__ void __launch_bounds__(WARPS * 32)
 fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit) {
-    __shared__ double acc_s[WARPS][SN_SMEM];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double* accb = acc_s[wid];
+    const int lane = threadIdx.x & 31;
     const int n = P.n;
     for (;;) {
-        int D = 0;
-        if (lane == 0) D = atomicAdd(P.status + ST_CNT_FWD, 1);
-        D = __shfl_sync(FULL, D, 0);
-        if (D >= P.nnodes) return;
+        int i = 0;
+        if (lane == 0) i = atomicAdd(P.status + ST_CNT_FWD, 1);
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
+        const int D = P.node_of[i];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
-        const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
-        const double* Ub = P.pval + P.node_panel_off[D];
-        // wait for every source node of every row (a source is ready once its
-        // last row is published)
-        for (int i = r; i <= e; ++i) {
-            const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
-            int ok = 1;
-            for (int64_t t = l0 + lane; t < l1 && ok; t += 32) {
-                const int S = P.node_of[P.lcols[t]];
-                if (ld_acquire(P.fwd_ready + S) != gen) {
-                    long long it = 0;
-                    while (ld_acquire(P.fwd_ready + S) != gen) {
-                        if (++it > limit) {
-                            if (atomicCAS(P.status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0) P.status[ST_FAILED] = S;
-                            ok = 0;
-                            break;
-                        }
-                        if ((it & 255) == 0 && ld_relaxed(P.status + ST_ERR) != 0) { ok = 0; break; }
-                    }
-                }
-            }
-            if (!__all_sync(FULL, ok)) return;
+        const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
+        int ok = 1;
+        for (int64_t t = l0 + lane; t < l1 && ok; t += 32) {
+            const int S = P.node_of[P.lcols[t]];
+            ok = lane_wait(P.fwd_ready + S, gen, P.status, S, limit);
         }
+        if (!__all_sync(FULL, ok)) return;
         for (int rr = 0; rr < nrhs; ++rr) {
             double* zr = z + (int64_t)rr * n;
-            for (int i = r; i <= e; ++i) {
-                const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
-                double a = 0.0;
-                for (int64_t t = l0 + lane; t < l1; t += 32) a = fma(P.lval[t], zr[P.lcols[t]], a);
-                for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                if (s == 1) {
-                    if (lane == 0) zr[i] -= a;
-                } else if (lane == 0) {
-                    accb[i - r] = zr[i] - a;
-                }
+            double a0 = 0.0, a1 = 0.0;
+            int64_t t = l0 + lane;
+            for (; t + 32 < l1; t += 64) {
+                a0 = fma(P.lval[t], zr[P.lcols[t]], a0);
+                a1 = fma(P.lval[t + 32], zr[P.lcols[t + 32]], a1);
             }
-            if (s > 1) {
-                __syncwarp();
-                // unit lower triangular block: L(i, pos k) = panel(i, piv[k])
-                for (int i = r; i <= e; ++i) {
-                    const double* Ui = Ub + (int64_t)(i - r) * w;
-                    double a = 0.0;
-                    for (int k = r + lane; k < i; k += 32) a = fma(Ui[P.piv[k] - r], accb[k - r], a);
-                    for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                    if (lane == 0) accb[i - r] -= a;
-                    __syncwarp();
-                }
-                for (int i = r + lane; i <= e; i += 32) zr[i] = accb[i - r];
+            if (t < l1) a0 = fma(P.lval[t], zr[P.lcols[t]], a0);
+            double a = a0 + a1;
+            for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+            if (lane == 0) zr[i] -= a;
+        }
+        __threadfence();
+        __syncwarp();
+        if (s == 1) {
+            if (lane == 0) st_release(P.fwd_ready + D, gen);
+            continue;
+        }
+        if (lane == 0) st_release(P.fwd_row + i, gen);
+        if (i != e) continue;
+        // last row of the supernode: block solve once every row has its external part
+        ok = 1;
+        for (int k = r + lane; k < e && ok; k += 32) ok = lane_wait(P.fwd_row + k, gen, P.status, k, limit);
+        if (!__all_sync(FULL, ok)) return;
+        const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+        const double* Ub = P.pval + P.node_panel_off[D];
+        for (int rr = 0; rr < nrhs; ++rr) {
+            double* zr = z + (int64_t)rr * n;
+            for (int ii = r + 1; ii <= e; ++ii) {
+                const double* Ui = Ub + (int64_t)(ii - r) * w;
+                double a = 0.0;
+                for (int k = r + lane; k < ii; k += 32) a = fma(Ui[P.piv[k] - r], zr[k], a);
+                for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+                if (lane == 0) zr[ii] -= a;
                 __syncwarp();
             }
         }
@@ -338,64 +404,76 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit
     }
 }
 
-// Backward substitution U w = z by position, nodes in descending order; the
-// solution is written by label: xh[piv[p]] = w_p.
+// Backward substitution U w = z by position, rows in descending order; the
+// solution is written by label: xh[piv[p]] = w_p.  Every warp claims the next
+// row (from the bottom), subtracts its U tail; the warp of the FIRST row of a
+// supernode then back-substitutes the block.  z is overwritten.
 __global__ void __launch_bounds__(WARPS * 32)
-bwd_kernel(DevPlan P, const double* __restrict__ dinv, const double* __restrict__ z,
+bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
            double* __restrict__ xh, int nrhs, int gen, long long limit) {
-    __shared__ double acc_s[WARPS][SN_SMEM];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double* accb = acc_s[wid];
+    const int lane = threadIdx.x & 31;
     const int n = P.n;
     for (;;) {
         int t = 0;
         if (lane == 0) t = atomicAdd(P.status + ST_CNT_BWD, 1);
         t = __shfl_sync(FULL, t, 0);
-        if (t >= P.nnodes) return;
+        if (t >= n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
-        const int D = P.nnodes - 1 - t;
+        const int i = n - 1 - t;
+        const int D = P.node_of[i];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int64_t t0 = P.node_tail_off[D];
         const int nT = (int)(P.node_tail_off[D + 1] - t0);
         const int w = s + nT;
         const int32_t* tc = P.tcols + t0;
-        const double* Ub = P.pval + P.node_panel_off[D];
+        const double* Ui = P.pval + P.node_panel_off[D] + (int64_t)(i - r) * w;
         int ok = 1;
         for (int j = lane; j < nT && ok; j += 32) {
             const int S = P.node_of[tc[j]];
-            if (ld_acquire(P.bwd_ready + S) != gen) {
-                long long it = 0;
-                while (ld_acquire(P.bwd_ready + S) != gen) {
-                    if (++it > limit) {
-                        if (atomicCAS(P.status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0) P.status[ST_FAILED] = S;
-                        ok = 0;
-                        break;
-                    }
-                    if ((it & 255) == 0 && ld_relaxed(P.status + ST_ERR) != 0) { ok = 0; break; }
-                }
-            }
+            ok = lane_wait(P.bwd_ready + S, gen, P.status, S, limit);
         }
         if (!__all_sync(FULL, ok)) return;
         for (int rr = 0; rr < nrhs; ++rr) {
-            const double* zr = z + (int64_t)rr * n;
-            double* xr = xh + (int64_t)rr * n;
-            for (int i = r; i <= e; ++i) {
-                const double* Ui = Ub + (int64_t)(i - r) * w + s;
-                double a = 0.0;
-                for (int j = lane; j < nT; j += 32) a = fma(Ui[j], xr[tc[j]], a);
-                for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                if (lane == 0) accb[i - r] = zr[i] - a;
+            double* zr = z + (int64_t)rr * n;
+            const double* xr = xh + (int64_t)rr * n;
+            double a0 = 0.0, a1 = 0.0;
+            int j = lane;
+            for (; j + 32 < nT; j += 64) {
+                a0 = fma(Ui[s + j], xr[tc[j]], a0);
+                a1 = fma(Ui[s + j + 32], xr[tc[j + 32]], a1);
             }
-            __syncwarp();
-            for (int i = e; i >= r; --i) {
-                const double* Ui = Ub + (int64_t)(i - r) * w;
+            if (j < nT) a0 = fma(Ui[s + j], xr[tc[j]], a0);
+            double a = a0 + a1;
+            for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+            if (lane == 0) {
+                if (s == 1) xh[(int64_t)rr * n + i] = (zr[i] - a) * dinv[i];
+                else zr[i] -= a;
+            }
+        }
+        __threadfence();
+        __syncwarp();
+        if (s == 1) {
+            if (lane == 0) st_release(P.bwd_ready + D, gen);
+            continue;
+        }
+        if (lane == 0) st_release(P.bwd_row + i, gen);
+        if (i != r) continue;
+        ok = 1;
+        for (int k = r + 1 + lane; k <= e && ok; k += 32) ok = lane_wait(P.bwd_row + k, gen, P.status, k, limit);
+        if (!__all_sync(FULL, ok)) return;
+        const double* Ub = P.pval + P.node_panel_off[D];
+        for (int rr = 0; rr < nrhs; ++rr) {
+            double* zr = z + (int64_t)rr * n;
+            double* xr = xh + (int64_t)rr * n;
+            for (int ii = e; ii >= r; --ii) {
+                const double* Uii = Ub + (int64_t)(ii - r) * w;
                 double a = 0.0;
-                for (int p = i + 1 + lane; p <= e; p += 32) a = fma(Ui[P.piv[p] - r], accb[p - r], a);
+                for (int p = ii + 1 + lane; p <= e; p += 32) a = fma(Uii[P.piv[p] - r], zr[p], a);
                 for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                if (lane == 0) accb[i - r] = (accb[i - r] - a) * dinv[i];
+                if (lane == 0) zr[ii] = (zr[ii] - a) * dinv[ii];
                 __syncwarp();
             }
-            for (int p = r + lane; p <= e; p += 32) xr[P.piv[p]] = accb[p - r];
+            for (int p = r + lane; p <= e; p += 32) xr[P.piv[p]] = zr[p];
             __syncwarp();
         }
         __threadfence();
@@ -480,29 +558,34 @@ int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t n, cudaSt
 }
 
 int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t gen,
-                  double tau_rel, long long spin_limit, int grid, cudaStream_t st) {
+                  double tau_rel, long long spin_limit, int grid, cudaStream_t st, cudaEvent_t e0,
+                  cudaEvent_t e1) {
     int blocks = (int)std::min<int64_t>(2048, (nnz_a + 255) / 256 + 1);
     amax_kernel<<<blocks, 256, 0, st>>>(d_vals, P.ah_src, P.ah_scale, nnz_a, P.status);
     count_launch();
-    factor_kernel<<<grid, WARPS * 32, 0, st>>>(P, d_vals, P.dinv, gen,
-                                                                            tau_rel, spin_limit);
+    if (e0) cudaEventRecord(e0, st);
+    factor_kernel<<<grid, WARPS * 32, 0, st>>>(P, d_vals, P.dinv, gen, tau_rel, spin_limit);
     count_launch();
+    if (e1) cudaEventRecord(e1, st);
     return check("factor");
 }
 
 int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, double* d_xh,
                  const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
-                 int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st) {
+                 int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st,
+                 cudaEvent_t e0, cudaEvent_t e1) {
     const int64_t tot = (int64_t)P.n * nrhs;
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
     if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return HYLU_ERR_CUDA;
     permute_in_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld);
     count_launch();
     const int blocks = grid;
+    if (e0) cudaEventRecord(e0, st);
     fwd_kernel<<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, gen, spin_limit);
     count_launch();
     bwd_kernel<<<blocks, WARPS * 32, 0, st>>>(P, P.dinv, d_z, d_xh, nrhs, gen, spin_limit);
     count_launch();
+    if (e1) cudaEventRecord(e1, st);
     permute_out_kernel<<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);
     count_launch();
     return check("solve");

@@ -34,16 +34,20 @@ struct DevPlan {
     int32_t* ready;                // per row, factor generation
     int32_t* fwd_ready;            // per node, solve generation
     int32_t* bwd_ready;            // per node, solve generation
+    int32_t* fwd_row;              // per row of a supernode, solve generation
+    int32_t* bwd_row;
     int32_t* pos;                  // per-warp column -> slot maps, n each
     double* dinv;                  // 1 / u_ii by position (row)
     int32_t* status;
 };
 
 int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t gen,
-                  double tau_rel, long long spin_limit, int grid, cudaStream_t st);
+                  double tau_rel, long long spin_limit, int grid, cudaStream_t st,
+                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, double* d_xh,
                  const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
-                 int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st);
+                 int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st,
+                 cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 int launch_residual(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x,
                     const double* b, double* r, double* norms, int nrhs, int ld, cudaStream_t st);
 int launch_axpy(int32_t n, double* x, const double* d, int nrhs, int ld, cudaStream_t st);
@@ -51,6 +55,7 @@ int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t n, cudaSt
 int factor_grid(int device);   // blocks of the persistent kernels
 int warps_per_block();
 int64_t launches();
+int measure_fp64_peak(double* gflops, cudaStream_t st);
 void count_launch();
 
 }  // namespace hylu
