@@ -44,6 +44,7 @@ extern "C" {
 #define HYLU_ERR_DEVICE_TIMEOUT (-6)  /* a bounded device wait expired        */
 #define HYLU_ERR_STATE (-7)           /* call out of order (e.g. solve before factor) */
 #define HYLU_ERR_INTERNAL (-8)        /* plan inconsistency (a bug)           */
+#define HYLU_ERR_TOO_LARGE (-9)       /* size above a fixed library limit     */
 
 /* ---- options ---- */
 #define HYLU_ORDER_AMD 0
@@ -160,6 +161,35 @@ int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv);
 
 /* Release device and host memory of the handle (NULL is accepted). */
 int hylu_destroy(hylu_handle* h);
+
+/* Substitution that allocates nothing (no counterpart in the paper: this is
+ * an interface for callers that must not allocate).  Some callers cannot let
+ * a library call cudaMalloc on their behalf: a program that reserves the whole
+ * device memory up front for its own pool (a framework's caching allocator),
+ * where an extra cudaMalloc fails or fragments that pool, and latency-bound
+ * loops, where cudaMalloc's implicit device-wide synchronization is not
+ * acceptable.  hylu_solve allocates its work vectors on first use; this call
+ * instead keeps them in one fixed array compiled into the library
+ * (2 * HYLU_STATIC_SOLVE_MAX_N doubles = 4 MiB, held on every device that
+ * loads the library until the process exits).
+ *
+ * Solves A x = b for ONE right-hand side with the factors of the last
+ * hylu_factor/hylu_refactor on `h` (which must have completed its own
+ * allocations earlier: this call does not allocate them).  d_b is read, d_x
+ * written, both DEVICE arrays of n doubles.  No iterative refinement is
+ * applied (use hylu_solve when a pivot was perturbed).  Asynchronous on
+ * `stream`; nothing is synchronized.
+ *
+ * Limits and sharing: n above HYLU_STATIC_SOLVE_MAX_N returns
+ * HYLU_ERR_TOO_LARGE before any device work.  The array is shared by every
+ * call in the process and keeps the last call's contents (all of it is
+ * rewritten before it is read, so nothing needs clearing); two calls whose
+ * work overlaps on the GPU -- on different streams, or on different handles
+ * -- race on it and must be ordered by the caller.  The first call on each
+ * device looks up the array's device address (cudaGetSymbolAddress, with that
+ * device current); make that first call before any stream capture. */
+#define HYLU_STATIC_SOLVE_MAX_N 262144
+int hylu_solve_static(hylu_handle* h, const double* d_b, double* d_x, void* stream);
 
 /* Number of kernel launches this library has issued since it was loaded. */
 int64_t hylu_launch_count(void);

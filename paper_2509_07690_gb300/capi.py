@@ -17,7 +17,9 @@ HYLU_WARN_PERTURBED = 1
 HYLU_WARN_REFINE_STALLED = 2
 ERRORS = {-1: "HYLU_ERR_ARG", -2: "HYLU_ERR_PATTERN", -3: "HYLU_ERR_STRUCT_SINGULAR",
           -4: "HYLU_ERR_NOMEM", -5: "HYLU_ERR_CUDA", -6: "HYLU_ERR_DEVICE_TIMEOUT",
-          -7: "HYLU_ERR_STATE", -8: "HYLU_ERR_INTERNAL"}
+          -7: "HYLU_ERR_STATE", -8: "HYLU_ERR_INTERNAL", -9: "HYLU_ERR_TOO_LARGE"}
+HYLU_ERR_TOO_LARGE = -9
+HYLU_STATIC_SOLVE_MAX_N = 262144
 
 
 class HyluError(RuntimeError):
@@ -79,6 +81,7 @@ def load():
     lib.hylu_launch_count.restype = C.c_int64
     lib.hylu_launch_count.argtypes = []
     lib.hylu_measure_fp64_peak.argtypes = [C.POINTER(C.c_double), C.c_void_p]
+    lib.hylu_solve_static.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
     _lib = lib
     return lib
 
@@ -174,3 +177,8 @@ def hylu_measure_fp64_peak(stream: int = 0) -> float:
     g = C.c_double()
     _check(load().hylu_measure_fp64_peak(C.byref(g), stream), "hylu_measure_fp64_peak")
     return g.value
+
+
+def hylu_solve_static(h: int, d_b: int, d_x: int, stream: int = 0) -> int:
+    """Allocation-free substitution for one right-hand side (see include/hylu.h)."""
+    return _check(load().hylu_solve_static(h, d_b, d_x, stream), "hylu_solve_static")

@@ -213,6 +213,21 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
 
 }  // namespace
 
+// Substitution into caller-provided work vectors z and xh (n doubles each):
+// no allocation, no synchronization, no refinement.  Used by the
+// allocation-free entry point in static_solve.cu.
+namespace hylu {
+int32_t handle_n(const hylu_handle* h) { return h->P.n; }
+
+int solve_into(hylu_handle* h, const double* d_b, double* d_x, double* z, double* xh, cudaStream_t st) {
+    if (!h->factored || !h->uploaded) return HYLU_ERR_STATE;
+    ++h->gen_solve;
+    h->last = st;
+    return launch_solve(h->dp, d_b, d_x, z, xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc, 1, h->P.n,
+                        h->gen_solve, h->opt.spin_limit, h->grid, st);
+}
+}  // namespace hylu
+
 extern "C" {
 
 int hylu_default_options(hylu_options* o) {
