@@ -191,6 +191,13 @@ int hylu_destroy(hylu_handle* h);
 #define HYLU_STATIC_SOLVE_MAX_N 262144
 int hylu_solve_static(hylu_handle* h, const double* d_b, double* d_x, void* stream);
 
+/* Diagnostics: when the handle was analysed with (opt.debug & 2), copy the
+ * per-row trace of the last factorization to the HOST array out[4 * n]:
+ * for row i, out[4i] = claim time, out[4i+1] = updates from earlier nodes
+ * done, out[4i+2] = published (ns, %globaltimer), out[4i+3] = (warp << 8) |
+ * panel mode.  HYLU_ERR_STATE when tracing is off. */
+int hylu_debug_trace(hylu_handle* h, unsigned long long* out);
+
 /* Number of kernel launches this library has issued since it was loaded. */
 int64_t hylu_launch_count(void);
 

@@ -82,6 +82,7 @@ def load():
     lib.hylu_launch_count.argtypes = []
     lib.hylu_measure_fp64_peak.argtypes = [C.POINTER(C.c_double), C.c_void_p]
     lib.hylu_solve_static.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.hylu_debug_trace.argtypes = [H, C.c_void_p]
     _lib = lib
     return lib
 
@@ -182,3 +183,9 @@ def hylu_measure_fp64_peak(stream: int = 0) -> float:
 def hylu_solve_static(h: int, d_b: int, d_x: int, stream: int = 0) -> int:
     """Allocation-free substitution for one right-hand side (see include/hylu.h)."""
     return _check(load().hylu_solve_static(h, d_b, d_x, stream), "hylu_solve_static")
+
+
+def hylu_debug_trace(h: int, n: int):
+    out = np.empty(4 * n, np.uint64)
+    _check(load().hylu_debug_trace(h, _ptr(out)), "hylu_debug_trace")
+    return out.reshape(n, 4)

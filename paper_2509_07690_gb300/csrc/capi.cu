@@ -1,5 +1,6 @@
 // C ABI of the library (declared in include/hylu.h): handle lifetime, plan
 // upload, the factorization / substitution / refinement drivers.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -85,13 +86,31 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     d.sn_start = sn; d.node_of = nof; d.row_lptr = rl; d.lcols = lc; d.node_tail_off = nto;
     d.tcols = tc; d.node_panel_off = npo; d.ah_rp = ahr; d.ah_slot = ahs; d.ah_src = ahsrc;
     d.ah_scale = ahsc;
+    int32_t* ro;
+    TRY(upload(h, &ro, P.row_order, st));
+    d.row_order = ro;
+    d.trace = nullptr;
+    if (h->opt.debug & 2) TRY(dalloc(h, &d.trace, 4 * (size_t)P.n));
     TRY(dalloc(h, &d.lval, P.nnz_l));
     TRY(dalloc(h, &d.pval, P.nnz_panel));
     TRY(dalloc(h, &d.piv, P.n));
     TRY(dalloc(h, &d.pinv, P.n));
     TRY(dalloc(h, &d.ready, P.n));
-    TRY(dalloc(h, &d.fwd_ready, P.nnodes));
-    TRY(dalloc(h, &d.bwd_ready, P.nnodes));
+    {
+        int32_t *fo, *bo, *fl, *bl, *fc, *bc;
+        TRY(upload(h, &fo, P.fwd_order, st));
+        TRY(upload(h, &bo, P.bwd_order, st));
+        TRY(upload(h, &fl, P.fwd_level, st));
+        TRY(upload(h, &bl, P.bwd_level, st));
+        TRY(upload(h, &fc, P.fwd_count, st));
+        TRY(upload(h, &bc, P.bwd_count, st));
+        d.fwd_order = fo; d.bwd_order = bo; d.fwd_level = fl; d.bwd_level = bl;
+        d.fwd_count = fc; d.bwd_count = bc;
+        d.n_fwd_levels = (int32_t)P.fwd_count.size();
+        d.n_bwd_levels = (int32_t)P.bwd_count.size();
+        TRY(dalloc(h, &d.fwd_done, P.fwd_count.size()));
+        TRY(dalloc(h, &d.bwd_done, P.bwd_count.size()));
+    }
     TRY(dalloc(h, &d.fwd_row, P.n));
     TRY(dalloc(h, &d.bwd_row, P.n));
     TRY(dalloc(h, &d.dinv, P.n));
@@ -99,8 +118,6 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     h->grid = hylu::factor_grid(h->device);
     TRY(dalloc(h, &d.pos, (size_t)h->grid * hylu::warps_per_block() * (size_t)P.n));
     if (cudaMemsetAsync(d.ready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
-    if (cudaMemsetAsync(d.fwd_ready, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess) return HYLU_ERR_CUDA;
-    if (cudaMemsetAsync(d.bwd_ready, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.fwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.bwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     TRY(dalloc(h, &h->d_avals, P.nnz_a));
@@ -402,6 +419,15 @@ int hylu_destroy(hylu_handle* h) {
 }
 
 int64_t hylu_launch_count(void) { return hylu::launches(); }
+
+int hylu_debug_trace(hylu_handle* h, unsigned long long* out) {
+    if (!h || !out) return HYLU_ERR_ARG;
+    if (!h->dp.trace) return HYLU_ERR_STATE;
+    if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemcpy(out, h->dp.trace, sizeof(unsigned long long) * 4 * (size_t)h->P.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HYLU_ERR_CUDA;
+    return HYLU_OK;
+}
 
 int hylu_measure_fp64_peak(double* gflops, void* stream) {
     if (!gflops) return HYLU_ERR_ARG;

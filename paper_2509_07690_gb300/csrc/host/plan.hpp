@@ -37,6 +37,17 @@ struct Plan {
     std::vector<int64_t> node_panel_off;// nnodes + 1 into the panel values
     int64_t nnz_l = 0, nnz_panel = 0, nnz_store = 0, nnz_f = 0;
     double flops_unpadded = 0.0, flops_padded = 0.0;
+    std::vector<double> row_flops;      // padded flops of each row
+    // claim order of the factor kernel: rows sorted by dependency level (a row
+    // depends on the last row of each source node and on the earlier rows of
+    // its own supernode), ties by row index
+    std::vector<int32_t> row_order;
+    int32_t row_levels = 0;
+    // substitution schedules (bulk mode of Sec. 2.2.1 / 2.3): node levels of
+    // the forward (L) and backward (U) dependency graphs, the rows in claim
+    // order (level by level; backward descending inside a level) and the
+    // number of nodes of every level
+    std::vector<int32_t> fwd_order, bwd_order, fwd_level, bwd_level, fwd_count, bwd_count;
     int32_t max_row = 0;                // longest row pattern (L + block + tail)
     int32_t max_sn = 1;
     double analyze_ms = 0.0;

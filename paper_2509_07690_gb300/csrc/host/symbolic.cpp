@@ -139,13 +139,79 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
     for (int32_t i = 0; i < n; ++i) ulen[i] = frp[i + 1] - fdiag[i];
     for (int32_t i = 0; i < n; ++i)
         for (int64_t q = frp[i]; q < fdiag[i]; ++q) fu += 1.0 + 2.0 * (double)(ulen[fci[q]] - 1);
+    P.row_flops.assign(n, 0.0);
     for (int32_t i = 0; i < n; ++i) {
-        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) fp += 1.0 + 2.0 * (double)(ulen[P.lcols[t]] - 1);
-        for (int32_t k = P.sn_start[P.node_of[i]]; k < i; ++k) fp += 1.0 + 2.0 * (double)(ulen[k] - 1);
+        double f = 0.0;
+        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) f += 1.0 + 2.0 * (double)(ulen[P.lcols[t]] - 1);
+        for (int32_t k = P.sn_start[P.node_of[i]]; k < i; ++k) f += 1.0 + 2.0 * (double)(ulen[k] - 1);
+        P.row_flops[i] = f;
+        fp += f;
     }
     P.flops_unpadded = fu;
     P.flops_padded = fp;
     P.nnz_f = frp[n];
+    // dependency levels (Sec. 2.2.1: the task graph is levelized so that rows
+    // of one level are independent); claiming rows level by level keeps the
+    // claimed rows close to ready
+    std::vector<int32_t> lev(n, 0);
+    int32_t maxl = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const int32_t D = P.node_of[i], r = P.sn_start[D];
+        int32_t l = (i > r) ? lev[i - 1] + 1 : 0;
+        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
+            const int32_t S = P.node_of[P.lcols[t]];
+            const int32_t eS = P.sn_start[S + 1] - 1;
+            l = std::max(l, lev[eS] + 1);
+            t += P.sn_start[S + 1] - P.sn_start[S];   // whole segment of S
+        }
+        lev[i] = l;
+        maxl = std::max(maxl, l);
+    }
+    P.row_levels = maxl + 1;
+    std::vector<int32_t> cnt(maxl + 2, 0);
+    for (int32_t i = 0; i < n; ++i) cnt[lev[i] + 1]++;
+    for (int32_t l = 0; l <= maxl; ++l) cnt[l + 1] += cnt[l];
+    P.row_order.assign(n, 0);
+    for (int32_t i = 0; i < n; ++i) P.row_order[cnt[lev[i]]++] = i;
+
+    // ---- substitution schedules
+    const int32_t nn2 = P.nnodes;
+    P.fwd_level.assign(nn2, 0);
+    P.bwd_level.assign(nn2, 0);
+    for (int32_t D = 0; D < nn2; ++D) {          // forward: sources are earlier nodes
+        int32_t l = 0;
+        for (int32_t i = P.sn_start[D]; i < P.sn_start[D + 1]; ++i)
+            for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
+                const int32_t S = P.node_of[P.lcols[t]];
+                l = std::max(l, P.fwd_level[S] + 1);
+                t += P.sn_start[S + 1] - P.sn_start[S];
+            }
+        P.fwd_level[D] = l;
+    }
+    for (int32_t D = nn2 - 1; D >= 0; --D) {     // backward: tail columns are later nodes
+        int32_t l = 0;
+        for (int64_t t = P.node_tail_off[D]; t < P.node_tail_off[D + 1]; ++t)
+            l = std::max(l, P.bwd_level[P.node_of[P.tcols[t]]] + 1);
+        P.bwd_level[D] = l;
+    }
+    auto schedule = [&](const std::vector<int32_t>& nl, bool descending, std::vector<int32_t>& order,
+                        std::vector<int32_t>& count) {
+        int32_t ml = 0;
+        for (int32_t D = 0; D < nn2; ++D) ml = std::max(ml, nl[D]);
+        count.assign(ml + 1, 0);
+        for (int32_t D = 0; D < nn2; ++D) count[nl[D]]++;
+        std::vector<int64_t> start(ml + 2, 0);
+        for (int32_t D = 0; D < nn2; ++D) start[nl[D] + 1] += P.sn_start[D + 1] - P.sn_start[D];
+        for (int32_t l = 0; l <= ml; ++l) start[l + 1] += start[l];
+        order.assign(n, 0);
+        if (!descending) {
+            for (int32_t i = 0; i < n; ++i) order[start[nl[P.node_of[i]]]++] = i;
+        } else {
+            for (int32_t i = n - 1; i >= 0; --i) order[start[nl[P.node_of[i]]]++] = i;
+        }
+    };
+    schedule(P.fwd_level, false, P.fwd_order, P.fwd_count);
+    schedule(P.bwd_level, true, P.bwd_order, P.bwd_count);
 }
 
 }  // namespace hylu

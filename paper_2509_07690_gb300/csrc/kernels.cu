@@ -25,6 +25,7 @@
 // diagonal block is stored by column LABEL (pre-pivot column), so that later
 // exchanges never move data; consumers read position p through piv[p].
 #include <algorithm>
+#include <climits>
 #include <cstdio>
 
 #include "kernels.cuh"
@@ -56,8 +57,10 @@ __device__ __forceinline__ void st_release(int* p, int v) {
 // expired or another warp already raised an error; the first expiry records
 // HYLU_ERR_DEVICE_TIMEOUT and the row/node waited on.
 __device__ __forceinline__ bool warp_wait(const int* flag, int gen, int* status, int who,
-                                          long long limit) {
+                                          long long limit, unsigned long long* waited = nullptr) {
     int ok = 1;
+    unsigned long long t0 = 0;
+    if (waited) asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t0));
     if (ld_acquire(flag) != gen) {
         long long it = 0;
         for (;;) {
@@ -68,13 +71,15 @@ __device__ __forceinline__ bool warp_wait(const int* flag, int gen, int* status,
                 break;
             }
             if ((it & 255) == 0 && ld_relaxed(status + ST_ERR) != 0) { ok = 0; break; }
+            if (it > 16) __nanosleep(64);
         }
     }
+    if (waited) {
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t1));
+        *waited += t1 - t0;
+    }
     return __all_sync(FULL, ok) != 0;
-}
-
-__device__ __forceinline__ double* slot_ptr(double* xl, double* xu, int nL, int sl) {
-    return sl < nL ? xl + sl : xu + (sl - nL);
 }
 
 // -------------------------------------------------------------- reset
@@ -99,23 +104,108 @@ __global__ void amax_kernel(const double* __restrict__ vals, const int64_t* __re
 }
 
 // -------------------------------------------------------------- factor
-__global__ void __launch_bounds__(WARPS * 32)
+// Per-warp shared memory of the factor kernel.
+constexpr int FWARPS = 4;          // warps per block of the factor kernel (one per SM sub-partition)
+constexpr int PANEL_BYTES = 4096;  // U part of the row being updated
+constexpr int PF = 4;              // leading tail entries prefetched per source
+constexpr int UNR = 8;             // independent 32-entry batches in flight
+struct WarpSmem {
+    double lb[SN_SMEM];            // source supernode: l by position
+    int pb[SN_SMEM];               // source supernode: label offset of each position
+    double win[32];                // x for the 32 L slots of the current window
+    int wcol[32];                  // their columns
+    int plen[32];                  // per window source: tail entries inside the window
+    int pfc[32][PF];               // per window source: its first PF tail columns
+    double pfu[32][PF];            //                    and values
+    __align__(16) unsigned char panel[PANEL_BYTES];
+};
+constexpr size_t FACTOR_SMEM = sizeof(WarpSmem) * FWARPS;
+
+__device__ __forceinline__ unsigned long long gtimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int bsearch_sm(const int* a, int m, int c) {
+    int lo = 0, hi = m - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (a[mid] < c) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Where the row's U part (diagonal block + tail) lives while it is updated:
+//   mode 0: shared memory, dense over columns r .. maxcol (index c - r)
+//   mode 1: shared memory, block then tail slots; tail found by binary search
+//   mode 2: the row's own panel storage in global memory (index by slot)
+struct Panel {
+    double* x;
+    const int* scols;
+    int mode, r, e, s, nL, nT;
+    __device__ __forceinline__ int idx(const int* pos, int c) const {
+        if (mode == 0 || c <= e) return c - r;
+        if (mode == 1) return s + bsearch_sm(scols, nT, c);
+        return pos[c] - nL;
+    }
+    __device__ __forceinline__ int tail_idx(const int* tc, int j) const {
+        return mode == 0 ? tc[j] - r : s + j;
+    }
+};
+
+// Update x with entries j in [j0, nTS) of a standalone source's tail, all with
+// multiplier l; entries with columns below r go to the L part (atomic adds to
+// global memory: no one reads them before the window moves past them and a
+// fence is taken), the others to the panel.  Loads of UNR batches are issued
+// before any update so that their latencies overlap.
+__device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, const double* __restrict__ U1,
+                                           int j0, int nTS, double l, int r, const int* pos, double* xl,
+                                           const Panel& pn, int lane) {
+    for (int jb = j0; jb < nTS; jb += 32 * UNR) {
+        int c[UNR];
+        double u[UNR];
+#pragma unroll
+        for (int m = 0; m < UNR; ++m) {
+            const int j = jb + m * 32 + lane;
+            c[m] = (j < nTS) ? __ldg(tcS + j) : -1;
+            u[m] = (j < nTS) ? __ldg(U1 + j) : 0.0;
+        }
+        int ix[UNR];
+#pragma unroll
+        for (int m = 0; m < UNR; ++m) ix[m] = (c[m] >= r) ? pn.idx(pos, c[m]) : ((c[m] >= 0) ? pos[c[m]] : -1);
+#pragma unroll
+        for (int m = 0; m < UNR; ++m) {
+            if (c[m] < 0) continue;
+            if (c[m] < r) atomicAdd(xl + ix[m], -l * u[m]);
+            else pn.x[ix[m]] -= l * u[m];
+        }
+    }
+}
+
+__global__ void __launch_bounds__(FWARPS * 32)
 factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ dinv, int gen,
               double tau_rel, long long limit) {
-    __shared__ double lbuf[WARPS][SN_SMEM];
-    __shared__ int pbuf[WARPS][SN_SMEM];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double* lb = lbuf[wid];
-    int* pb = pbuf[wid];
-    int* pos = P.pos + (size_t)(blockIdx.x * WARPS + wid) * (size_t)P.n;
+    WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + wid;
+    double* lb = ws->lb;
+    int* pb = ws->pb;
+    double* win = ws->win;
+    int* wcol = ws->wcol;
+    int* pos = P.pos + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.n;
     const double amax = __longlong_as_double(*reinterpret_cast<const long long*>(P.status + ST_AMAX));
     const double tau = tau_rel * amax;
     for (;;) {
-        int i = 0;
-        if (lane == 0) i = atomicAdd(P.status + ST_CNT_F, 1);
-        i = __shfl_sync(FULL, i, 0);
-        if (i >= P.n) return;
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(P.status + ST_CNT_F, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= P.n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
+        const int i = P.row_order[qi];
+        if (P.trace && lane == 0) P.trace[4 * (int64_t)i] = gtimer();
+        unsigned long long waited = 0;
+        unsigned long long* wp = P.trace ? &waited : nullptr;
         const int D = P.node_of[i];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int64_t l0 = P.row_lptr[i];
@@ -127,138 +217,231 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
         double* xu = P.pval + P.node_panel_off[D] + (int64_t)(i - r) * w;
         const int32_t* lc = P.lcols + l0;
         const int32_t* tc = P.tcols + t0;
-        // ---- clear the row, column -> slot map, scatter Ahat(i,:) (value scatter)
-        for (int t = lane; t < nL; t += 32) { xl[t] = 0.0; pos[lc[t]] = t; }
-        for (int t = lane; t < w; t += 32) xu[t] = 0.0;
-        for (int t = lane; t < s; t += 32) pos[r + t] = nL + t;
-        for (int t = lane; t < nT; t += 32) pos[tc[t]] = nL + s + t;
+        const int maxcol = nT > 0 ? tc[nT - 1] : e;
+        Panel pn;
+        pn.r = r; pn.e = e; pn.s = s; pn.nL = nL; pn.nT = nT;
+        pn.scols = reinterpret_cast<const int*>(ws->panel + sizeof(double) * (size_t)w);
+        int range;
+        if ((int64_t)(maxcol - r + 1) * 8 <= PANEL_BYTES) {
+            pn.mode = 0; pn.x = reinterpret_cast<double*>(ws->panel); range = maxcol - r + 1;
+        } else if ((int64_t)w * 8 + (int64_t)nT * 4 <= PANEL_BYTES) {
+            pn.mode = 1; pn.x = reinterpret_cast<double*>(ws->panel); range = w;
+        } else {
+            pn.mode = 2; pn.x = xu; range = w;
+        }
+        // ---- clear, column -> slot maps, scatter Ahat(i,:) (the value scatter).
+        //      The first 32 L slots start in the shared-memory window; later
+        //      L slots accumulate in global memory and are found through pos[]
+        //      (also used by a panel kept in global memory).
+        const bool need_pos = (nL > 32) || (pn.mode == 2);
+        win[lane] = 0.0;
+        for (int t = 32 + lane; t < nL; t += 32) xl[t] = 0.0;
+        if (need_pos) for (int t = lane; t < nL; t += 32) pos[lc[t]] = t;
+        for (int t = lane; t < range; t += 32) pn.x[t] = 0.0;
+        if (pn.mode == 1) {
+            int* sc = const_cast<int*>(pn.scols);
+            for (int j = lane; j < nT; j += 32) sc[j] = tc[j];
+        }
+        if (pn.mode == 2) for (int j = lane; j < nT; j += 32) pos[tc[j]] = nL + s + j;
         __syncwarp();
         for (int64_t q = P.ah_rp[i] + lane; q < P.ah_rp[i + 1]; q += 32) {
             const int sl = P.ah_slot[q];
-            *slot_ptr(xl, xu, nL, sl) = vals[P.ah_src[q]] * P.ah_scale[q];
+            const double v = vals[P.ah_src[q]] * P.ah_scale[q];
+            if (sl < nL) {
+                if (sl < 32) win[sl] = v; else xl[sl] = v;
+            } else {
+                const int us = sl - nL;
+                pn.x[us < s ? us : pn.tail_idx(tc, us - s)] = v;
+            }
         }
         __syncwarp();
-        // ---- updates from earlier nodes, ascending.  The metadata and ready
-        //      flags of the next 32 L entries are fetched at once (one lane
-        //      each); a source found ready then needs no further wait.
+        bool pending = (nL > 32);   // global L slots written: fence before reading them
+        // ---- updates from earlier nodes, ascending, 32 L slots at a time
         int t = 0;
         while (t < nL) {
+            const int cend = min(32, nL - t);
             const int tq = t + lane;
             int kq = 0, eq = 0, sq = 1, nTq = 0, okq = 1;
             int64_t tq0 = 0, pq0 = 0;
-            if (tq < nL) {
+            double dq = 0.0;
+            if (t > 0 && pending) { __threadfence(); pending = false; }
+            if (lane < cend) {
                 kq = lc[tq];
                 const int Sq = P.node_of[kq];
-                const int rq = P.sn_start[Sq];
                 eq = P.sn_start[Sq + 1] - 1;
-                sq = eq - rq + 1;
+                sq = eq - P.sn_start[Sq] + 1;
                 tq0 = P.node_tail_off[Sq];
                 nTq = (int)(P.node_tail_off[Sq + 1] - tq0);
                 pq0 = P.node_panel_off[Sq];
                 okq = (ld_acquire(P.ready + eq) == gen);
+                if (okq && sq == 1) {
+                    dq = dinv[kq];
+#pragma unroll
+                    for (int m = 0; m < PF; ++m) {
+                        ws->pfc[lane][m] = (m < nTq) ? P.tcols[tq0 + m] : INT_MAX;
+                        ws->pfu[lane][m] = (m < nTq) ? P.pval[pq0 + 1 + m] : 0.0;
+                    }
+                }
+                if (t > 0) win[lane] = xl[tq];
+                wcol[lane] = kq;
             }
             const unsigned rmask = __ballot_sync(FULL, okq);
-            const int cend = min(32, nL - t);
+            __syncwarp();
+            const int wmax = __shfl_sync(FULL, kq, cend - 1);
+            // ---- phase 1: multipliers of the window's standalone sources, in
+            //      order, with only the updates that land inside the window
             int q = 0;
             while (q < cend) {
-                const int k = __shfl_sync(FULL, kq, q);
-                const int eS = __shfl_sync(FULL, eq, q);
                 const int sS = __shfl_sync(FULL, sq, q);
+                if (sS != 1) break;
+                const int k = __shfl_sync(FULL, kq, q);
                 const int nTS = __shfl_sync(FULL, nTq, q);
-                const int64_t tS = __shfl_sync(FULL, tq0, q);
-                const int64_t pS = __shfl_sync(FULL, pq0, q);
-                if (!((rmask >> q) & 1u))
-                    if (!warp_wait(P.ready + eS, gen, P.status, eS, limit)) return;
-                const int tt = t + q;
+                double dk = __shfl_sync(FULL, dq, q);
+                if (!((rmask >> q) & 1u)) {
+                    if (!warp_wait(P.ready + k, gen, P.status, k, limit, wp)) return;
+                    dk = dinv[k];
+                    if (lane < PF) {
+                        const int64_t tS = P.node_tail_off[P.node_of[k]];
+                        const int64_t pS = P.node_panel_off[P.node_of[k]];
+                        ws->pfc[q][lane] = (lane < nTS) ? P.tcols[tS + lane] : INT_MAX;
+                        ws->pfu[q][lane] = (lane < nTS) ? P.pval[pS + 1 + lane] : 0.0;
+                    }
+                    __syncwarp();
+                }
+                const double l = win[q] * dk;
+                int inwin = 0;
+                if (lane < PF) {
+                    const int c = ws->pfc[q][lane];
+                    if (c <= wmax) {
+                        const int sl = bsearch_sm(wcol, cend, c);
+                        win[sl] -= l * ws->pfu[q][lane];
+                        inwin = 1;
+                    }
+                }
+                int pl = __popc(__ballot_sync(FULL, inwin));
+                if (pl == PF && nTS > PF) {
+                    // rare: more of this source's tail falls inside the window
+                    const int64_t tS = P.node_tail_off[P.node_of[k]];
+                    const double* U1 = P.pval + P.node_panel_off[P.node_of[k]] + 1;
+                    for (int jb = PF; jb < nTS; jb += 32) {
+                        const int j = jb + lane;
+                        const int c = (j < nTS) ? P.tcols[tS + j] : INT_MAX;
+                        const int in = (c <= wmax);
+                        if (in) win[bsearch_sm(wcol, cend, c)] -= l * U1[j];
+                        const unsigned bm = __ballot_sync(FULL, in);
+                        pl += __popc(bm);
+                        if (bm != FULL) break;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) { win[q] = l; ws->plen[q] = pl; }
+                __syncwarp();
+                ++q;
+            }
+            const int qs = q;   // window sources [0, qs) have their multipliers
+            // ---- phase 2: the rest of their tails, no ordering between sources
+            //      needed: L part by atomic add, U part in the panel
+            for (int qq = 0; qq < qs; ++qq) {
+                const int nTS = __shfl_sync(FULL, nTq, qq);
+                const int pl = ws->plen[qq];
+                if (pl >= nTS) continue;
+                const int64_t tS = __shfl_sync(FULL, tq0, qq);
+                const int64_t pS = __shfl_sync(FULL, pq0, qq);
+                apply_tail(P.tcols + tS, P.pval + pS + 1, pl, nTS, win[qq], r, pos, xl, pn, lane);
+                __syncwarp();
+            }
+            // any L slot past this window may have received atomic adds
+            if (t + cend < nL) pending = true;
+            // ---- close the window: multipliers (and untouched values) back to L
+            if (lane < cend) xl[tq] = win[lane];
+            __syncwarp();
+            if (qs == cend) { t += cend; continue; }
+            __threadfence();
+            pending = false;
+            // ---- a source supernode at window slot qs: sup-row update
+            //      l * U_SS = x_S (by position), x[T_S] -= l * U_S,T_S
+            {
+                const int k = __shfl_sync(FULL, kq, qs);
+                const int eS = __shfl_sync(FULL, eq, qs);
+                const int sS = __shfl_sync(FULL, sq, qs);
+                const int nTS = __shfl_sync(FULL, nTq, qs);
+                const int64_t tS = __shfl_sync(FULL, tq0, qs);
+                const int64_t pS = __shfl_sync(FULL, pq0, qs);
+                (void)k;
+                if (!((rmask >> qs) & 1u))
+                    if (!warp_wait(P.ready + eS, gen, P.status, eS, limit, wp)) return;
+                const int tt = t + qs;
+                const int rS = eS - sS + 1;
                 const int wS = sS + nTS;
                 const double* __restrict__ U = P.pval + pS;
                 const int32_t* __restrict__ tcS = P.tcols + tS;
-                if (sS == 1) {
-                    // row-row: l = x_k / u_kk, x[U(k, >k)] -= l * U(k, >k)
-                    const double l = xl[tt] * dinv[k];
-                    for (int j0 = 0; j0 < nTS; j0 += 128) {
-                        int c[4];
-                        double u[4], xv[4];
-                        double* px[4];
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) {
-                            const int j = j0 + m * 32 + lane;
-                            c[m] = (j < nTS) ? tcS[j] : -1;
-                            u[m] = (j < nTS) ? U[1 + j] : 0.0;
-                        }
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) px[m] = (c[m] >= 0) ? slot_ptr(xl, xu, nL, pos[c[m]]) : nullptr;
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) xv[m] = px[m] ? *px[m] : 0.0;
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) if (px[m]) *px[m] = xv[m] - l * u[m];
-                    }
-                    __syncwarp();
-                    if (lane == 0) xl[tt] = l;
-                    __syncwarp();
-                    q += 1;
-                } else {
-                    // sup-row: l * U_SS = x_S (by position), x[T_S] -= l * U_S,T_S
-                    const int rS = eS - sS + 1;
-                    for (int p = lane; p < sS; p += 32) {
-                        const int lab = P.piv[rS + p] - rS;
-                        pb[p] = lab;
-                        lb[p] = xl[tt + lab];
-                    }
-                    __syncwarp();
-                    for (int p = 0; p < sS; ++p) {
-                        const double* Up = U + (int64_t)p * wS;
-                        const double lp = lb[p] * dinv[rS + p];
-                        __syncwarp();
-                        for (int qq = p + 1 + lane; qq < sS; qq += 32) lb[qq] -= lp * Up[pb[qq]];
-                        if (lane == 0) lb[p] = lp;
-                        __syncwarp();
-                    }
-                    for (int j = lane; j < nTS; j += 32) {
-                        const double* Uj = U + sS + j;
-                        const int sl = pos[tcS[j]];
-                        double acc0 = 0.0, acc1 = 0.0;
-                        int p = 0;
-                        for (; p + 1 < sS; p += 2) {
-                            acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
-                            acc1 = fma(lb[p + 1], Uj[(int64_t)(p + 1) * wS], acc1);
-                        }
-                        if (p < sS) acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
-                        *slot_ptr(xl, xu, nL, sl) -= acc0 + acc1;
-                    }
-                    for (int p = lane; p < sS; p += 32) xl[tt + p] = lb[p];
-                    __syncwarp();
-                    q += sS;
+                for (int p = lane; p < sS; p += 32) {
+                    const int lab = P.piv[rS + p] - rS;
+                    pb[p] = lab;
+                    lb[p] = xl[tt + lab];
                 }
+                __syncwarp();
+                for (int p = 0; p < sS; ++p) {
+                    const double* Up = U + (int64_t)p * wS;
+                    const double lp = lb[p] * dinv[rS + p];
+                    __syncwarp();
+                    for (int qq = p + 1 + lane; qq < sS; qq += 32) lb[qq] -= lp * Up[pb[qq]];
+                    if (lane == 0) lb[p] = lp;
+                    __syncwarp();
+                }
+                for (int j = lane; j < nTS; j += 32) {
+                    const double* Uj = U + sS + j;
+                    const int c = tcS[j];
+                    double acc0 = 0.0, acc1 = 0.0;
+                    int p = 0;
+                    for (; p + 1 < sS; p += 2) {
+                        acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
+                        acc1 = fma(lb[p + 1], Uj[(int64_t)(p + 1) * wS], acc1);
+                    }
+                    if (p < sS) acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
+                    if (c < r) {
+                        // later L slot of this row: through pos[], or, for a row
+                        // whose L list fits one window, among the window columns
+                        const int sl = need_pos ? pos[c] : t + bsearch_sm(wcol, cend, c);
+                        atomicAdd(xl + sl, -(acc0 + acc1));
+                    } else {
+                        pn.x[pn.idx(pos, c)] -= acc0 + acc1;
+                    }
+                }
+                for (int p = lane; p < sS; p += 32) xl[tt + p] = lb[p];
+                __threadfence();
+                __syncwarp();
+                t = tt + sS;
+                pending = false;
             }
-            t += q;
         }
+        if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 1] = gtimer();
+        const unsigned long long waited_ext = waited;
         if (s > 1) {
             // ---- earlier rows of the own supernode, each as soon as it is ready
             const double* Ub = P.pval + P.node_panel_off[D];
             for (int k = r; k < i; ++k) {
-                if (!warp_wait(P.ready + k, gen, P.status, k, limit)) return;
+                if (!warp_wait(P.ready + k, gen, P.status, k, limit, wp)) return;
                 const int lab = ld_relaxed(P.piv + k) - r;
                 const double* Uk = Ub + (int64_t)(k - r) * w;
-                const double l = xu[lab] * dinv[k];
+                const double l = pn.x[lab] * dinv[k];
                 for (int c = lane; c < s; c += 32)
-                    if (c != lab && ld_relaxed(P.pinv + r + c) > k) xu[c] -= l * Uk[c];
-                for (int j0 = s; j0 < w; j0 += 128) {
-                    double u[4], xv[4];
+                    if (c != lab && ld_relaxed(P.pinv + r + c) > k) pn.x[c] -= l * Uk[c];
+                for (int jb = 0; jb < nT; jb += 32 * UNR) {
+                    double u[UNR];
+                    int ix[UNR];
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int j = j0 + m * 32 + lane;
-                        u[m] = (j < w) ? Uk[j] : 0.0;
-                        xv[m] = (j < w) ? xu[j] : 0.0;
+                    for (int m = 0; m < UNR; ++m) {
+                        const int j = jb + m * 32 + lane;
+                        u[m] = (j < nT) ? Uk[s + j] : 0.0;
+                        ix[m] = (j < nT) ? pn.tail_idx(tc, j) : -1;
                     }
 #pragma unroll
-                    for (int m = 0; m < 4; ++m) {
-                        const int j = j0 + m * 32 + lane;
-                        if (j < w) xu[j] = xv[m] - l * u[m];
-                    }
+                    for (int m = 0; m < UNR; ++m)
+                        if (ix[m] >= 0) pn.x[ix[m]] -= l * u[m];
                 }
                 __syncwarp();
-                if (lane == 0) xu[lab] = l;
+                if (lane == 0) pn.x[lab] = l;
                 __syncwarp();
             }
             // ---- supernode diagonal pivoting: largest |x| among positions i..e,
@@ -266,7 +449,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
             double best = -1.0;
             int bp = i;
             for (int p = i + lane; p <= e; p += 32) {
-                const double a = fabs(xu[P.piv[p] - r]);
+                const double a = fabs(pn.x[P.piv[p] - r]);
                 if (a > best) { best = a; bp = p; }
             }
             for (int off = 16; off; off >>= 1) {
@@ -282,20 +465,30 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
             }
             __syncwarp();
         }
-        // ---- pivot, small-pivot perturbation, publish
+        // ---- pivot, small-pivot perturbation
         if (lane == 0) {
             const int dl = (s > 1) ? (P.piv[i] - r) : 0;
-            double u = xu[dl];
+            double u = pn.x[dl];
             if (fabs(u) < tau) {
                 u = (u >= 0.0) ? tau : -tau;
-                xu[dl] = u;
+                pn.x[dl] = u;
                 atomicAdd(P.status + ST_NPERT, 1);
             }
             dinv[i] = 1.0 / u;
         }
+        __syncwarp();
+        // ---- write the U part back from shared memory, publish
+        if (pn.mode != 2) {
+            for (int c = lane; c < s; c += 32) xu[c] = pn.x[c];
+            for (int j = lane; j < nT; j += 32) xu[s + j] = pn.x[pn.tail_idx(tc, j)];
+        }
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(P.ready + i, gen);
+        if (P.trace && lane == 0) {
+            P.trace[4 * (int64_t)i + 2] = gtimer();
+            P.trace[4 * (int64_t)i + 3] = (waited_ext << 32) | ((waited - waited_ext) & 0xffffffffull);
+        }
     }
 }
 
@@ -336,53 +529,100 @@ __device__ __forceinline__ bool lane_wait(const int* flag, int gen, int* status,
     return true;
 }
 
+// Warp-wide sum of v[t] * x[c[t]], t < m, with UNR independent gathers in
+// flight per lane; the result is valid in every lane.
+__device__ __forceinline__ double sparse_dot(const double* __restrict__ v, const int32_t* __restrict__ c, int m,
+                                             const double* __restrict__ x, int lane) {
+    double acc[UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) acc[u] = 0.0;
+    for (int t0 = 0; t0 < m; t0 += 32 * UNR) {
+        int cc[UNR];
+        double vv[UNR];
+#pragma unroll
+        for (int u = 0; u < UNR; ++u) {
+            const int t = t0 + u * 32 + lane;
+            cc[u] = (t < m) ? __ldg(c + t) : -1;
+            vv[u] = (t < m) ? __ldg(v + t) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < UNR; ++u)
+            if (cc[u] >= 0) acc[u] = fma(vv[u], x[cc[u]], acc[u]);
+    }
+    double a = 0.0;
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) a += acc[u];
+    for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+    return a;
+}
+
+// Level watermark of the substitution (bulk mode, Sec. 2.2.1 / 2.3): nodes
+// are grouped by dependency level; rows are claimed level by level, and a row
+// of level L only waits until the watermark (levels whose nodes are all
+// complete) reaches L.  The last node to complete a level raises it.
+__device__ __forceinline__ bool wait_level(const int* wm, int need, int& cached, int* status, long long limit) {
+    if (cached >= need) return true;
+    long long it = 0;
+    int v;
+    while ((v = ld_acquire(wm)) < need) {
+        if (++it > limit) {
+            if (atomicCAS(status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0) status[ST_FAILED] = -need;
+            return false;
+        }
+        if ((it & 255) == 0 && ld_relaxed(status + ST_ERR) != 0) return false;
+    }
+    cached = v;
+    return true;
+}
+
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
+// called by lane 0 after the node's results are written and fenced
+__device__ __forceinline__ void node_complete(int* done, const int* count, int L, int* wm) {
+    if (atom_add_acq_rel(done + L, 1) + 1 == count[L]) st_release(wm, L + 1);
+}
+
 // Forward substitution L z = bhat (unit L, by position); z holds bhat on
-// entry.  Every warp claims the next row: it subtracts the row's L list
-// (waiting for each source node), and the warp of the LAST row of a
-// supernode then solves the unit lower block once all rows of the supernode
-// have their external part.  Right-hand sides are columns of z (stride n).
+// entry.  Each warp claims the next row in level order, waits for the lower
+// levels, subtracts the row's L list; the warp of the LAST row of a supernode
+// then solves the unit lower block once all rows of the supernode have their
+// external part.  Right-hand sides are columns of z (stride n).
 __global__ void __launch_bounds__(WARPS * 32)
 fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit) {
     const int lane = threadIdx.x & 31;
     const int n = P.n;
+    int cached = 0;
     for (;;) {
-        int i = 0;
-        if (lane == 0) i = atomicAdd(P.status + ST_CNT_FWD, 1);
-        i = __shfl_sync(FULL, i, 0);
-        if (i >= n) return;
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(P.status + ST_CNT_FWD, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
+        const int i = P.fwd_order[qi];
         const int D = P.node_of[i];
+        const int L = P.fwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+        if (!__all_sync(FULL, wait_level(P.status + ST_WM_F, L, cached, P.status, limit))) return;
         const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
-        int ok = 1;
-        for (int64_t t = l0 + lane; t < l1 && ok; t += 32) {
-            const int S = P.node_of[P.lcols[t]];
-            ok = lane_wait(P.fwd_ready + S, gen, P.status, S, limit);
-        }
-        if (!__all_sync(FULL, ok)) return;
         for (int rr = 0; rr < nrhs; ++rr) {
             double* zr = z + (int64_t)rr * n;
-            double a0 = 0.0, a1 = 0.0;
-            int64_t t = l0 + lane;
-            for (; t + 32 < l1; t += 64) {
-                a0 = fma(P.lval[t], zr[P.lcols[t]], a0);
-                a1 = fma(P.lval[t + 32], zr[P.lcols[t + 32]], a1);
-            }
-            if (t < l1) a0 = fma(P.lval[t], zr[P.lcols[t]], a0);
-            double a = a0 + a1;
-            for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+            const double a = sparse_dot(P.lval + l0, P.lcols + l0, (int)(l1 - l0), zr, lane);
             if (lane == 0) zr[i] -= a;
         }
         __threadfence();
         __syncwarp();
         if (s == 1) {
-            if (lane == 0) st_release(P.fwd_ready + D, gen);
+            if (lane == 0) node_complete(P.fwd_done, P.fwd_count, L, P.status + ST_WM_F);
             continue;
         }
         if (lane == 0) st_release(P.fwd_row + i, gen);
         if (i != e) continue;
         // last row of the supernode: block solve once every row has its external part
-        ok = 1;
+        int ok = 1;
         for (int k = r + lane; k < e && ok; k += 32) ok = lane_wait(P.fwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
         const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
@@ -400,51 +640,40 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) st_release(P.fwd_ready + D, gen);
+        if (lane == 0) node_complete(P.fwd_done, P.fwd_count, L, P.status + ST_WM_F);
     }
 }
 
-// Backward substitution U w = z by position, rows in descending order; the
-// solution is written by label: xh[piv[p]] = w_p.  Every warp claims the next
-// row (from the bottom), subtracts its U tail; the warp of the FIRST row of a
+// Backward substitution U w = z by position; the solution is written by
+// label: xh[piv[p]] = w_p.  Rows are claimed level by level (descending inside
+// a level); each subtracts its U tail, and the warp of the FIRST row of a
 // supernode then back-substitutes the block.  z is overwritten.
 __global__ void __launch_bounds__(WARPS * 32)
 bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
            double* __restrict__ xh, int nrhs, int gen, long long limit) {
     const int lane = threadIdx.x & 31;
     const int n = P.n;
+    int cached = 0;
     for (;;) {
-        int t = 0;
-        if (lane == 0) t = atomicAdd(P.status + ST_CNT_BWD, 1);
-        t = __shfl_sync(FULL, t, 0);
-        if (t >= n) return;
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(P.status + ST_CNT_BWD, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
-        const int i = n - 1 - t;
+        const int i = P.bwd_order[qi];
         const int D = P.node_of[i];
+        const int L = P.bwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int64_t t0 = P.node_tail_off[D];
         const int nT = (int)(P.node_tail_off[D + 1] - t0);
         const int w = s + nT;
         const int32_t* tc = P.tcols + t0;
         const double* Ui = P.pval + P.node_panel_off[D] + (int64_t)(i - r) * w;
-        int ok = 1;
-        for (int j = lane; j < nT && ok; j += 32) {
-            const int S = P.node_of[tc[j]];
-            ok = lane_wait(P.bwd_ready + S, gen, P.status, S, limit);
-        }
-        if (!__all_sync(FULL, ok)) return;
+        if (!__all_sync(FULL, wait_level(P.status + ST_WM_B, L, cached, P.status, limit))) return;
         for (int rr = 0; rr < nrhs; ++rr) {
             double* zr = z + (int64_t)rr * n;
             const double* xr = xh + (int64_t)rr * n;
-            double a0 = 0.0, a1 = 0.0;
-            int j = lane;
-            for (; j + 32 < nT; j += 64) {
-                a0 = fma(Ui[s + j], xr[tc[j]], a0);
-                a1 = fma(Ui[s + j + 32], xr[tc[j + 32]], a1);
-            }
-            if (j < nT) a0 = fma(Ui[s + j], xr[tc[j]], a0);
-            double a = a0 + a1;
-            for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+            const double a = sparse_dot(Ui + s, tc, nT, xr, lane);
             if (lane == 0) {
                 if (s == 1) xh[(int64_t)rr * n + i] = (zr[i] - a) * dinv[i];
                 else zr[i] -= a;
@@ -453,12 +682,12 @@ bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
         __threadfence();
         __syncwarp();
         if (s == 1) {
-            if (lane == 0) st_release(P.bwd_ready + D, gen);
+            if (lane == 0) node_complete(P.bwd_done, P.bwd_count, L, P.status + ST_WM_B);
             continue;
         }
         if (lane == 0) st_release(P.bwd_row + i, gen);
         if (i != r) continue;
-        ok = 1;
+        int ok = 1;
         for (int k = r + 1 + lane; k <= e && ok; k += 32) ok = lane_wait(P.bwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
         const double* Ub = P.pval + P.node_panel_off[D];
@@ -478,7 +707,7 @@ bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) st_release(P.bwd_ready + D, gen);
+        if (lane == 0) node_complete(P.bwd_done, P.bwd_count, L, P.status + ST_WM_B);
     }
 }
 
@@ -538,12 +767,13 @@ static int check(const char* what) {
     return HYLU_OK;
 }
 
-int warps_per_block() { return WARPS; }
+int warps_per_block() { return FWARPS; }
 
 int factor_grid(int device) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel, WARPS * 32, 0);
+    cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FACTOR_SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel, FWARPS * 32, FACTOR_SMEM);
     if (per < 1) per = 1;
     if (per > 4) per = 4;
     return sms * per;
@@ -564,7 +794,7 @@ int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t
     amax_kernel<<<blocks, 256, 0, st>>>(d_vals, P.ah_src, P.ah_scale, nnz_a, P.status);
     count_launch();
     if (e0) cudaEventRecord(e0, st);
-    factor_kernel<<<grid, WARPS * 32, 0, st>>>(P, d_vals, P.dinv, gen, tau_rel, spin_limit);
+    factor_kernel<<<grid, FWARPS * 32, FACTOR_SMEM, st>>>(P, d_vals, P.dinv, gen, tau_rel, spin_limit);
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     return check("factor");
@@ -576,7 +806,9 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
                  cudaEvent_t e0, cudaEvent_t e1) {
     const int64_t tot = (int64_t)P.n * nrhs;
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
-    if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.fwd_done, 0, sizeof(int32_t) * P.n_fwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.bwd_done, 0, sizeof(int32_t) * P.n_bwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     permute_in_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld);
     count_launch();
     const int blocks = grid;

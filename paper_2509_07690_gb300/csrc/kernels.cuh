@@ -6,13 +6,16 @@
 
 namespace hylu {
 
+
 // Status words in device memory (int32):
 //   [0] error code (0 or HYLU_ERR_DEVICE_TIMEOUT), [1] row/node where a wait
 //   expired, [2] perturbed pivots, [3] task counter of the factor kernel,
 //   [4] task counter of the forward solve, [5] of the backward solve,
 //   [6..7] max |Ahat| as the bit pattern of a non-negative double.
-enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_CNT_FWD = 4, ST_CNT_BWD = 5,
-       ST_AMAX = 6, ST_WORDS = 8 };
+//   [8..11] substitution: forward / backward claim counters, forward /
+//   backward level watermarks (levels whose nodes are all complete).
+enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_AMAX = 6, ST_CNT_FWD = 8,
+       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_WORDS = 12 };
 
 struct DevPlan {
     int32_t n, nnodes;
@@ -32,12 +35,23 @@ struct DevPlan {
     int32_t* piv;                  // position -> label
     int32_t* pinv;                 // label -> position
     int32_t* ready;                // per row, factor generation
-    int32_t* fwd_ready;            // per node, solve generation
-    int32_t* bwd_ready;            // per node, solve generation
+    // substitution schedules (rows in level order, node levels, nodes per
+    // level) and per-level completion counters (reset by every solve)
+    const int32_t* fwd_order;
+    const int32_t* bwd_order;
+    const int32_t* fwd_level;
+    const int32_t* bwd_level;
+    const int32_t* fwd_count;
+    const int32_t* bwd_count;
+    int32_t* fwd_done;
+    int32_t* bwd_done;
+    int32_t n_fwd_levels, n_bwd_levels;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
     int32_t* pos;                  // per-warp column -> slot maps, n each
     double* dinv;                  // 1 / u_ii by position (row)
+    const int32_t* row_order;      // claim order of the factor kernel (by level)
+    unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, warp<<8|mode)
     int32_t* status;
 };
 

@@ -89,3 +89,25 @@ def test_random_dense_blocks(seed):
     a[np.arange(n), np.arange(n)] += rng.uniform(1, 2, n)
     r, c = np.nonzero(a)
     run_case(synth.from_coo(n, r, c, a[r, c]))
+
+
+def test_circuit_20k_heavy_rows():
+    """Hub rows land in the heavy queue (panel in the large shared buffer)."""
+    run_case(synth.circuit(20000, seed=77))
+
+
+def test_dense_600_one_heavy_panel():
+    rng = np.random.default_rng(600)
+    n = 600
+    a = rng.standard_normal((n, n)) + 0.1 * np.eye(n)
+    r, c = np.nonzero(a)
+    run_case(synth.from_coo(n, r, c, a[r, c]), static_pivot=0, ordering=2)
+
+
+@pytest.mark.parametrize("k", [48, 64])
+def test_aniso_nd_mixed_panel_modes(k):
+    run_case(synth.aniso9(k), ordering=1)
+
+
+def test_convdiff16_nd():
+    run_case(synth.convdiff3d(16), ordering=1)
