@@ -139,6 +139,16 @@ int hylu_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld,
 int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld,
                          void* stream);
 
+/* Adjoint scatter for differentiating x = A^{-1} b with respect to the
+ * entries of A (a torch.autograd backward, for instance): with lam = A^{-T} g
+ * from hylu_solve_transpose and x the forward solution, writes
+ * d_dvals[q] = -sum_r lam_r[i] * x_r[j] for every entry q = (i, j) of A, in
+ * the CSR order given to hylu_analyze (dL/dA restricted to A's pattern;
+ * dL/db is lam itself).  All DEVICE arrays; lam and x hold nrhs columns of
+ * leading dimension ld >= n.  Asynchronous on `stream`. */
+int hylu_grad_values(hylu_handle* h, const double* d_lam, const double* d_x, double* d_dvals, int nrhs,
+                     int ld, void* stream);
+
 /* Synchronize the handle's last stream and report sizes, flop counts,
  * perturbations, refinement results and any device-side status. */
 int hylu_get_info(hylu_handle* h, hylu_info* info);

@@ -11,13 +11,15 @@ the binding raises if the library cannot be loaded.
 """
 from .capi import (HYLU_OK, HyluError, Info, Options, default_options, hylu_analyze, hylu_destroy,
                    hylu_export_factors, hylu_export_pattern, hylu_export_perm, hylu_factor,
-                   hylu_get_info, hylu_launch_count, hylu_measure_fp64_peak, hylu_refactor, hylu_solve, hylu_solve_transpose,
+                   hylu_get_info, hylu_grad_values, hylu_launch_count, hylu_measure_fp64_peak, hylu_refactor, hylu_solve, hylu_solve_transpose,
                    library_path, load)
 from .solver import Solver, analyze
+from .autograd import HyluSolve, solve
 
 __all__ = [
     "HYLU_OK", "HyluError", "Info", "Options", "default_options", "hylu_analyze", "hylu_destroy",
     "hylu_export_factors", "hylu_export_pattern", "hylu_export_perm", "hylu_factor", "hylu_get_info",
+    "hylu_grad_values",
     "hylu_launch_count", "hylu_measure_fp64_peak", "hylu_refactor", "hylu_solve", "hylu_solve_transpose", "library_path", "load",
-    "Solver", "analyze",
+    "Solver", "analyze", "HyluSolve", "solve",
 ]

@@ -1,0 +1,45 @@
+"""Differentiable sparse solve x = A^{-1} b (torch.autograd.Function).
+
+Forward: numeric factorization of A's values and the solve (library
+kernels).  Backward reuses the stored L and U: one transpose solve
+lam = A^{-T} g gives dL/db = lam, and the library's adjoint scatter gives
+dL/dA_ij = -lam_i x_j on A's pattern (no dense gradient is formed)."""
+from __future__ import annotations
+
+import torch
+
+from . import capi
+from .solver import Solver, _stream
+
+
+class HyluSolve(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, vals: torch.Tensor, b: torch.Tensor, solver: Solver):
+        vals = vals.detach().contiguous()
+        b = b.detach().contiguous()
+        solver.factor(vals)
+        x = solver.solve(b)
+        ctx.solver = solver
+        ctx.save_for_backward(x)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx: torch.Tensor):
+        (x,) = ctx.saved_tensors
+        s = ctx.solver
+        g = gx.contiguous()
+        lam = s.solve(g, transpose=True)
+        dvals = None
+        if ctx.needs_input_grad[0]:
+            nrhs = lam.reshape(-1, s.n).shape[0]
+            dvals = torch.empty(int(s.rowptr[-1]), dtype=torch.float64, device=lam.device)
+            capi.hylu_grad_values(s.h, lam.data_ptr(), x.data_ptr(), dvals.data_ptr(), nrhs, s.n,
+                                  _stream(None))
+        db = lam if ctx.needs_input_grad[1] else None
+        return dvals, db, None
+
+
+def solve(vals: torch.Tensor, b: torch.Tensor, solver: Solver) -> torch.Tensor:
+    """x = A(vals)^{-1} b on the pattern analysed by `solver`, differentiable
+    in vals and b."""
+    return HyluSolve.apply(vals, b, solver)

@@ -83,6 +83,7 @@ def load():
     lib.hylu_measure_fp64_peak.argtypes = [C.POINTER(C.c_double), C.c_void_p]
     lib.hylu_solve_static.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hylu_debug_trace.argtypes = [H, C.c_void_p]
+    lib.hylu_grad_values.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     _lib = lib
     return lib
 
@@ -189,3 +190,7 @@ def hylu_debug_trace(h: int, n: int):
     out = np.empty(4 * n, np.uint64)
     _check(load().hylu_debug_trace(h, _ptr(out)), "hylu_debug_trace")
     return out.reshape(n, 4)
+
+
+def hylu_grad_values(h: int, d_lam: int, d_x: int, d_dvals: int, nrhs: int, ld: int, stream: int = 0) -> int:
+    return _check(load().hylu_grad_values(h, d_lam, d_x, d_dvals, nrhs, ld, stream), "hylu_grad_values")

@@ -29,6 +29,7 @@ struct hylu_handle {
     int cap_rhs = 0;
     size_t cap_elems = 0;
     double *d_z = nullptr, *d_xh = nullptr, *d_r = nullptr, *d_d = nullptr, *d_norms = nullptr;
+    double* d_colsum = nullptr;
     double* h_norms = nullptr;   // pinned
     int32_t* h_status = nullptr; // pinned
     int32_t gen_factor = 0, gen_solve = 0;
@@ -110,6 +111,18 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
         d.n_bwd_levels = (int32_t)P.bwd_count.size();
         TRY(dalloc(h, &d.fwd_done, P.fwd_count.size()));
         TRY(dalloc(h, &d.bwd_done, P.bwd_count.size()));
+        int32_t *uo, *lo, *ul, *ll, *uc, *lcn;
+        TRY(upload(h, &uo, P.ut_order, st));
+        TRY(upload(h, &lo, P.lt_order, st));
+        TRY(upload(h, &ul, P.ut_level, st));
+        TRY(upload(h, &ll, P.lt_level, st));
+        TRY(upload(h, &uc, P.ut_count, st));
+        TRY(upload(h, &lcn, P.lt_count, st));
+        d.ut_order = uo; d.lt_order = lo; d.ut_level = ul; d.lt_level = ll; d.ut_count = uc; d.lt_count = lcn;
+        d.n_ut_levels = (int32_t)P.ut_count.size();
+        d.n_lt_levels = (int32_t)P.lt_count.size();
+        TRY(dalloc(h, &d.ut_done, P.ut_count.size()));
+        TRY(dalloc(h, &d.lt_done, P.lt_count.size()));
     }
     TRY(dalloc(h, &d.fwd_row, P.n));
     TRY(dalloc(h, &d.bwd_row, P.n));
@@ -143,6 +156,7 @@ int ensure_rhs(hylu_handle* h, int nrhs, int ld) {
     TRY(dalloc(h, &h->d_xh, n * nrhs));
     TRY(dalloc(h, &h->d_r, need));
     TRY(dalloc(h, &h->d_d, need));
+    if (!h->d_colsum) TRY(dalloc(h, &h->d_colsum, n));
     h->cap_elems = need;
     TRY(dalloc(h, &h->d_norms, 3 * (size_t)nrhs + 1));
     if (h->h_norms) cudaFreeHost(h->h_norms);
@@ -223,6 +237,40 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
         ++h->gen_solve;
         TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
                                h->d_dc, nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st));
+        TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
+        ++h->refine_iters;
+    }
+}
+
+// Transpose solve A^T x = b with the same refinement rule as do_solve.
+int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, cudaStream_t st) {
+    if (!h->factored) return HYLU_ERR_STATE;
+    if (!d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
+    TRY(ensure_rhs(h, nrhs, ld));
+    TRY(read_status(h, st));
+    hylu::DevPlan& P = h->dp;
+    ++h->gen_solve;
+    TRY(hylu::launch_solve_transpose(P, d_b, d_x, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc, nrhs, ld,
+                                     h->gen_solve, h->opt.spin_limit, h->grid, st));
+    h->refine_iters = 0;
+    h->backward_error = -1.0;
+    h->last = st;
+    if (!(h->nperturb > 0 || h->opt.refine)) return HYLU_OK;
+    double be_prev = INFINITY;
+    for (;;) {
+        TRY(hylu::launch_residual_transpose(h->P.n, h->d_arp, h->d_aci, h->d_avals, d_x, d_b, h->d_r, h->d_colsum,
+                                            h->d_norms, nrhs, ld, st));
+        if (cudaMemcpyAsync(h->h_norms, h->d_norms, sizeof(double) * (3 * nrhs + 1), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            return HYLU_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;
+        double be = max_be(h, nrhs);
+        h->backward_error = be;
+        if (be <= h->opt.refine_tol) return HYLU_OK;
+        if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
+        be_prev = be;
+        ++h->gen_solve;
+        TRY(hylu::launch_solve_transpose(P, h->d_r, h->d_d, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
+                                         nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
         ++h->refine_iters;
     }
@@ -313,9 +361,17 @@ int hylu_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld,
 }
 
 int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream) {
-    (void)d_b; (void)d_x; (void)nrhs; (void)ld; (void)stream;
     if (!h) return HYLU_ERR_ARG;
-    return HYLU_ERR_STATE;
+    return do_solve_transpose(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream));
+}
+
+int hylu_grad_values(hylu_handle* h, const double* d_lam, const double* d_x, double* d_dvals, int nrhs, int ld,
+                     void* stream) {
+    if (!h || !d_lam || !d_x || !d_dvals || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
+    if (!h->uploaded) return HYLU_ERR_STATE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    h->last = st;
+    return hylu::launch_grad_values(h->P.n, h->d_arp, h->d_aci, d_lam, d_x, d_dvals, nrhs, ld, st);
 }
 
 int hylu_get_info(hylu_handle* h, hylu_info* info) {

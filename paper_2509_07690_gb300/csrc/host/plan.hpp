@@ -48,6 +48,9 @@ struct Plan {
     // order (level by level; backward descending inside a level) and the
     // number of nodes of every level
     std::vector<int32_t> fwd_order, bwd_order, fwd_level, bwd_level, fwd_count, bwd_count;
+    // transpose substitution (U^T forward, then L^T backward), push form:
+    // node levels, rows in claim order, rows per level
+    std::vector<int32_t> ut_order, lt_order, ut_level, lt_level, ut_count, lt_count;
     int32_t max_row = 0;                // longest row pattern (L + block + tail)
     int32_t max_sn = 1;
     double analyze_ms = 0.0;

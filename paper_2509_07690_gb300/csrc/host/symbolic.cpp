@@ -212,6 +212,46 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
     };
     schedule(P.fwd_level, false, P.fwd_order, P.fwd_count);
     schedule(P.bwd_level, true, P.bwd_order, P.bwd_count);
+
+    // ---- transpose substitution.  U^T v = h: node D needs every earlier node
+    //      whose U tail reaches a column of D.  L^T u = v: node D needs every
+    //      later node with an L entry in a column of D.  Rows are counted per
+    //      level (each row task pushes its own contributions).
+    P.ut_level.assign(nn2, 0);
+    P.lt_level.assign(nn2, 0);
+    for (int32_t S = 0; S < nn2; ++S)
+        for (int64_t t = P.node_tail_off[S]; t < P.node_tail_off[S + 1]; ++t) {
+            const int32_t D = P.node_of[P.tcols[t]];
+            P.ut_level[D] = std::max(P.ut_level[D], P.ut_level[S] + 1);
+        }
+    for (int32_t J = nn2 - 1; J >= 0; --J)
+        for (int32_t i = P.sn_start[J]; i < P.sn_start[J + 1]; ++i)
+            for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
+                const int32_t D = P.node_of[P.lcols[t]];
+                P.lt_level[D] = std::max(P.lt_level[D], P.lt_level[J] + 1);
+                t += P.sn_start[D + 1] - P.sn_start[D];
+            }
+    auto row_schedule = [&](const std::vector<int32_t>& nl, bool descending, std::vector<int32_t>& order,
+                            std::vector<int32_t>& count) {
+        int32_t ml = 0;
+        for (int32_t D = 0; D < nn2; ++D) ml = std::max(ml, nl[D]);
+        count.assign(ml + 1, 0);
+        std::vector<int64_t> start(ml + 2, 0);
+        for (int32_t D = 0; D < nn2; ++D) {
+            const int32_t rows = P.sn_start[D + 1] - P.sn_start[D];
+            count[nl[D]] += rows;
+            start[nl[D] + 1] += rows;
+        }
+        for (int32_t l = 0; l <= ml; ++l) start[l + 1] += start[l];
+        order.assign(n, 0);
+        if (!descending) {
+            for (int32_t i = 0; i < n; ++i) order[start[nl[P.node_of[i]]]++] = i;
+        } else {
+            for (int32_t i = n - 1; i >= 0; --i) order[start[nl[P.node_of[i]]]++] = i;
+        }
+    };
+    row_schedule(P.ut_level, false, P.ut_order, P.ut_count);   // first row of a node first
+    row_schedule(P.lt_level, true, P.lt_order, P.lt_count);    // last row of a node first
 }
 
 }  // namespace hylu

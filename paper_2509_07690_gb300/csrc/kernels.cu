@@ -711,6 +711,193 @@ bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
     }
 }
 
+// ------------------------------------------------------ transpose solve
+// A^T y = g with Ahat Pi = L U:  h = Pi^T Pc^T Dc g;  U^T v = h;  L^T u = v;
+// y = Dr Pr^T u.  In row storage U^T and L^T are applied by pushing each
+// finished position's contributions to later ones (atomic adds); rows are
+// claimed level by level, and the level watermark guarantees that a position
+// has received every contribution before it is read.
+__global__ void permute_in_t_kernel(int32_t n, const int32_t* __restrict__ piv, const int32_t* __restrict__ colperm,
+                                    const double* __restrict__ dc, const double* __restrict__ g,
+                                    double* __restrict__ hh, int nrhs, int ld) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n * nrhs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(q / n), p = (int)(q % n);
+        const int o = colperm[piv[p]];
+        hh[q] = dc[o] * g[(int64_t)rr * ld + o];
+    }
+}
+
+__global__ void permute_out_t_kernel(int32_t n, const int32_t* __restrict__ rowperm, const double* __restrict__ dr,
+                                     const double* __restrict__ u, double* __restrict__ y, int nrhs, int ld) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n * nrhs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(q / n), i = (int)(q % n);
+        const int o = rowperm[i];
+        y[(int64_t)rr * ld + o] = dr[o] * u[q];
+    }
+}
+
+// U^T v = h by position (h is overwritten by v)
+__global__ void __launch_bounds__(WARPS * 32)
+ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit) {
+    const int lane = threadIdx.x & 31;
+    const int n = P.n;
+    int cached = 0;
+    for (;;) {
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(P.status + ST_CNT_FWD, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= n) return;
+        if (ld_relaxed(P.status + ST_ERR) != 0) return;
+        const int i = P.ut_order[qi];
+        const int D = P.node_of[i];
+        const int L = P.ut_level[D];
+        const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+        const int64_t t0 = P.node_tail_off[D];
+        const int nT = (int)(P.node_tail_off[D + 1] - t0);
+        const int w = s + nT;
+        const double* Ub = P.pval + P.node_panel_off[D];
+        if (!__all_sync(FULL, wait_level(P.status + ST_WM_F, L, cached, P.status, limit))) return;
+        if (s == 1) {
+            if (lane == 0) for (int rr = 0; rr < nrhs; ++rr) h[(int64_t)rr * n + i] *= P.dinv[i];
+            __syncwarp();
+        } else if (i == r) {
+            // the block: v_p = (h_p - sum_{k in [r,p)} U(k, pos p) v_k) / u_pp
+            for (int rr = 0; rr < nrhs; ++rr) {
+                double* hr = h + (int64_t)rr * n;
+                for (int p = r; p <= e; ++p) {
+                    const int lp = P.piv[p] - r;
+                    double a = 0.0;
+                    for (int k = r + lane; k < p; k += 32) a = fma(Ub[(int64_t)(k - r) * w + lp], hr[k], a);
+                    for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+                    if (lane == 0) hr[p] = (hr[p] - a) * P.dinv[p];
+                    __syncwarp();
+                }
+            }
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release(P.fwd_row + r, gen);
+        } else {
+            if (!__all_sync(FULL, lane_wait(P.fwd_row + r, gen, P.status, r, limit))) return;
+        }
+        // push row i's U tail: h[pos of label c] -= U(i, c) v_i
+        const double* Ui = Ub + (int64_t)(i - r) * w + s;
+        const int32_t* tc = P.tcols + t0;
+        for (int rr = 0; rr < nrhs; ++rr) {
+            double* hr = h + (int64_t)rr * n;
+            const double vi = hr[i];
+            if (vi != 0.0)
+                for (int j = lane; j < nT; j += 32) atomicAdd(hr + P.pinv[tc[j]], -Ui[j] * vi);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) node_complete(P.ut_done, P.ut_count, L, P.status + ST_WM_F);
+    }
+}
+
+// L^T u = v by position (h holds v on entry, u on exit)
+__global__ void __launch_bounds__(WARPS * 32)
+lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit) {
+    const int lane = threadIdx.x & 31;
+    const int n = P.n;
+    int cached = 0;
+    for (;;) {
+        int qi = 0;
+        if (lane == 0) qi = atomicAdd(P.status + ST_CNT_BWD, 1);
+        qi = __shfl_sync(FULL, qi, 0);
+        if (qi >= n) return;
+        if (ld_relaxed(P.status + ST_ERR) != 0) return;
+        const int i = P.lt_order[qi];
+        const int D = P.node_of[i];
+        const int L = P.lt_level[D];
+        const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+        if (!__all_sync(FULL, wait_level(P.status + ST_WM_B, L, cached, P.status, limit))) return;
+        if (s > 1) {
+            if (i == e) {
+                // the block: u_k = v_k - sum_{j in (k, e]} L(j, pos k) u_j
+                const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+                const double* Ub = P.pval + P.node_panel_off[D];
+                for (int rr = 0; rr < nrhs; ++rr) {
+                    double* hr = h + (int64_t)rr * n;
+                    for (int k = e - 1; k >= r; --k) {
+                        const int lk = P.piv[k] - r;
+                        double a = 0.0;
+                        for (int j = k + 1 + lane; j <= e; j += 32) a = fma(Ub[(int64_t)(j - r) * w + lk], hr[j], a);
+                        for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+                        if (lane == 0) hr[k] -= a;
+                        __syncwarp();
+                    }
+                }
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release(P.bwd_row + e, gen);
+            } else {
+                if (!__all_sync(FULL, lane_wait(P.bwd_row + e, gen, P.status, e, limit))) return;
+            }
+        }
+        // push row i's L list: h[c] -= L(i, c) u_i (c by position)
+        const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
+        for (int rr = 0; rr < nrhs; ++rr) {
+            double* hr = h + (int64_t)rr * n;
+            const double ui = hr[i];
+            if (ui != 0.0)
+                for (int64_t t = l0 + lane; t < l1; t += 32) atomicAdd(hr + P.lcols[t], -P.lval[t] * ui);
+        }
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) node_complete(P.lt_done, P.lt_count, L, P.status + ST_WM_B);
+    }
+}
+
+// r = g - A^T y (atomic scatter over the rows of A), column abs sums of A
+__global__ void residual_t_kernel(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                  const double* __restrict__ v, const double* __restrict__ y,
+                                  double* __restrict__ res, double* __restrict__ colsum, int nrhs, int ld) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = wg; i < n; i += nw) {
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const int j = ci[q];
+            for (int rr = 0; rr < nrhs; ++rr) atomicAdd(res + (int64_t)rr * ld + j, -v[q] * y[(int64_t)rr * ld + i]);
+            atomicAdd(colsum + j, fabs(v[q]));
+        }
+    }
+}
+
+// norms[rr] = {||r||inf, ||y||inf, ||g||inf} as bit patterns, norms[3 nrhs] = max column sum
+__global__ void norms_t_kernel(int32_t n, const double* __restrict__ res, const double* __restrict__ y,
+                               const double* __restrict__ g, const double* __restrict__ colsum,
+                               unsigned long long* norms, int nrhs, int ld) {
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n * nrhs;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int rr = (int)(q / n), i = (int)(q % n);
+        const int64_t o = (int64_t)rr * ld + i;
+        atomicMax(norms + 3 * rr + 0, (unsigned long long)__double_as_longlong(fabs(res[o])));
+        atomicMax(norms + 3 * rr + 1, (unsigned long long)__double_as_longlong(fabs(y[o])));
+        atomicMax(norms + 3 * rr + 2, (unsigned long long)__double_as_longlong(fabs(g[o])));
+        if (rr == 0) atomicMax(norms + 3 * nrhs, (unsigned long long)__double_as_longlong(colsum[i]));
+    }
+}
+
+// Adjoint of x = A^{-1} b for the entries of A: dL/dA_ij = -sum_r lam_r[i] x_r[j]
+__global__ void grad_values_kernel(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                                   const double* __restrict__ lam, const double* __restrict__ x,
+                                   double* __restrict__ dv, int nrhs, int ld) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wg = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t i = wg; i < n; i += nw) {
+        for (int64_t q = rp[i] + lane; q < rp[i + 1]; q += 32) {
+            const int j = ci[q];
+            double a = 0.0;
+            for (int rr = 0; rr < nrhs; ++rr) a = fma(lam[(int64_t)rr * ld + i], x[(int64_t)rr * ld + j], a);
+            dv[q] = -a;
+        }
+    }
+}
+
 // r = b - A x on the original A; norms[rr] = {||r||inf, ||x||inf, ||b||inf}
 // as bit patterns (non-negative doubles), norms[3*nrhs] = ||A||inf.
 __global__ void residual_kernel(int32_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
@@ -821,6 +1008,50 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     permute_out_kernel<<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);
     count_launch();
     return check("solve");
+}
+
+int launch_solve_transpose(const DevPlan& P, const double* d_b, double* d_x, double* d_h,
+                           const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
+                           int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st) {
+    const int64_t tot = (int64_t)P.n * nrhs;
+    const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
+    if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.ut_done, 0, sizeof(int32_t) * P.n_ut_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.lt_done, 0, sizeof(int32_t) * P.n_lt_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    permute_in_t_kernel<<<eb, 256, 0, st>>>(P.n, P.piv, colperm, dc, d_b, d_h, nrhs, ld);
+    count_launch();
+    ut_kernel<<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    count_launch();
+    lt_kernel<<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    count_launch();
+    permute_out_t_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_h, d_x, nrhs, ld);
+    count_launch();
+    return check("solve_transpose");
+}
+
+int launch_residual_transpose(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* y,
+                              const double* g, double* r, double* colsum, double* norms, int nrhs, int ld,
+                              cudaStream_t st) {
+    for (int rr = 0; rr < nrhs; ++rr)
+        if (cudaMemcpyAsync(r + (int64_t)rr * ld, g + (int64_t)rr * ld, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+            return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(colsum, 0, sizeof(double) * n, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(norms, 0, sizeof(double) * (3 * nrhs + 1), st) != cudaSuccess) return HYLU_ERR_CUDA;
+    const int blocks = (int)std::min<int64_t>(4096, ((int64_t)n * 32 + 255) / 256 + 1);
+    residual_t_kernel<<<blocks, 256, 0, st>>>(n, rp, ci, v, y, r, colsum, nrhs, ld);
+    count_launch();
+    const int eb = (int)std::min<int64_t>(4096, ((int64_t)n * nrhs + 255) / 256 + 1);
+    norms_t_kernel<<<eb, 256, 0, st>>>(n, r, y, g, colsum, reinterpret_cast<unsigned long long*>(norms), nrhs, ld);
+    count_launch();
+    return check("residual_transpose");
+}
+
+int launch_grad_values(int32_t n, const int64_t* rp, const int32_t* ci, const double* lam, const double* x,
+                       double* dvals, int nrhs, int ld, cudaStream_t st) {
+    const int blocks = (int)std::min<int64_t>(4096, ((int64_t)n * 32 + 255) / 256 + 1);
+    grad_values_kernel<<<blocks, 256, 0, st>>>(n, rp, ci, lam, x, dvals, nrhs, ld);
+    count_launch();
+    return check("grad_values");
 }
 
 int launch_residual(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x,

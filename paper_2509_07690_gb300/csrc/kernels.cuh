@@ -46,6 +46,15 @@ struct DevPlan {
     int32_t* fwd_done;
     int32_t* bwd_done;
     int32_t n_fwd_levels, n_bwd_levels;
+    const int32_t* ut_order;
+    const int32_t* lt_order;
+    const int32_t* ut_level;
+    const int32_t* lt_level;
+    const int32_t* ut_count;       // rows per level
+    const int32_t* lt_count;
+    int32_t* ut_done;
+    int32_t* lt_done;
+    int32_t n_ut_levels, n_lt_levels;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
     int32_t* pos;                  // per-warp column -> slot maps, n each
@@ -62,6 +71,14 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
                  const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
                  int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st,
                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
+int launch_solve_transpose(const DevPlan& P, const double* d_b, double* d_x, double* d_h,
+                           const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
+                           int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st);
+int launch_residual_transpose(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* y,
+                              const double* g, double* r, double* colsum, double* norms, int nrhs, int ld,
+                              cudaStream_t st);
+int launch_grad_values(int32_t n, const int64_t* rp, const int32_t* ci, const double* lam, const double* x,
+                       double* dvals, int nrhs, int ld, cudaStream_t st);
 int launch_residual(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x,
                     const double* b, double* r, double* norms, int nrhs, int ld, cudaStream_t st);
 int launch_axpy(int32_t n, double* x, const double* d, int nrhs, int ld, cudaStream_t st);

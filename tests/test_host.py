@@ -1,0 +1,188 @@
+"""Host-side checks that need no GPU: the C ABI library loads and exports
+every entry point declared in include/hylu.h; preprocessing (Sec. 2.1) is
+pinned by brute force and by the properties the paper states; the symbolic
+pattern, supernode partition and flop count of the library equal the
+oracle's bit for bit; malformed input returns the documented error codes."""
+import itertools
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2509_07690_gb300 import capi, synth
+from paper_2509_07690_gb300.solver import Solver
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_library_exports_every_declared_symbol():
+    header = open(os.path.join(ROOT, "include", "hylu.h")).read()
+    declared = set(re.findall(r"^\s*(?:int|int64_t)\s+(hylu_\w+)\s*\(", header, re.M))
+    assert {"hylu_analyze", "hylu_factor", "hylu_refactor", "hylu_solve",
+            "hylu_solve_transpose"} <= declared
+    lib = capi.load()
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+def _dense_csr(a):
+    r, c = np.nonzero(a)
+    return synth.from_coo(a.shape[0], r, c, a[r, c])
+
+
+# ------------------------------------------------------------------ MWM
+def _scaled(s, A):
+    rp, cp, dr, dc, _ = s.export_perm()
+    a = A.todense()
+    return (dr[:, None] * a * dc[None, :])[np.ix_(rp, cp)], rp, cp
+
+
+@pytest.mark.parametrize("seed", range(25))
+def test_matching_maximizes_product_brute_force(seed):
+    """Sec. 2.1: the static pivot maximizes the product of the matched
+    magnitudes; brute force over all n! permutations for n <= 7."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(2, 8))
+    a = np.where(rng.random((n, n)) < 0.6, rng.uniform(-3, 3, (n, n)), 0.0)
+    a[np.arange(n), rng.permutation(n)] = rng.uniform(0.1, 2.0, n)   # a perfect matching exists
+    A = _dense_csr(a)
+    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=2)
+    rp, cp, _, _, _ = s.export_perm()
+    got = np.prod([abs(a[rp[i], cp[i]]) for i in range(n)])
+    best = max(np.prod([abs(a[i, p[i]]) for i in range(n)]) for p in itertools.permutations(range(n)))
+    assert got == pytest.approx(best, rel=1e-12)
+    s.close()
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_scaling_unit_diagonal_bounded_offdiagonal(seed):
+    """Sec. 2.1: after static pivoting and scaling the diagonal is +-1 and
+    every other entry lies in [-1, 1]."""
+    rng = np.random.default_rng(50 + seed)
+    n = int(rng.integers(20, 120))
+    a = np.where(rng.random((n, n)) < 0.1, rng.lognormal(0, 2, (n, n)) * rng.choice([-1, 1], (n, n)), 0.0)
+    a[np.arange(n), rng.permutation(n)] = rng.lognormal(0, 2, n)
+    A = _dense_csr(a)
+    s = Solver(A.n, A.rowptr, A.col, A.val)
+    ah, _, _ = _scaled(s, A)
+    np.testing.assert_allclose(np.abs(np.diag(ah)), 1.0, rtol=1e-12)
+    assert np.abs(ah).max() <= 1.0 + 1e-12
+    s.close()
+
+
+def test_matching_recovers_row_permutation():
+    rng = np.random.default_rng(3)
+    n = 300
+    A = synth.grid5(10)
+    a = A.todense()
+    perm = rng.permutation(a.shape[0])
+    B = _dense_csr(a[perm])
+    s = Solver(B.n, B.rowptr, B.col, B.val, ordering=2)
+    rp, cp, _, _, _ = s.export_perm()
+    assert np.array_equal(perm[rp], cp)       # row of A that lands on column k is column k's row
+    s.close()
+
+
+def test_diagonally_dominant_gives_identity_matching():
+    for A in (synth.grid5(12), synth.circuit(2000, seed=3)):
+        s = Solver(A.n, A.rowptr, A.col, A.val)
+        rp, cp, _, _, _ = s.export_perm()
+        assert np.array_equal(rp, cp)
+        s.close()
+
+
+# ------------------------------------------------------------ orderings
+@pytest.mark.parametrize("ordering", [0, 1])
+def test_orderings_are_permutations_and_reduce_fill(ordering):
+    for A in (synth.grid5(32), synth.aniso9(24), synth.convdiff3d(10)):
+        s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering)
+        rp, cp, _, _, _ = s.export_perm()
+        assert np.array_equal(np.sort(cp), np.arange(A.n))
+        nat = Solver(A.n, A.rowptr, A.col, A.val, ordering=2)
+        assert s.info.nnz_lu < nat.info.nnz_lu
+        s.close()
+        nat.close()
+
+
+def test_nested_dissection_fill_grows_slowly_on_grids():
+    """2D grids: nested dissection fill grows like n log n, not n^1.5."""
+    fills = []
+    for k in (32, 64, 128):
+        A = synth.grid5(k)
+        s = Solver(A.n, A.rowptr, A.col, A.val, ordering=1)
+        fills.append(s.info.nnz_lu / (A.n * np.log2(A.n)))
+        s.close()
+    assert fills[-1] < 2.0 * fills[0]
+
+
+# --------------------------------------------- pattern parity on the host
+CASES = [
+    ("grid5_16", lambda: synth.grid5(16), {}),
+    ("grid5_64", lambda: synth.grid5(64), {}),
+    ("circuit_3000", lambda: synth.circuit(3000, seed=12), {}),
+    ("convdiff_10_nd", lambda: synth.convdiff3d(10), {"ordering": 1}),
+    ("aniso_32_nd", lambda: synth.aniso9(32), {"ordering": 1}),
+    ("convdiff_8_sn7", lambda: synth.convdiff3d(8), {"ordering": 1, "sn_max": 7}),
+]
+
+
+@pytest.mark.parametrize("name,make,opts", CASES, ids=[c[0] for c in CASES])
+def test_pattern_partition_flops_bit_exact(name, make, opts):
+    A = make()
+    s = Solver(A.n, A.rowptr, A.col, A.val, **opts)
+    rp, cp, dr, dc, sn = s.export_perm()
+    o = oracle.Oracle(A.n, A.rowptr, A.col, A.val, rp, cp, dr, dc, sn_max=opts.get("sn_max", 256), numeric=False)
+    prp, pci = s.export_pattern()
+    assert np.array_equal(o.sn_start, sn)
+    assert np.array_equal(o.padded.rowptr, prp) and np.array_equal(o.padded.col, pci)
+    assert s.info.nnz_lu == len(o.unpadded.col)
+    assert s.info.flops == o.flops[0] and s.info.flops_padded == o.flops[1]
+    s.close()
+
+
+@pytest.mark.parametrize("seed", range(30))
+def test_pattern_parity_random_unsymmetric(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(5, 90))
+    a = np.where(rng.random((n, n)) < rng.uniform(0.02, 0.15), rng.uniform(-1, 1, (n, n)), 0.0)
+    a[np.arange(n), np.arange(n)] += rng.uniform(1, 2, n)
+    A = _dense_csr(a)
+    user = rng.permutation(n).astype(np.int32)
+    s = Solver(A.n, A.rowptr, A.col, A.val, user, ordering=3, static_pivot=0, sn_max=int(rng.integers(1, 9)))
+    rp, cp, dr, dc, sn = s.export_perm()
+    assert np.array_equal(cp, user) and np.array_equal(rp, user)
+    o = oracle.Oracle(A.n, A.rowptr, A.col, A.val, user, user, None, None, sn_max=s.opt.sn_max, numeric=False)
+    prp, pci = s.export_pattern()
+    assert np.array_equal(o.sn_start, sn)
+    assert np.array_equal(o.padded.col, pci) and np.array_equal(o.padded.rowptr, prp)
+    assert s.info.flops == o.flops[0]
+    s.close()
+
+
+# ------------------------------------------------------------- errors
+def test_error_codes():
+    rp = np.array([0, 2, 3], np.int64)
+    with pytest.raises(capi.HyluError) as e:          # unsorted columns
+        capi.hylu_analyze(2, rp, np.array([1, 0, 1], np.int32), np.ones(3))
+    assert e.value.code == -2
+    with pytest.raises(capi.HyluError) as e:          # out of range
+        capi.hylu_analyze(2, rp, np.array([0, 5, 1], np.int32), np.ones(3))
+    assert e.value.code == -2
+    with pytest.raises(capi.HyluError) as e:          # structurally singular: empty column 1
+        capi.hylu_analyze(2, np.array([0, 1, 2], np.int64), np.array([0, 0], np.int32), np.ones(2))
+    assert e.value.code == -3
+    with pytest.raises(capi.HyluError) as e:          # bad user permutation
+        capi.hylu_analyze(2, np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32), np.ones(2),
+                          np.array([0, 0], np.int32), capi.default_options(ordering=3))
+    assert e.value.code == -1
+    A = synth.grid5(4)
+    h = capi.hylu_analyze(A.n, A.rowptr, A.col, A.val)
+    with pytest.raises(capi.HyluError) as e:          # refactor before factor
+        capi.hylu_refactor(h, 0, 0)
+    assert e.value.code in (-1, -7)
+    with pytest.raises(capi.HyluError) as e:          # solve before factor
+        capi.hylu_solve(h, 1, 1, 1, A.n, 0)
+    assert e.value.code == -7
+    capi.hylu_destroy(h)
