@@ -35,6 +35,12 @@ VALUE_SETS = 16
 METRIC = "numeric LU ms/factor (circuit-like n=100000, refactor of 16 value sets, backward error <= 1e-12)"
 
 
+def metric_name() -> str:
+    if WORKLOAD == "circuit_100k":
+        return METRIC
+    return f"numeric LU ms/factor ({WORKLOAD}, backward error <= 1e-12)"
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -43,7 +49,15 @@ def parse():
     ap.add_argument("--impl", default="hylu", choices=["hylu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--workload", default="circuit_100k",
+                    choices=["circuit_100k", "circuit", "grid5_64", "aniso9_512", "convdiff3d_64"],
+                    help="circuit_100k is the headline configuration; 'circuit' with --n is the same "
+                         "generator at another size (profiling cases)")
+    ap.add_argument("--n", type=int, default=30000, help="size for --workload circuit")
+    args = ap.parse_args()
+    global WORKLOAD
+    WORKLOAD = args.workload
+    return args
 
 
 def dist_setup(args):
@@ -89,13 +103,26 @@ def allsum(ws, v: float) -> float:
 
 
 # ----------------------------------------------------------------- inputs
-def make_inputs():
+def make_inputs(n_circuit: int = 30000):
+    """The workload matrix, VALUE_SETS value sets on its pattern (fresh values
+    for the circuit generator, the matrix itself otherwise) and b = A x_true."""
     from paper_2509_07690_gb300 import synth
-    A = synth.workload(WORKLOAD)
-    idx = synth.WORKLOADS[WORKLOAD]["index"]
-    sets = [synth.circuit_value_set(A, 1002 + idx + j) for j in range(VALUE_SETS)]
+    if WORKLOAD == "circuit":
+        idx = 1
+        A = synth.circuit(n_circuit, seed=1000 + idx)
+    else:
+        idx = synth.WORKLOADS[WORKLOAD]["index"]
+        A = synth.workload(WORKLOAD)
+    if WORKLOAD.startswith("circuit"):
+        sets = [synth.circuit_value_set(A, 1002 + idx + j) for j in range(VALUE_SETS)]
+    else:
+        sets = [A] * VALUE_SETS
     xt, b = synth.rhs(A, 1001 + idx)
     return A, sets, b[0]
+
+
+def ordering_for(workload: str) -> int:
+    return 1 if workload in ("aniso9_512", "convdiff3d_64") else 0
 
 
 def backward_error(A, vals, x, b) -> float:
@@ -247,8 +274,8 @@ def run_hylu(args, ws, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    A, sets, b = make_inputs()
-    s = Solver(A.n, A.rowptr, A.col, A.val, timing=1)
+    A, sets, b = make_inputs(args.n)
+    s = Solver(A.n, A.rowptr, A.col, A.val, timing=1, ordering=ordering_for(WORKLOAD))
     info = s.info
     flops = info.flops
     d_sets = [torch.from_numpy(v.val).to(dev) for v in sets]
@@ -318,7 +345,7 @@ def run_hylu(args, ws, rank, local):
     be_e2e = backward_error(A, sets[(args.steps - 1) % VALUE_SETS].val, h_x.numpy(), b)
     # ---------------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and WORKLOAD == "circuit_100k":
         n_s = oracle_size(args.cpu_seconds / 2)
         dt, fl = oracle_once(n_s)
         cpu = {"value": dt * 1e3 * flops / fl, "unit": "ms", "cores": 1, "kind": "oracle",
@@ -326,10 +353,11 @@ def run_hylu(args, ws, rank, local):
                          f"extrapolated to the n={A.n} flop count; host has {os.cpu_count()} cores"}
     if rank == 0:
         out = {
-            "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+            "metric": metric_name(), "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "ordering": "AMD",
+            "config": {"workload": WORKLOAD if WORKLOAD != "circuit" else f"circuit_{A.n}", "n": A.n,
+                       "nnz": A.nnz, "ordering": "ND" if ordering_for(WORKLOAD) else "AMD",
                        "value_sets": VALUE_SETS, "flops": flops, "nnz_lu": info.nnz_lu,
                        "nnz_store": info.nnz_store, "supernodes": info.nsupernodes,
                        "rows_in_supernodes": info.rows_in_supernodes,
