@@ -149,6 +149,40 @@ int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrh
 int hylu_grad_values(hylu_handle* h, const double* d_lam, const double* d_x, double* d_dvals, int nrhs,
                      int ld, void* stream);
 
+/* ---- batched form (many value sets of one pattern, many patterns) ----
+ * Analyse k independent systems (system s: CSR n[s], rowptr[s], col[s],
+ * vals[s] host arrays, same conventions as hylu_analyze) to be factored with
+ * nsets value sets each.  The handle holds one block-diagonal plan of the
+ * k * nsets instances; instance q = v * k + s (value set v of system s).
+ * hylu_factor / hylu_refactor then take d_vals = all instances' values
+ * concatenated in instance order, and hylu_solve right-hand sides of length
+ * N = sum over instances of n[s] (instance q at rows hylu_batch_layout's
+ * row_base[q]): every instance is factored in ONE persistent launch and
+ * solved in one launch sequence.  The k systems are analysed on host threads. */
+int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr, const int32_t* const* col,
+                       const double* const* vals, int32_t nsets, const hylu_options* opt, hylu_handle** out);
+
+/* Layout of a batch handle (HOST arrays, any may be NULL): row_base int32[k*nsets]
+ * first row of each instance in the combined system, val_base int64[k*nsets]
+ * offset of each instance's values in d_vals.  *total_n gets N. */
+int hylu_batch_layout(hylu_handle* h, int32_t* row_base, int64_t* val_base, int32_t* total_n);
+
+/* Capture refactorization of d_vals followed by the substitution of d_b into
+ * d_x (nrhs columns, leading dimension ld; no refinement inside the graph) as
+ * a CUDA graph on `stream`, replayed by hylu_graph_launch.  Requires a
+ * previous hylu_factor and hylu_solve with at least nrhs right-hand sides (so
+ * that nothing is allocated during capture), and a created stream (the legacy
+ * default stream cannot be captured: HYLU_ERR_ARG).  The pointers are baked
+ * into the graph. */
+int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
+                       void* stream);
+int hylu_graph_launch(hylu_handle* h, void* stream);
+
+/* Autotune the persistent grid (thread blocks per SM, 1..4) of the factor
+ * and substitution kernels on d_vals (refactorizes; synchronizes).  The best
+ * setting stays in the handle; *blocks_per_sm receives it. */
+int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream);
+
 /* Synchronize the handle's last stream and report sizes, flop counts,
  * perturbations, refinement results and any device-side status. */
 int hylu_get_info(hylu_handle* h, hylu_info* info);

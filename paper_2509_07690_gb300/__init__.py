@@ -13,7 +13,7 @@ from .capi import (HYLU_OK, HyluError, Info, Options, default_options, hylu_anal
                    hylu_export_factors, hylu_export_pattern, hylu_export_perm, hylu_factor,
                    hylu_get_info, hylu_grad_values, hylu_launch_count, hylu_measure_fp64_peak, hylu_refactor, hylu_solve, hylu_solve_transpose,
                    library_path, load)
-from .solver import Solver, analyze
+from .solver import BatchSolver, Solver, analyze
 from .autograd import HyluSolve, solve
 
 __all__ = [
@@ -21,5 +21,5 @@ __all__ = [
     "hylu_export_factors", "hylu_export_pattern", "hylu_export_perm", "hylu_factor", "hylu_get_info",
     "hylu_grad_values",
     "hylu_launch_count", "hylu_measure_fp64_peak", "hylu_refactor", "hylu_solve", "hylu_solve_transpose", "library_path", "load",
-    "Solver", "analyze", "HyluSolve", "solve",
+    "Solver", "BatchSolver", "analyze", "HyluSolve", "solve",
 ]

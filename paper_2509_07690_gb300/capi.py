@@ -84,6 +84,12 @@ def load():
     lib.hylu_solve_static.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hylu_debug_trace.argtypes = [H, C.c_void_p]
     lib.hylu_grad_values.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.hylu_analyze_batch.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
+                                       C.POINTER(Options), C.POINTER(H)]
+    lib.hylu_batch_layout.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.hylu_graph_capture.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.hylu_graph_launch.argtypes = [H, C.c_void_p]
+    lib.hylu_tune.argtypes = [H, C.c_void_p, C.POINTER(C.c_int), C.c_void_p]
     _lib = lib
     return lib
 
@@ -194,3 +200,49 @@ def hylu_debug_trace(h: int, n: int):
 
 def hylu_grad_values(h: int, d_lam: int, d_x: int, d_dvals: int, nrhs: int, ld: int, stream: int = 0) -> int:
     return _check(load().hylu_grad_values(h, d_lam, d_x, d_dvals, nrhs, ld, stream), "hylu_grad_values")
+
+
+def hylu_analyze_batch(systems, nsets: int, opt: Options | None = None) -> int:
+    """systems: list of (n, rowptr, col, vals) host arrays."""
+    k = len(systems)
+    ns = np.array([int(s[0]) for s in systems], np.int32)
+    keep = []
+    rps = (C.c_void_p * k)()
+    cis = (C.c_void_p * k)()
+    vls = (C.c_void_p * k)()
+    for q, (n, rp, ci, v) in enumerate(systems):
+        rp = np.ascontiguousarray(rp, np.int64)
+        ci = np.ascontiguousarray(ci, np.int32)
+        v = np.ascontiguousarray(v, np.float64)
+        keep += [rp, ci, v]
+        rps[q] = rp.ctypes.data
+        cis[q] = ci.ctypes.data
+        vls[q] = v.ctypes.data
+    h = C.c_void_p()
+    rc = load().hylu_analyze_batch(k, ns.ctypes.data_as(C.c_void_p), C.cast(rps, C.c_void_p),
+                                   C.cast(cis, C.c_void_p), C.cast(vls, C.c_void_p), int(nsets),
+                                   C.byref(opt) if opt is not None else None, C.byref(h))
+    _check(rc, "hylu_analyze_batch")
+    return h.value
+
+
+def hylu_batch_layout(h: int, ninst: int):
+    rb = np.empty(ninst, np.int32)
+    vb = np.empty(ninst, np.int64)
+    tot = C.c_int32()
+    _check(load().hylu_batch_layout(h, _ptr(rb), _ptr(vb), C.byref(tot)), "hylu_batch_layout")
+    return rb, vb, tot.value
+
+
+def hylu_graph_capture(h: int, d_vals: int, d_b: int, d_x: int, nrhs: int, ld: int, stream: int = 0) -> int:
+    return _check(load().hylu_graph_capture(h, d_vals, d_b, d_x, nrhs, ld, stream), "hylu_graph_capture")
+
+
+def hylu_graph_launch(h: int, stream: int = 0) -> int:
+    return _check(load().hylu_graph_launch(h, stream), "hylu_graph_launch")
+
+
+def hylu_tune(h: int, d_vals: int, stream: int = 0) -> int:
+    b = C.c_int()
+    _check(load().hylu_tune(h, d_vals, C.byref(b), stream), "hylu_tune")
+    return b.value

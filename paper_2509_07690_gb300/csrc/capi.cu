@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <thread>
 #include <vector>
 
 #include "../../include/hylu.h"
@@ -38,6 +39,12 @@ struct hylu_handle {
     int32_t nperturb = 0, refine_iters = 0, device_status = 0, failed_node = -1;
     double backward_error = -1.0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    // batched form
+    bool batch = false;
+    hylu::BatchLayout layout;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    int grid_max = 0;
     bool timed_factor = false, timed_solve = false;
 };
 
@@ -129,7 +136,19 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     TRY(dalloc(h, &d.dinv, P.n));
     TRY(dalloc(h, &d.status, hylu::ST_WORDS));
     h->grid = hylu::factor_grid(h->device);
-    TRY(dalloc(h, &d.pos, (size_t)h->grid * hylu::warps_per_block() * (size_t)P.n));
+    {
+        int sms = 0;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        h->grid_max = std::max(h->grid, sms * 4);
+    }
+    d.pos_n = h->batch ? h->layout.pos_n : P.n;
+    d.node_base = nullptr;
+    if (h->batch) {
+        int32_t* nb;
+        TRY(upload(h, &nb, h->layout.node_base, st));
+        d.node_base = nb;
+    }
+    TRY(dalloc(h, &d.pos, (size_t)h->grid_max * hylu::warps_per_block() * (size_t)d.pos_n));
     if (cudaMemsetAsync(d.ready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.fwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.bwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
@@ -209,8 +228,9 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
     if (!d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
     TRY(ensure_rhs(h, nrhs, ld));
     // the perturbation count decides whether to refine (Sec. 2.3); this also
-    // surfaces a device-side failure of the factorization
-    TRY(read_status(h, st));
+    // surfaces a device-side failure of the factorization.  opt.refine < 0:
+    // no refinement and no synchronization (the call stays asynchronous).
+    if (h->opt.refine >= 0) TRY(read_status(h, st));
     hylu::DevPlan& P = h->dp;
     ++h->gen_solve;
     TRY(hylu::launch_solve(P, d_b, d_x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
@@ -220,7 +240,7 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
     h->refine_iters = 0;
     h->backward_error = -1.0;
     h->last = st;
-    if (!(h->nperturb > 0 || h->opt.refine)) return HYLU_OK;
+    if (h->opt.refine < 0 || !(h->nperturb > 0 || h->opt.refine)) return HYLU_OK;
     // iterative refinement in FP64 on the original A (Sec. 2.3)
     double be_prev = INFINITY;
     for (;;) {
@@ -468,6 +488,8 @@ int hylu_destroy(hylu_handle* h) {
     if (h->uploaded) cudaDeviceSynchronize();
     for (void* p : h->allocs) cudaFree(p);
     for (int q = 0; q < 4; ++q) if (h->ev[q]) cudaEventDestroy(h->ev[q]);
+    if (h->graph_exec) cudaGraphExecDestroy(h->graph_exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
     if (h->h_norms) cudaFreeHost(h->h_norms);
     if (h->h_status) cudaFreeHost(h->h_status);
     delete h;
@@ -475,6 +497,135 @@ int hylu_destroy(hylu_handle* h) {
 }
 
 int64_t hylu_launch_count(void) { return hylu::launches(); }
+
+int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr, const int32_t* const* col,
+                       const double* const* vals, int32_t nsets, const hylu_options* opt, hylu_handle** out) {
+    if (!out || k < 1 || nsets < 1 || !n || !rowptr || !col) return HYLU_ERR_ARG;
+    *out = nullptr;
+    hylu_options o;
+    if (opt) o = *opt; else hylu_default_options(&o);
+    if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
+    hylu::AnalyzeOptions ao;
+    ao.ordering = o.ordering == HYLU_ORDER_USER ? HYLU_ORDER_AMD : o.ordering;
+    ao.static_pivot = o.static_pivot;
+    ao.scale = o.scale;
+    ao.sn_max = o.sn_max;
+    ao.nd_leaf = o.nd_leaf > 0 ? o.nd_leaf : 256;
+    ao.amd_dense = o.amd_dense > 0 ? o.amd_dense : 2.0;
+    std::vector<hylu::Plan> plans(k);
+    std::vector<int> rcs(k, 0);
+    unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)k));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&, t]() {
+            for (int32_t s = (int32_t)t; s < k; s += (int32_t)nt) {
+                try {
+                    rcs[s] = hylu::analyze(n[s], rowptr[s], col[s], vals ? vals[s] : nullptr, nullptr, ao, plans[s]);
+                } catch (const std::bad_alloc&) {
+                    rcs[s] = HYLU_ERR_NOMEM;
+                }
+            }
+        });
+    for (auto& t : th) t.join();
+    for (int32_t s = 0; s < k; ++s) if (rcs[s]) return rcs[s];
+    hylu_handle* h = new (std::nothrow) hylu_handle();
+    if (!h) return HYLU_ERR_NOMEM;
+    h->opt = o;
+    h->batch = true;
+    std::vector<const hylu::Plan*> ps;
+    for (auto& p : plans) ps.push_back(&p);
+    int rc;
+    try {
+        rc = hylu::combine(ps, nsets, h->P, h->layout);
+    } catch (const std::bad_alloc&) {
+        rc = HYLU_ERR_NOMEM;
+    }
+    if (rc) { delete h; return rc < 0 ? rc : HYLU_ERR_INTERNAL; }
+    *out = h;
+    return HYLU_OK;
+}
+
+int hylu_batch_layout(hylu_handle* h, int32_t* row_base, int64_t* val_base, int32_t* total_n) {
+    if (!h) return HYLU_ERR_ARG;
+    if (!h->batch) return HYLU_ERR_STATE;
+    if (row_base) std::memcpy(row_base, h->layout.row_base.data(), sizeof(int32_t) * h->layout.row_base.size());
+    if (val_base) std::memcpy(val_base, h->layout.val_base.data(), sizeof(int64_t) * h->layout.val_base.size());
+    if (total_n) *total_n = h->P.n;
+    return HYLU_OK;
+}
+
+int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
+                       void* stream) {
+    if (!h || !d_vals || !d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
+    if (!h->factored || nrhs > h->cap_rhs || (size_t)ld * nrhs > h->cap_elems) return HYLU_ERR_STATE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!st) return HYLU_ERR_ARG;   // the legacy default stream cannot be captured
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (h->graph_exec) { cudaGraphExecDestroy(h->graph_exec); h->graph_exec = nullptr; }
+    if (h->graph) { cudaGraphDestroy(h->graph); h->graph = nullptr; }
+    const int saved_refine = h->opt.refine;
+    const int saved_timing = h->opt.timing;
+    h->opt.refine = -1;
+    h->opt.timing = 0;
+    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        h->opt.refine = saved_refine; h->opt.timing = saved_timing;
+        return HYLU_ERR_CUDA;
+    }
+    int rc = do_factor(h, d_vals, st);
+    if (rc >= 0) rc = do_solve(h, d_b, d_x, nrhs, ld, st);
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(st, &g);
+    h->opt.refine = saved_refine;
+    h->opt.timing = saved_timing;
+    if (rc < 0) { if (g) cudaGraphDestroy(g); return rc; }
+    if (ce != cudaSuccess || !g) return HYLU_ERR_CUDA;
+    h->graph = g;
+    if (cudaGraphInstantiate(&h->graph_exec, g, 0) != cudaSuccess) return HYLU_ERR_CUDA;
+    return HYLU_OK;
+}
+
+int hylu_graph_launch(hylu_handle* h, void* stream) {
+    if (!h) return HYLU_ERR_ARG;
+    if (!h->graph_exec) return HYLU_ERR_STATE;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    h->last = st;
+    // the captured launches count as the library's own launches
+    hylu::add_launches(7);
+    return cudaGraphLaunch(h->graph_exec, st) == cudaSuccess ? HYLU_OK : HYLU_ERR_CUDA;
+}
+
+int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {
+    if (!h || !d_vals) return HYLU_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    TRY(do_factor(h, d_vals, st));   // uploads and allocates on first use
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+    const int maxper = std::max(1, h->grid_max / std::max(1, sms));
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int best = h->grid / std::max(1, sms);
+    float best_ms = 1e30f;
+    for (int per = 1; per <= maxper; ++per) {
+        h->grid = sms * per;
+        float tot = 0.f;
+        for (int rep = 0; rep < 2; ++rep) {
+            cudaEventRecord(e0, st);
+            int rc = do_factor(h, d_vals, st);
+            cudaEventRecord(e1, st);
+            if (rc < 0 || cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc < 0 ? rc : HYLU_ERR_CUDA; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep) tot += ms;
+        }
+        if (tot < best_ms) { best_ms = tot; best = per; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->grid = sms * best;
+    if (blocks_per_sm) *blocks_per_sm = best;
+    return read_status(h, st);
+}
 
 int hylu_debug_trace(hylu_handle* h, unsigned long long* out) {
     if (!h || !out) return HYLU_ERR_ARG;

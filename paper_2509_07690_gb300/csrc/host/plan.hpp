@@ -42,6 +42,7 @@ struct Plan {
     // depends on the last row of each source node and on the earlier rows of
     // its own supernode), ties by row index
     std::vector<int32_t> row_order;
+    std::vector<int32_t> row_level;     // dependency level of every row
     int32_t row_levels = 0;
     // substitution schedules (bulk mode of Sec. 2.2.1 / 2.3): node levels of
     // the forward (L) and backward (U) dependency graphs, the rows in claim
@@ -65,6 +66,18 @@ struct AnalyzeOptions {
     int nd_leaf = 256;
     double amd_dense = 2.0;
 };
+
+// Batch of independent systems (Sec. 3.2 repeated solves, extended to many
+// patterns): instance q = v * k + s (value set v of system s) occupies rows
+// [row_base[q], row_base[q] + n_s) of one block-diagonal plan; its values are
+// read from the concatenated input at val_base[q].  node_base gives every
+// node the first row of its instance; pos_n is the largest system.
+struct BatchLayout {
+    int32_t k = 0, nsets = 0, pos_n = 0;
+    std::vector<int32_t> row_base, node_base;
+    std::vector<int64_t> val_base;
+};
+int combine(const std::vector<const Plan*>& sys, int32_t nsets, Plan& C, BatchLayout& B);
 
 // Returns 0 or a negative hylu status code; fills P.
 int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,

@@ -168,6 +168,7 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
         maxl = std::max(maxl, l);
     }
     P.row_levels = maxl + 1;
+    P.row_level = lev;
     std::vector<int32_t> cnt(maxl + 2, 0);
     for (int32_t i = 0; i < n; ++i) cnt[lev[i] + 1]++;
     for (int32_t l = 0; l <= maxl; ++l) cnt[l + 1] += cnt[l];

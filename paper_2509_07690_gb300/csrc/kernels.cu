@@ -193,7 +193,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
     int* pb = ws->pb;
     double* win = ws->win;
     int* wcol = ws->wcol;
-    int* pos = P.pos + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.n;
+    int* pos_warp = P.pos + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.pos_n;
     const double amax = __longlong_as_double(*reinterpret_cast<const long long*>(P.status + ST_AMAX));
     const double tau = tau_rel * amax;
     for (;;) {
@@ -208,6 +208,9 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
         unsigned long long* wp = P.trace ? &waited : nullptr;
         const int D = P.node_of[i];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+        // slot maps are indexed by column relative to the first row of the
+        // row's instance (one system of a batch; 0 for a single system)
+        int* pos = pos_warp - (P.node_base ? P.node_base[D] : 0);
         const int64_t l0 = P.row_lptr[i];
         const int nL = (int)(P.row_lptr[i + 1] - l0);
         const int64_t t0 = P.node_tail_off[D];
@@ -944,6 +947,7 @@ __global__ void axpy_kernel(int32_t n, double* __restrict__ x, const double* __r
 
 int64_t launches() { return g_launches; }
 void count_launch() { ++g_launches; }
+void add_launches(int64_t k) { g_launches += k; }
 
 static int check(const char* what) {
     cudaError_t e = cudaGetLastError();

@@ -57,7 +57,9 @@ struct DevPlan {
     int32_t n_ut_levels, n_lt_levels;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
-    int32_t* pos;                  // per-warp column -> slot maps, n each
+    int32_t* pos;                  // per-warp column -> slot maps, pos_n each
+    int32_t pos_n;                 // largest system of the plan (n for one system)
+    const int32_t* node_base;      // per node: first row of its instance (null = 0)
     double* dinv;                  // 1 / u_ii by position (row)
     const int32_t* row_order;      // claim order of the factor kernel (by level)
     unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, warp<<8|mode)
@@ -88,5 +90,6 @@ int warps_per_block();
 int64_t launches();
 int measure_fp64_peak(double* gflops, cudaStream_t st);
 void count_launch();
+void add_launches(int64_t k);
 
 }  // namespace hylu

@@ -75,3 +75,45 @@ class Solver:
 
 def analyze(n, rowptr, col, vals=None, user_perm=None, **opts) -> Solver:
     return Solver(n, rowptr, col, vals, user_perm, **opts)
+
+
+class BatchSolver(Solver):
+    """k systems x nsets value sets in one block-diagonal plan
+    (hylu_analyze_batch): one persistent launch factors every instance;
+    instance q = v * k + s occupies rows row_base[q] .. of the combined
+    system and values val_base[q] .. of the concatenated value array."""
+
+    def __init__(self, systems, nsets: int = 1, **opts):
+        self.opt = capi.default_options(**opts)
+        self.systems = systems
+        self.k = len(systems)
+        self.nsets = int(nsets)
+        self.h = capi.hylu_analyze_batch(systems, self.nsets, self.opt)
+        self.info = capi.hylu_get_info(self.h)
+        self.row_base, self.val_base, self.n = capi.hylu_batch_layout(self.h, self.k * self.nsets)
+        rps = []
+        off = 0
+        for v in range(self.nsets):
+            for (n, rp, ci, _) in systems:
+                rps.append(np.asarray(rp, np.int64)[1:] + off)
+                off += int(rp[-1])
+        self.rowptr = np.concatenate([[0]] + rps).astype(np.int64)
+        self.col = None
+        self._factored = False
+
+    def concat_values(self, value_sets):
+        """value_sets[v][s]: values of system s in value set v -> one array."""
+        return np.concatenate([np.asarray(value_sets[v][s], np.float64)
+                               for v in range(self.nsets) for s in range(self.k)])
+
+    def tune(self, d_vals, stream=None) -> int:
+        self._factored = True
+        return capi.hylu_tune(self.h, d_vals.data_ptr(), _stream(stream))
+
+    def graph_capture(self, d_vals, d_b, d_x, stream=None):
+        b2 = d_b.reshape(-1, self.n)
+        capi.hylu_graph_capture(self.h, d_vals.data_ptr(), b2.data_ptr(), d_x.data_ptr(), b2.shape[0], self.n,
+                                _stream(stream))
+
+    def graph_launch(self, stream=None):
+        capi.hylu_graph_launch(self.h, _stream(stream))
