@@ -69,6 +69,8 @@ typedef struct {
     int debug;             /* 1: extra host checks                                     */
     double amd_dense;      /* AMD: rows denser than max(16, amd_dense*sqrt(n)) go last (2) */
     int timing;            /* 1: time the factor and solve kernels with CUDA events     */
+    int precision;         /* 0: FP64 factors; 1: FP32 factors (scaling and the small-pivot
+                              check in FP64) with FP64 iterative refinement on every solve */
 } hylu_options;
 
 typedef struct {

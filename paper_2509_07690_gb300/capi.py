@@ -33,7 +33,7 @@ class Options(C.Structure):
                 ("sn_max", C.c_int), ("nd_leaf", C.c_int), ("pivot_tau", C.c_double),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine", C.c_int),
                 ("spin_limit", C.c_longlong), ("rows_per_task", C.c_int), ("debug", C.c_int),
-                ("amd_dense", C.c_double), ("timing", C.c_int)]
+                ("amd_dense", C.c_double), ("timing", C.c_int), ("precision", C.c_int)]
 
 
 class Info(C.Structure):

@@ -99,8 +99,15 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     d.row_order = ro;
     d.trace = nullptr;
     if (h->opt.debug & 2) TRY(dalloc(h, &d.trace, 4 * (size_t)P.n));
-    TRY(dalloc(h, &d.lval, P.nnz_l));
-    TRY(dalloc(h, &d.pval, P.nnz_panel));
+    d.lval = nullptr; d.pval = nullptr; d.lval32 = nullptr; d.pval32 = nullptr; d.dinv32 = nullptr;
+    if (h->opt.precision == 1) {
+        TRY(dalloc(h, &d.lval32, P.nnz_l));
+        TRY(dalloc(h, &d.pval32, P.nnz_panel));
+        TRY(dalloc(h, &d.dinv32, P.n));
+    } else {
+        TRY(dalloc(h, &d.lval, P.nnz_l));
+        TRY(dalloc(h, &d.pval, P.nnz_panel));
+    }
     TRY(dalloc(h, &d.piv, P.n));
     TRY(dalloc(h, &d.pinv, P.n));
     TRY(dalloc(h, &d.ready, P.n));
@@ -332,6 +339,7 @@ int hylu_default_options(hylu_options* o) {
     o->debug = 0;
     o->amd_dense = 2.0;
     o->timing = 0;
+    o->precision = 0;
     return HYLU_OK;
 }
 
@@ -343,6 +351,8 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
     hylu_options o;
     if (opt) o = *opt; else hylu_default_options(&o);
     if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
+    if (o.precision != 0 && o.precision != 1) return HYLU_ERR_ARG;
+    if (o.precision == 1 && o.refine == 0) o.refine = 1;   // FP32 factors: always refine in FP64
     hylu_handle* h = new (std::nothrow) hylu_handle();
     if (!h) return HYLU_ERR_NOMEM;
     h->opt = o;
@@ -465,9 +475,18 @@ int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv) {
     if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
     std::vector<double> lv(P.nnz_l), pv(P.nnz_panel);
     std::vector<int32_t> pv_piv(P.n);
-    if (cudaMemcpy(lv.data(), h->dp.lval, sizeof(double) * P.nnz_l, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(pv.data(), h->dp.pval, sizeof(double) * P.nnz_panel, cudaMemcpyDeviceToHost) != cudaSuccess ||
-        cudaMemcpy(pv_piv.data(), h->dp.piv, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+    if (h->dp.lval32) {
+        std::vector<float> lf(P.nnz_l), pf(P.nnz_panel);
+        if (cudaMemcpy(lf.data(), h->dp.lval32, sizeof(float) * P.nnz_l, cudaMemcpyDeviceToHost) != cudaSuccess ||
+            cudaMemcpy(pf.data(), h->dp.pval32, sizeof(float) * P.nnz_panel, cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HYLU_ERR_CUDA;
+        for (int64_t q = 0; q < P.nnz_l; ++q) lv[q] = lf[q];
+        for (int64_t q = 0; q < P.nnz_panel; ++q) pv[q] = pf[q];
+    } else if (cudaMemcpy(lv.data(), h->dp.lval, sizeof(double) * P.nnz_l, cudaMemcpyDeviceToHost) != cudaSuccess ||
+               cudaMemcpy(pv.data(), h->dp.pval, sizeof(double) * P.nnz_panel, cudaMemcpyDeviceToHost) != cudaSuccess) {
+        return HYLU_ERR_CUDA;
+    }
+    if (cudaMemcpy(pv_piv.data(), h->dp.piv, sizeof(int32_t) * P.n, cudaMemcpyDeviceToHost) != cudaSuccess)
         return HYLU_ERR_CUDA;
     if (piv) std::memcpy(piv, pv_piv.data(), sizeof(int32_t) * P.n);
     if (!vals) return HYLU_OK;
@@ -505,6 +524,8 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
     hylu_options o;
     if (opt) o = *opt; else hylu_default_options(&o);
     if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
+    if (o.precision != 0 && o.precision != 1) return HYLU_ERR_ARG;
+    if (o.precision == 1 && o.refine == 0) o.refine = 1;
     hylu::AnalyzeOptions ao;
     ao.ordering = o.ordering == HYLU_ORDER_USER ? HYLU_ORDER_AMD : o.ordering;
     ao.static_pivot = o.static_pivot;

@@ -103,23 +103,36 @@ __global__ void amax_kernel(const double* __restrict__ vals, const int64_t* __re
                   (unsigned long long)__double_as_longlong(m));
 }
 
+// Factor values of the plan in precision T (FP64 or the FP32 form).
+template <typename T> __device__ __forceinline__ T* LV(const DevPlan& P);
+template <typename T> __device__ __forceinline__ T* PV(const DevPlan& P);
+template <> __device__ __forceinline__ double* LV<double>(const DevPlan& P) { return P.lval; }
+template <> __device__ __forceinline__ double* PV<double>(const DevPlan& P) { return P.pval; }
+template <> __device__ __forceinline__ float* LV<float>(const DevPlan& P) { return P.lval32; }
+template <> __device__ __forceinline__ float* PV<float>(const DevPlan& P) { return P.pval32; }
+template <typename T> __device__ __forceinline__ T* DI(const DevPlan& P);
+template <> __device__ __forceinline__ double* DI<double>(const DevPlan& P) { return P.dinv; }
+template <> __device__ __forceinline__ float* DI<float>(const DevPlan& P) { return P.dinv32; }
+
 // -------------------------------------------------------------- factor
 // Per-warp shared memory of the factor kernel.
 constexpr int FWARPS = 4;          // warps per block of the factor kernel (one per SM sub-partition)
 constexpr int PANEL_BYTES = 4096;  // U part of the row being updated
 constexpr int PF = 4;              // leading tail entries prefetched per source
 constexpr int UNR = 8;             // independent 32-entry batches in flight
+template <typename T>
 struct WarpSmem {
-    double lb[SN_SMEM];            // source supernode: l by position
+    T lb[SN_SMEM];            // source supernode: l by position
     int pb[SN_SMEM];               // source supernode: label offset of each position
-    double win[32];                // x for the 32 L slots of the current window
+    T win[32];                     // x for the 32 L slots of the current window
     int wcol[32];                  // their columns
     int plen[32];                  // per window source: tail entries inside the window
     int pfc[32][PF];               // per window source: its first PF tail columns
-    double pfu[32][PF];            //                    and values
+    T pfu[32][PF];                 //                    and values
     __align__(16) unsigned char panel[PANEL_BYTES];
 };
-constexpr size_t FACTOR_SMEM = sizeof(WarpSmem) * FWARPS;
+template <typename T>
+constexpr size_t factor_smem() { return sizeof(WarpSmem<T>) * FWARPS; }
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -140,8 +153,9 @@ __device__ __forceinline__ int bsearch_sm(const int* a, int m, int c) {
 //   mode 0: shared memory, dense over columns r .. maxcol (index c - r)
 //   mode 1: shared memory, block then tail slots; tail found by binary search
 //   mode 2: the row's own panel storage in global memory (index by slot)
+template <typename T>
 struct Panel {
-    double* x;
+    T* x;
     const int* scols;
     int mode, r, e, s, nL, nT;
     __device__ __forceinline__ int idx(const int* pos, int c) const {
@@ -159,17 +173,18 @@ struct Panel {
 // global memory: no one reads them before the window moves past them and a
 // fence is taken), the others to the panel.  Loads of UNR batches are issued
 // before any update so that their latencies overlap.
-__device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, const double* __restrict__ U1,
-                                           int j0, int nTS, double l, int r, const int* pos, double* xl,
-                                           const Panel& pn, int lane) {
+template <typename T>
+__device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, const T* __restrict__ U1,
+                                           int j0, int nTS, T l, int r, const int* pos, T* xl,
+                                           const Panel<T>& pn, int lane) {
     for (int jb = j0; jb < nTS; jb += 32 * UNR) {
         int c[UNR];
-        double u[UNR];
+        T u[UNR];
 #pragma unroll
         for (int m = 0; m < UNR; ++m) {
             const int j = jb + m * 32 + lane;
             c[m] = (j < nTS) ? __ldg(tcS + j) : -1;
-            u[m] = (j < nTS) ? __ldg(U1 + j) : 0.0;
+            u[m] = (j < nTS) ? __ldg(U1 + j) : T(0);
         }
         int ix[UNR];
 #pragma unroll
@@ -183,15 +198,16 @@ __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, cons
     }
 }
 
+template <typename T>
 __global__ void __launch_bounds__(FWARPS * 32)
-factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ dinv, int gen,
+factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, int gen,
               double tau_rel, long long limit) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    WarpSmem* ws = reinterpret_cast<WarpSmem*>(smem_raw) + wid;
-    double* lb = ws->lb;
+    WarpSmem<T>* ws = reinterpret_cast<WarpSmem<T>*>(smem_raw) + wid;
+    T* lb = ws->lb;
     int* pb = ws->pb;
-    double* win = ws->win;
+    T* win = ws->win;
     int* wcol = ws->wcol;
     int* pos_warp = P.pos + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.pos_n;
     const double amax = __longlong_as_double(*reinterpret_cast<const long long*>(P.status + ST_AMAX));
@@ -216,19 +232,19 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
         const int64_t t0 = P.node_tail_off[D];
         const int nT = (int)(P.node_tail_off[D + 1] - t0);
         const int w = s + nT;
-        double* xl = P.lval + l0;
-        double* xu = P.pval + P.node_panel_off[D] + (int64_t)(i - r) * w;
+        T* xl = LV<T>(P) + l0;
+        T* xu = PV<T>(P) + P.node_panel_off[D] + (int64_t)(i - r) * w;
         const int32_t* lc = P.lcols + l0;
         const int32_t* tc = P.tcols + t0;
         const int maxcol = nT > 0 ? tc[nT - 1] : e;
-        Panel pn;
+        Panel<T> pn;
         pn.r = r; pn.e = e; pn.s = s; pn.nL = nL; pn.nT = nT;
-        pn.scols = reinterpret_cast<const int*>(ws->panel + sizeof(double) * (size_t)w);
+        pn.scols = reinterpret_cast<const int*>(ws->panel + sizeof(T) * (size_t)w);
         int range;
-        if ((int64_t)(maxcol - r + 1) * 8 <= PANEL_BYTES) {
-            pn.mode = 0; pn.x = reinterpret_cast<double*>(ws->panel); range = maxcol - r + 1;
-        } else if ((int64_t)w * 8 + (int64_t)nT * 4 <= PANEL_BYTES) {
-            pn.mode = 1; pn.x = reinterpret_cast<double*>(ws->panel); range = w;
+        if ((int64_t)(maxcol - r + 1) * (int64_t)sizeof(T) <= PANEL_BYTES) {
+            pn.mode = 0; pn.x = reinterpret_cast<T*>(ws->panel); range = maxcol - r + 1;
+        } else if ((int64_t)w * (int64_t)sizeof(T) + (int64_t)nT * 4 <= PANEL_BYTES) {
+            pn.mode = 1; pn.x = reinterpret_cast<T*>(ws->panel); range = w;
         } else {
             pn.mode = 2; pn.x = xu; range = w;
         }
@@ -237,10 +253,10 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
         //      L slots accumulate in global memory and are found through pos[]
         //      (also used by a panel kept in global memory).
         const bool need_pos = (nL > 32) || (pn.mode == 2);
-        win[lane] = 0.0;
-        for (int t = 32 + lane; t < nL; t += 32) xl[t] = 0.0;
+        win[lane] = T(0);
+        for (int t = 32 + lane; t < nL; t += 32) xl[t] = T(0);
         if (need_pos) for (int t = lane; t < nL; t += 32) pos[lc[t]] = t;
-        for (int t = lane; t < range; t += 32) pn.x[t] = 0.0;
+        for (int t = lane; t < range; t += 32) pn.x[t] = T(0);
         if (pn.mode == 1) {
             int* sc = const_cast<int*>(pn.scols);
             for (int j = lane; j < nT; j += 32) sc[j] = tc[j];
@@ -249,7 +265,8 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
         __syncwarp();
         for (int64_t q = P.ah_rp[i] + lane; q < P.ah_rp[i + 1]; q += 32) {
             const int sl = P.ah_slot[q];
-            const double v = vals[P.ah_src[q]] * P.ah_scale[q];
+            // scaling in FP64, then rounded to the factor precision
+            const T v = (T)(vals[P.ah_src[q]] * P.ah_scale[q]);
             if (sl < nL) {
                 if (sl < 32) win[sl] = v; else xl[sl] = v;
             } else {
@@ -266,7 +283,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
             const int tq = t + lane;
             int kq = 0, eq = 0, sq = 1, nTq = 0, okq = 1;
             int64_t tq0 = 0, pq0 = 0;
-            double dq = 0.0;
+            T dq = T(0);
             if (t > 0 && pending) { __threadfence(); pending = false; }
             if (lane < cend) {
                 kq = lc[tq];
@@ -282,7 +299,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
 #pragma unroll
                     for (int m = 0; m < PF; ++m) {
                         ws->pfc[lane][m] = (m < nTq) ? P.tcols[tq0 + m] : INT_MAX;
-                        ws->pfu[lane][m] = (m < nTq) ? P.pval[pq0 + 1 + m] : 0.0;
+                        ws->pfu[lane][m] = (m < nTq) ? PV<T>(P)[pq0 + 1 + m] : T(0);
                     }
                 }
                 if (t > 0) win[lane] = xl[tq];
@@ -299,7 +316,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
                 if (sS != 1) break;
                 const int k = __shfl_sync(FULL, kq, q);
                 const int nTS = __shfl_sync(FULL, nTq, q);
-                double dk = __shfl_sync(FULL, dq, q);
+                T dk = __shfl_sync(FULL, dq, q);
                 if (!((rmask >> q) & 1u)) {
                     if (!warp_wait(P.ready + k, gen, P.status, k, limit, wp)) return;
                     dk = dinv[k];
@@ -307,11 +324,11 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
                         const int64_t tS = P.node_tail_off[P.node_of[k]];
                         const int64_t pS = P.node_panel_off[P.node_of[k]];
                         ws->pfc[q][lane] = (lane < nTS) ? P.tcols[tS + lane] : INT_MAX;
-                        ws->pfu[q][lane] = (lane < nTS) ? P.pval[pS + 1 + lane] : 0.0;
+                        ws->pfu[q][lane] = (lane < nTS) ? PV<T>(P)[pS + 1 + lane] : T(0);
                     }
                     __syncwarp();
                 }
-                const double l = win[q] * dk;
+                const T l = win[q] * dk;
                 int inwin = 0;
                 if (lane < PF) {
                     const int c = ws->pfc[q][lane];
@@ -325,7 +342,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
                 if (pl == PF && nTS > PF) {
                     // rare: more of this source's tail falls inside the window
                     const int64_t tS = P.node_tail_off[P.node_of[k]];
-                    const double* U1 = P.pval + P.node_panel_off[P.node_of[k]] + 1;
+                    const T* U1 = PV<T>(P) + P.node_panel_off[P.node_of[k]] + 1;
                     for (int jb = PF; jb < nTS; jb += 32) {
                         const int j = jb + lane;
                         const int c = (j < nTS) ? P.tcols[tS + j] : INT_MAX;
@@ -350,7 +367,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
                 if (pl >= nTS) continue;
                 const int64_t tS = __shfl_sync(FULL, tq0, qq);
                 const int64_t pS = __shfl_sync(FULL, pq0, qq);
-                apply_tail(P.tcols + tS, P.pval + pS + 1, pl, nTS, win[qq], r, pos, xl, pn, lane);
+                apply_tail<T>(P.tcols + tS, PV<T>(P) + pS + 1, pl, nTS, win[qq], r, pos, xl, pn, lane);
                 __syncwarp();
             }
             // any L slot past this window may have received atomic adds
@@ -376,7 +393,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
                 const int tt = t + qs;
                 const int rS = eS - sS + 1;
                 const int wS = sS + nTS;
-                const double* __restrict__ U = P.pval + pS;
+                const T* __restrict__ U = PV<T>(P) + pS;
                 const int32_t* __restrict__ tcS = P.tcols + tS;
                 for (int p = lane; p < sS; p += 32) {
                     const int lab = P.piv[rS + p] - rS;
@@ -385,17 +402,17 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
                 }
                 __syncwarp();
                 for (int p = 0; p < sS; ++p) {
-                    const double* Up = U + (int64_t)p * wS;
-                    const double lp = lb[p] * dinv[rS + p];
+                    const T* Up = U + (int64_t)p * wS;
+                    const T lp = lb[p] * dinv[rS + p];
                     __syncwarp();
                     for (int qq = p + 1 + lane; qq < sS; qq += 32) lb[qq] -= lp * Up[pb[qq]];
                     if (lane == 0) lb[p] = lp;
                     __syncwarp();
                 }
                 for (int j = lane; j < nTS; j += 32) {
-                    const double* Uj = U + sS + j;
+                    const T* Uj = U + sS + j;
                     const int c = tcS[j];
-                    double acc0 = 0.0, acc1 = 0.0;
+                    T acc0 = T(0), acc1 = T(0);
                     int p = 0;
                     for (; p + 1 < sS; p += 2) {
                         acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
@@ -422,21 +439,21 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
         const unsigned long long waited_ext = waited;
         if (s > 1) {
             // ---- earlier rows of the own supernode, each as soon as it is ready
-            const double* Ub = P.pval + P.node_panel_off[D];
+            const T* Ub = PV<T>(P) + P.node_panel_off[D];
             for (int k = r; k < i; ++k) {
                 if (!warp_wait(P.ready + k, gen, P.status, k, limit, wp)) return;
                 const int lab = ld_relaxed(P.piv + k) - r;
-                const double* Uk = Ub + (int64_t)(k - r) * w;
-                const double l = pn.x[lab] * dinv[k];
+                const T* Uk = Ub + (int64_t)(k - r) * w;
+                const T l = pn.x[lab] * dinv[k];
                 for (int c = lane; c < s; c += 32)
                     if (c != lab && ld_relaxed(P.pinv + r + c) > k) pn.x[c] -= l * Uk[c];
                 for (int jb = 0; jb < nT; jb += 32 * UNR) {
-                    double u[UNR];
+                    T u[UNR];
                     int ix[UNR];
 #pragma unroll
                     for (int m = 0; m < UNR; ++m) {
                         const int j = jb + m * 32 + lane;
-                        u[m] = (j < nT) ? Uk[s + j] : 0.0;
+                        u[m] = (j < nT) ? Uk[s + j] : T(0);
                         ix[m] = (j < nT) ? pn.tail_idx(tc, j) : -1;
                     }
 #pragma unroll
@@ -452,7 +469,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
             double best = -1.0;
             int bp = i;
             for (int p = i + lane; p <= e; p += 32) {
-                const double a = fabs(pn.x[P.piv[p] - r]);
+                const double a = fabs((double)pn.x[P.piv[p] - r]);
                 if (a > best) { best = a; bp = p; }
             }
             for (int off = 16; off; off >>= 1) {
@@ -471,13 +488,14 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, double* __restrict__ d
         // ---- pivot, small-pivot perturbation
         if (lane == 0) {
             const int dl = (s > 1) ? (P.piv[i] - r) : 0;
-            double u = pn.x[dl];
+            // the small-pivot check is taken in FP64 whatever the factor precision
+            double u = (double)pn.x[dl];
             if (fabs(u) < tau) {
                 u = (u >= 0.0) ? tau : -tau;
-                pn.x[dl] = u;
+                pn.x[dl] = (T)u;
                 atomicAdd(P.status + ST_NPERT, 1);
             }
-            dinv[i] = 1.0 / u;
+            dinv[i] = (T)(1.0 / (double)pn.x[dl]);
         }
         __syncwarp();
         // ---- write the U part back from shared memory, publish
@@ -534,23 +552,24 @@ __device__ __forceinline__ bool lane_wait(const int* flag, int gen, int* status,
 
 // Warp-wide sum of v[t] * x[c[t]], t < m, with UNR independent gathers in
 // flight per lane; the result is valid in every lane.
-__device__ __forceinline__ double sparse_dot(const double* __restrict__ v, const int32_t* __restrict__ c, int m,
+template <typename T>
+__device__ __forceinline__ double sparse_dot(const T* __restrict__ v, const int32_t* __restrict__ c, int m,
                                              const double* __restrict__ x, int lane) {
     double acc[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) acc[u] = 0.0;
     for (int t0 = 0; t0 < m; t0 += 32 * UNR) {
         int cc[UNR];
-        double vv[UNR];
+        T vv[UNR];
 #pragma unroll
         for (int u = 0; u < UNR; ++u) {
             const int t = t0 + u * 32 + lane;
             cc[u] = (t < m) ? __ldg(c + t) : -1;
-            vv[u] = (t < m) ? __ldg(v + t) : 0.0;
+            vv[u] = (t < m) ? __ldg(v + t) : T(0);
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
-            if (cc[u] >= 0) acc[u] = fma(vv[u], x[cc[u]], acc[u]);
+            if (cc[u] >= 0) acc[u] = fma((double)vv[u], x[cc[u]], acc[u]);
     }
     double a = 0.0;
 #pragma unroll
@@ -589,11 +608,100 @@ __device__ __forceinline__ void node_complete(int* done, const int* count, int L
     if (atom_add_acq_rel(done + L, 1) + 1 == count[L]) st_release(wm, L + 1);
 }
 
+// Dense block of a supernode in the substitution, by 32-row tiles with lanes
+// over rows: the tile's own triangle is solved from registers with shuffles,
+// then its 32 results are applied to the remaining rows with independent
+// loads (about s/32 dependent steps instead of s).  The block is stored by
+// label: entry (i, position p) of row i is Ub[(i - r) * w + piv[p] - r].
+template <typename T>
+__device__ void block_forward(const T* __restrict__ Ub, int w, int r, int s, const int32_t* __restrict__ piv,
+                              double* __restrict__ z, int lane) {
+    for (int T0 = 0; T0 < s; T0 += 32) {
+        const int nt = min(32, s - T0);
+        const int lp = (lane < nt) ? piv[r + T0 + lane] - r : 0;      // label offset of tile column `lane`
+        // the tile's own strictly lower triangle
+        double my = (lane < nt) ? z[r + T0 + lane] : 0.0;
+        T Lrow[32];
+        const T* Ui = Ub + (int64_t)(T0 + lane) * w;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const int lc = __shfl_sync(FULL, lp, c);
+            Lrow[c] = (lane < nt && c < lane) ? Ui[lc] : T(0);
+        }
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const double zc = __shfl_sync(FULL, my, c);
+            if (c < lane) my -= (double)Lrow[c] * zc;
+        }
+        if (lane < nt) z[r + T0 + lane] = my;
+        // the rows below the tile
+        for (int R0 = T0 + 32; R0 < s; R0 += 32) {
+            // every lane runs the same shuffles; only the loads and the
+            // update of rows past the block's end are switched off
+            const int row = R0 + lane;
+            const bool ok = row < s;
+            const T* Ur = Ub + (int64_t)(ok ? row : 0) * w;
+            double a = 0.0;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int lc = __shfl_sync(FULL, lp, c);
+                const double zc = __shfl_sync(FULL, my, c);
+                if (ok && c < nt) a = fma((double)Ur[lc], zc, a);
+            }
+            if (ok) z[r + row] -= a;
+        }
+        __syncwarp();
+    }
+}
+
+template <typename T>
+__device__ void block_backward(const T* __restrict__ Ub, int w, int r, int s, const int32_t* __restrict__ piv,
+                               const T* __restrict__ dinv, double* __restrict__ z, int lane) {
+    const int ntiles = (s + 31) / 32;
+    for (int tix = ntiles - 1; tix >= 0; --tix) {
+        const int T0 = tix * 32;
+        const int nt = min(32, s - T0);
+        const int lp = (lane < nt) ? piv[r + T0 + lane] - r : 0;
+        double my = (lane < nt) ? z[r + T0 + lane] : 0.0;
+        const double di = (lane < nt) ? (double)dinv[r + T0 + lane] : 0.0;
+        T Urow[32];
+        const T* Ui = Ub + (int64_t)(T0 + lane) * w;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            const int lc = __shfl_sync(FULL, lp, c);
+            Urow[c] = (lane < nt && c > lane && c < nt) ? Ui[lc] : T(0);
+        }
+        // upper triangle of the tile, last row first
+#pragma unroll
+        for (int c = 31; c >= 0; --c) {
+            if (lane == c) my *= di;
+            const double wc = __shfl_sync(FULL, my, c);
+            if (lane < c) my -= (double)Urow[c] * wc;
+        }
+        if (lane < nt) z[r + T0 + lane] = my;
+        // the rows above the tile
+        for (int R0 = 0; R0 < T0; R0 += 32) {
+            const int row = R0 + lane;          // R0 + 32 <= T0: every lane has a row
+            const T* Ur = Ub + (int64_t)row * w;
+            double a = 0.0;
+#pragma unroll
+            for (int c = 0; c < 32; ++c) {
+                const int lc = __shfl_sync(FULL, lp, c);
+                const double wc = __shfl_sync(FULL, my, c);
+                if (c < nt) a = fma((double)Ur[lc], wc, a);
+            }
+            z[r + row] -= a;
+        }
+        __syncwarp();
+    }
+}
+
 // Forward substitution L z = bhat (unit L, by position); z holds bhat on
 // entry.  Each warp claims the next row in level order, waits for the lower
 // levels, subtracts the row's L list; the warp of the LAST row of a supernode
 // then solves the unit lower block once all rows of the supernode have their
 // external part.  Right-hand sides are columns of z (stride n).
+template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit) {
     const int lane = threadIdx.x & 31;
@@ -613,7 +721,7 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit
         const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
         for (int rr = 0; rr < nrhs; ++rr) {
             double* zr = z + (int64_t)rr * n;
-            const double a = sparse_dot(P.lval + l0, P.lcols + l0, (int)(l1 - l0), zr, lane);
+            const double a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), zr, lane);
             if (lane == 0) zr[i] -= a;
         }
         __threadfence();
@@ -629,18 +737,8 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit
         for (int k = r + lane; k < e && ok; k += 32) ok = lane_wait(P.fwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
         const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
-        const double* Ub = P.pval + P.node_panel_off[D];
-        for (int rr = 0; rr < nrhs; ++rr) {
-            double* zr = z + (int64_t)rr * n;
-            for (int ii = r + 1; ii <= e; ++ii) {
-                const double* Ui = Ub + (int64_t)(ii - r) * w;
-                double a = 0.0;
-                for (int k = r + lane; k < ii; k += 32) a = fma(Ui[P.piv[k] - r], zr[k], a);
-                for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                if (lane == 0) zr[ii] -= a;
-                __syncwarp();
-            }
-        }
+        const T* Ub = PV<T>(P) + P.node_panel_off[D];
+        for (int rr = 0; rr < nrhs; ++rr) block_forward<T>(Ub, w, r, s, P.piv, z + (int64_t)rr * n, lane);
         __threadfence();
         __syncwarp();
         if (lane == 0) node_complete(P.fwd_done, P.fwd_count, L, P.status + ST_WM_F);
@@ -651,8 +749,9 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit
 // label: xh[piv[p]] = w_p.  Rows are claimed level by level (descending inside
 // a level); each subtracts its U tail, and the warp of the FIRST row of a
 // supernode then back-substitutes the block.  z is overwritten.
+template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
-bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
+bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
            double* __restrict__ xh, int nrhs, int gen, long long limit) {
     const int lane = threadIdx.x & 31;
     const int n = P.n;
@@ -671,14 +770,14 @@ bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
         const int nT = (int)(P.node_tail_off[D + 1] - t0);
         const int w = s + nT;
         const int32_t* tc = P.tcols + t0;
-        const double* Ui = P.pval + P.node_panel_off[D] + (int64_t)(i - r) * w;
+        const T* Ui = PV<T>(P) + P.node_panel_off[D] + (int64_t)(i - r) * w;
         if (!__all_sync(FULL, wait_level(P.status + ST_WM_B, L, cached, P.status, limit))) return;
         for (int rr = 0; rr < nrhs; ++rr) {
             double* zr = z + (int64_t)rr * n;
             const double* xr = xh + (int64_t)rr * n;
-            const double a = sparse_dot(Ui + s, tc, nT, xr, lane);
+            const double a = sparse_dot<T>(Ui + s, tc, nT, xr, lane);
             if (lane == 0) {
-                if (s == 1) xh[(int64_t)rr * n + i] = (zr[i] - a) * dinv[i];
+                if (s == 1) xh[(int64_t)rr * n + i] = (zr[i] - a) * (double)dinv[i];
                 else zr[i] -= a;
             }
         }
@@ -693,18 +792,11 @@ bwd_kernel(DevPlan P, const double* __restrict__ dinv, double* __restrict__ z,
         int ok = 1;
         for (int k = r + 1 + lane; k <= e && ok; k += 32) ok = lane_wait(P.bwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
-        const double* Ub = P.pval + P.node_panel_off[D];
+        const T* Ub = PV<T>(P) + P.node_panel_off[D];
         for (int rr = 0; rr < nrhs; ++rr) {
             double* zr = z + (int64_t)rr * n;
             double* xr = xh + (int64_t)rr * n;
-            for (int ii = e; ii >= r; --ii) {
-                const double* Uii = Ub + (int64_t)(ii - r) * w;
-                double a = 0.0;
-                for (int p = ii + 1 + lane; p <= e; p += 32) a = fma(Uii[P.piv[p] - r], zr[p], a);
-                for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                if (lane == 0) zr[ii] = (zr[ii] - a) * dinv[ii];
-                __syncwarp();
-            }
+            block_backward<T>(Ub, w, r, s, P.piv, dinv, zr, lane);
             for (int p = r + lane; p <= e; p += 32) xr[P.piv[p]] = zr[p];
             __syncwarp();
         }
@@ -742,6 +834,7 @@ __global__ void permute_out_t_kernel(int32_t n, const int32_t* __restrict__ rowp
 }
 
 // U^T v = h by position (h is overwritten by v)
+template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit) {
     const int lane = threadIdx.x & 31;
@@ -760,10 +853,10 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit)
         const int64_t t0 = P.node_tail_off[D];
         const int nT = (int)(P.node_tail_off[D + 1] - t0);
         const int w = s + nT;
-        const double* Ub = P.pval + P.node_panel_off[D];
+        const T* Ub = PV<T>(P) + P.node_panel_off[D];
         if (!__all_sync(FULL, wait_level(P.status + ST_WM_F, L, cached, P.status, limit))) return;
         if (s == 1) {
-            if (lane == 0) for (int rr = 0; rr < nrhs; ++rr) h[(int64_t)rr * n + i] *= P.dinv[i];
+            if (lane == 0) for (int rr = 0; rr < nrhs; ++rr) h[(int64_t)rr * n + i] *= (double)DI<T>(P)[i];
             __syncwarp();
         } else if (i == r) {
             // the block: v_p = (h_p - sum_{k in [r,p)} U(k, pos p) v_k) / u_pp
@@ -772,9 +865,9 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit)
                 for (int p = r; p <= e; ++p) {
                     const int lp = P.piv[p] - r;
                     double a = 0.0;
-                    for (int k = r + lane; k < p; k += 32) a = fma(Ub[(int64_t)(k - r) * w + lp], hr[k], a);
+                    for (int k = r + lane; k < p; k += 32) a = fma((double)Ub[(int64_t)(k - r) * w + lp], hr[k], a);
                     for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                    if (lane == 0) hr[p] = (hr[p] - a) * P.dinv[p];
+                    if (lane == 0) hr[p] = (hr[p] - a) * (double)DI<T>(P)[p];
                     __syncwarp();
                 }
             }
@@ -785,13 +878,13 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit)
             if (!__all_sync(FULL, lane_wait(P.fwd_row + r, gen, P.status, r, limit))) return;
         }
         // push row i's U tail: h[pos of label c] -= U(i, c) v_i
-        const double* Ui = Ub + (int64_t)(i - r) * w + s;
+        const T* Ui = Ub + (int64_t)(i - r) * w + s;
         const int32_t* tc = P.tcols + t0;
         for (int rr = 0; rr < nrhs; ++rr) {
             double* hr = h + (int64_t)rr * n;
             const double vi = hr[i];
             if (vi != 0.0)
-                for (int j = lane; j < nT; j += 32) atomicAdd(hr + P.pinv[tc[j]], -Ui[j] * vi);
+                for (int j = lane; j < nT; j += 32) atomicAdd(hr + P.pinv[tc[j]], -(double)Ui[j] * vi);
         }
         __threadfence();
         __syncwarp();
@@ -800,6 +893,7 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit)
 }
 
 // L^T u = v by position (h holds v on entry, u on exit)
+template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit) {
     const int lane = threadIdx.x & 31;
@@ -820,13 +914,13 @@ lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit)
             if (i == e) {
                 // the block: u_k = v_k - sum_{j in (k, e]} L(j, pos k) u_j
                 const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
-                const double* Ub = P.pval + P.node_panel_off[D];
+                const T* Ub = PV<T>(P) + P.node_panel_off[D];
                 for (int rr = 0; rr < nrhs; ++rr) {
                     double* hr = h + (int64_t)rr * n;
                     for (int k = e - 1; k >= r; --k) {
                         const int lk = P.piv[k] - r;
                         double a = 0.0;
-                        for (int j = k + 1 + lane; j <= e; j += 32) a = fma(Ub[(int64_t)(j - r) * w + lk], hr[j], a);
+                        for (int j = k + 1 + lane; j <= e; j += 32) a = fma((double)Ub[(int64_t)(j - r) * w + lk], hr[j], a);
                         for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
                         if (lane == 0) hr[k] -= a;
                         __syncwarp();
@@ -845,7 +939,7 @@ lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit)
             double* hr = h + (int64_t)rr * n;
             const double ui = hr[i];
             if (ui != 0.0)
-                for (int64_t t = l0 + lane; t < l1; t += 32) atomicAdd(hr + P.lcols[t], -P.lval[t] * ui);
+                for (int64_t t = l0 + lane; t < l1; t += 32) atomicAdd(hr + P.lcols[t], -(double)LV<T>(P)[t] * ui);
         }
         __threadfence();
         __syncwarp();
@@ -963,8 +1057,9 @@ int warps_per_block() { return FWARPS; }
 int factor_grid(int device) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaFuncSetAttribute(factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FACTOR_SMEM);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel, FWARPS * 32, FACTOR_SMEM);
+    cudaFuncSetAttribute(factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)factor_smem<double>());
+    cudaFuncSetAttribute(factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)factor_smem<float>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel<double>, FWARPS * 32, factor_smem<double>());
     if (per < 1) per = 1;
     if (per > 4) per = 4;
     return sms * per;
@@ -985,7 +1080,10 @@ int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t
     amax_kernel<<<blocks, 256, 0, st>>>(d_vals, P.ah_src, P.ah_scale, nnz_a, P.status);
     count_launch();
     if (e0) cudaEventRecord(e0, st);
-    factor_kernel<<<grid, FWARPS * 32, FACTOR_SMEM, st>>>(P, d_vals, P.dinv, gen, tau_rel, spin_limit);
+    if (P.lval32)
+        factor_kernel<float><<<grid, FWARPS * 32, factor_smem<float>(), st>>>(P, d_vals, P.dinv32, gen, tau_rel, spin_limit);
+    else
+        factor_kernel<double><<<grid, FWARPS * 32, factor_smem<double>(), st>>>(P, d_vals, P.dinv, gen, tau_rel, spin_limit);
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     return check("factor");
@@ -1004,9 +1102,11 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     count_launch();
     const int blocks = grid;
     if (e0) cudaEventRecord(e0, st);
-    fwd_kernel<<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, gen, spin_limit);
+    if (P.lval32) fwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, gen, spin_limit);
+    else fwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, gen, spin_limit);
     count_launch();
-    bwd_kernel<<<blocks, WARPS * 32, 0, st>>>(P, P.dinv, d_z, d_xh, nrhs, gen, spin_limit);
+    if (P.lval32) bwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv32, d_z, d_xh, nrhs, gen, spin_limit);
+    else bwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv, d_z, d_xh, nrhs, gen, spin_limit);
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     permute_out_kernel<<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);
@@ -1024,9 +1124,11 @@ int launch_solve_transpose(const DevPlan& P, const double* d_b, double* d_x, dou
     if (cudaMemsetAsync(P.lt_done, 0, sizeof(int32_t) * P.n_lt_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     permute_in_t_kernel<<<eb, 256, 0, st>>>(P.n, P.piv, colperm, dc, d_b, d_h, nrhs, ld);
     count_launch();
-    ut_kernel<<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    if (P.lval32) ut_kernel<float><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    else ut_kernel<double><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
     count_launch();
-    lt_kernel<<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    if (P.lval32) lt_kernel<float><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    else lt_kernel<double><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
     count_launch();
     permute_out_t_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_h, d_x, nrhs, ld);
     count_launch();

@@ -28,6 +28,9 @@ struct DevPlan {
     const int64_t* node_panel_off; // nnodes + 1
     double* lval;                  // nnz_l   : L(i, position) values
     double* pval;                  // nnz_panel: per node s x (s + tail), block by label
+    float* lval32;                 // the same in FP32 (precision form), else null
+    float* pval32;
+    float* dinv32;
     const int64_t* ah_rp;          // n + 1 (rows of Ahat)
     const int32_t* ah_slot;
     const int64_t* ah_src;
