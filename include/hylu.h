@@ -71,6 +71,9 @@ typedef struct {
     int timing;            /* 1: time the factor and solve kernels with CUDA events     */
     int precision;         /* 0: FP64 factors; 1: FP32 factors (scaling and the small-pivot
                               check in FP64) with FP64 iterative refinement on every solve */
+    double heavy_ratio;    /* rows whose update work is at least heavy_ratio x the mean row (and
+                              at least 1e6 flops) are claimed first, from a queue of their own,
+                              by one warp in four; 0 disables (32) */
 } hylu_options;
 
 typedef struct {
@@ -93,6 +96,7 @@ typedef struct {
     double analyze_ms;
     double factor_kernel_ms; /* last factorization kernel (opt.timing = 1), else -1 */
     double solve_kernel_ms;  /* last substitution kernels (opt.timing = 1), else -1  */
+    int32_t nheavy;          /* rows the factor kernel claims first (see heavy_ratio) */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */

@@ -33,7 +33,8 @@ class Options(C.Structure):
                 ("sn_max", C.c_int), ("nd_leaf", C.c_int), ("pivot_tau", C.c_double),
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine", C.c_int),
                 ("spin_limit", C.c_longlong), ("rows_per_task", C.c_int), ("debug", C.c_int),
-                ("amd_dense", C.c_double), ("timing", C.c_int), ("precision", C.c_int)]
+                ("amd_dense", C.c_double), ("timing", C.c_int), ("precision", C.c_int),
+                ("heavy_ratio", C.c_double)]
 
 
 class Info(C.Structure):
@@ -44,7 +45,8 @@ class Info(C.Structure):
                 ("nperturb", C.c_int32), ("refine_iters", C.c_int32),
                 ("backward_error", C.c_double), ("device_status", C.c_int32),
                 ("failed_node", C.c_int32), ("analyze_ms", C.c_double),
-                ("factor_kernel_ms", C.c_double), ("solve_kernel_ms", C.c_double)]
+                ("factor_kernel_ms", C.c_double), ("solve_kernel_ms", C.c_double),
+                ("nheavy", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

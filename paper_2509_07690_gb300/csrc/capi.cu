@@ -97,6 +97,16 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     int32_t* ro;
     TRY(upload(h, &ro, P.row_order, st));
     d.row_order = ro;
+    d.n_heavy = (int32_t)P.heavy_order.size();
+    d.heavy_order = nullptr;
+    d.heavy_rank = nullptr;
+    if (d.n_heavy > 0) {
+        int32_t *ho, *hr;
+        TRY(upload(h, &ho, P.heavy_order, st));
+        TRY(upload(h, &hr, P.heavy_rank, st));
+        d.heavy_order = ho;
+        d.heavy_rank = hr;
+    }
     d.trace = nullptr;
     if (h->opt.debug & 2) TRY(dalloc(h, &d.trace, 4 * (size_t)P.n));
     d.lval = nullptr; d.pval = nullptr; d.lval32 = nullptr; d.pval32 = nullptr; d.dinv32 = nullptr;
@@ -156,6 +166,17 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
         d.node_base = nb;
     }
     TRY(dalloc(h, &d.pos, (size_t)h->grid_max * hylu::warps_per_block() * (size_t)d.pos_n));
+    d.spa64 = nullptr;
+    d.spa32 = nullptr;
+    {
+        int64_t max_nl = 0;
+        for (int32_t i = 0; i < P.n; ++i) max_nl = std::max<int64_t>(max_nl, P.row_lptr[i + 1] - P.row_lptr[i]);
+        if (max_nl > hylu::dense_l_min()) {
+            const size_t cnt = (size_t)h->grid_max * hylu::warps_per_block() * (size_t)d.pos_n;
+            if (h->opt.precision == 1) TRY(dalloc(h, &d.spa32, cnt));
+            else TRY(dalloc(h, &d.spa64, cnt));
+        }
+    }
     if (cudaMemsetAsync(d.ready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.fwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.bwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
@@ -340,6 +361,7 @@ int hylu_default_options(hylu_options* o) {
     o->amd_dense = 2.0;
     o->timing = 0;
     o->precision = 0;
+    o->heavy_ratio = 32.0;
     return HYLU_OK;
 }
 
@@ -352,6 +374,7 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
     if (opt) o = *opt; else hylu_default_options(&o);
     if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
     if (o.precision != 0 && o.precision != 1) return HYLU_ERR_ARG;
+    if (!(o.heavy_ratio >= 0.0)) return HYLU_ERR_ARG;
     if (o.precision == 1 && o.refine == 0) o.refine = 1;   // FP32 factors: always refine in FP64
     hylu_handle* h = new (std::nothrow) hylu_handle();
     if (!h) return HYLU_ERR_NOMEM;
@@ -363,6 +386,7 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
     ao.sn_max = o.sn_max;
     ao.nd_leaf = o.nd_leaf > 0 ? o.nd_leaf : 256;
     ao.amd_dense = o.amd_dense > 0 ? o.amd_dense : 2.0;
+    ao.heavy_ratio = o.heavy_ratio;
     int rc;
     try {
         rc = hylu::analyze(n, rowptr, col, vals, user_perm, ao, h->P);
@@ -423,6 +447,7 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->rows_in_supernodes = rs;
     info->max_supernode = mx;
     info->ntasks = P.n;
+    info->nheavy = (int32_t)P.heavy_order.size();
     info->flops = P.flops_unpadded;
     info->flops_padded = P.flops_padded;
     info->analyze_ms = P.analyze_ms;
@@ -525,6 +550,7 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
     if (opt) o = *opt; else hylu_default_options(&o);
     if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
     if (o.precision != 0 && o.precision != 1) return HYLU_ERR_ARG;
+    if (!(o.heavy_ratio >= 0.0)) return HYLU_ERR_ARG;
     if (o.precision == 1 && o.refine == 0) o.refine = 1;
     hylu::AnalyzeOptions ao;
     ao.ordering = o.ordering == HYLU_ORDER_USER ? HYLU_ORDER_AMD : o.ordering;
@@ -533,6 +559,7 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
     ao.sn_max = o.sn_max;
     ao.nd_leaf = o.nd_leaf > 0 ? o.nd_leaf : 256;
     ao.amd_dense = o.amd_dense > 0 ? o.amd_dense : 2.0;
+    ao.heavy_ratio = o.heavy_ratio;
     std::vector<hylu::Plan> plans(k);
     std::vector<int> rcs(k, 0);
     unsigned nt = std::max(1u, std::min<unsigned>(std::thread::hardware_concurrency(), (unsigned)k));
@@ -558,6 +585,7 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
     int rc;
     try {
         rc = hylu::combine(ps, nsets, h->P, h->layout);
+        if (rc == 0) hylu::split_heavy_rows(h->P, ao.heavy_ratio);
     } catch (const std::bad_alloc&) {
         rc = HYLU_ERR_NOMEM;
     }

@@ -42,6 +42,10 @@ struct Plan {
     // depends on the last row of each source node and on the earlier rows of
     // its own supernode), ties by row index
     std::vector<int32_t> row_order;
+    // heavy rows (see split_heavy_rows), by level, and each row's rank there
+    // (INT32_MAX for the others); the factor kernel claims the first ones from
+    // a queue of their own
+    std::vector<int32_t> heavy_order, heavy_rank;
     std::vector<int32_t> row_level;     // dependency level of every row
     int32_t row_levels = 0;
     // substitution schedules (bulk mode of Sec. 2.2.1 / 2.3): node levels of
@@ -65,6 +69,7 @@ struct AnalyzeOptions {
     int sn_max = 256;
     int nd_leaf = 256;
     double amd_dense = 2.0;
+    double heavy_ratio = 32.0; // rows with this many times the mean row work are claimed first (0: off)
 };
 
 // Batch of independent systems (Sec. 3.2 repeated solves, extended to many
@@ -82,6 +87,12 @@ int combine(const std::vector<const Plan*>& sys, int32_t nsets, Plan& C, BatchLa
 // Returns 0 or a negative hylu status code; fills P.
 int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
             const int32_t* user_perm, const AnalyzeOptions& opt, Plan& P);
+
+// Picks the heavy rows: update work >= heavy_ratio x the mean row (and >= 1e6
+// flops), of which at least half comes from sources at no more than half the
+// row's own dependency level.  Fills heavy_order / heavy_rank from the
+// level-ordered row_order.
+void split_heavy_rows(Plan& P, double heavy_ratio);
 
 void symbolic_rows(const CsrPattern& ahat, std::vector<int64_t>& frp, std::vector<int32_t>& fci,
                    std::vector<int64_t>& fdiag);

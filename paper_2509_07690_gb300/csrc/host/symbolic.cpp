@@ -255,4 +255,44 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
     row_schedule(P.lt_level, true, P.lt_order, P.lt_count);    // last row of a node first
 }
 
+// Rows whose own update work dwarfs the rest (the dense rows that AMD puts
+// last in circuit matrices) sit at the deepest levels, so level order would
+// claim them last although most of their sources finish early.  Claimed at
+// once, they consume those sources while the rest of the task graph is still
+// running (Sec. 2.2.1 pipeline mode).  A row qualifies only if it has that
+// early work: the prefix of its L list (taken in order, as the kernel does)
+// whose sources lie at no more than half its level carries at least half of
+// its flops.  Top separators of nested dissection fail the test: their
+// sources finish late, and claiming them early would only idle warps.
+void split_heavy_rows(Plan& P, double heavy_ratio) {
+    const int32_t n = P.n;
+    P.heavy_order.clear();
+    P.heavy_rank.assign(n, INT32_MAX);
+    if (!(heavy_ratio > 0.0) || n == 0) return;
+    double tot = 0.0;
+    for (double f : P.row_flops) tot += f;
+    const double cut = std::max(1e6, heavy_ratio * tot / (double)n);
+    std::vector<int32_t> ulen(n);
+    for (int32_t D = 0; D < P.nnodes; ++D) {
+        const int32_t nT = (int32_t)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+        for (int32_t i = P.sn_start[D]; i < P.sn_start[D + 1]; ++i) ulen[i] = (P.sn_start[D + 1] - i) + nT;
+    }
+    for (int32_t q = 0; q < n; ++q) {
+        const int32_t i = P.row_order[q];
+        if (P.row_flops[i] < cut) continue;
+        const int32_t lam = P.row_level[i] / 2;
+        double early = 0.0;
+        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) {
+            const int32_t k = P.lcols[t];
+            const int32_t eS = P.sn_start[P.node_of[k] + 1] - 1;
+            if (P.row_level[eS] > lam) break;
+            early += 1.0 + 2.0 * (double)(ulen[k] - 1);
+        }
+        if (early >= 0.5 * P.row_flops[i]) {
+            P.heavy_rank[i] = (int32_t)P.heavy_order.size();
+            P.heavy_order.push_back(i);
+        }
+    }
+}
+
 }  // namespace hylu

@@ -110,6 +110,9 @@ template <> __device__ __forceinline__ double* LV<double>(const DevPlan& P) { re
 template <> __device__ __forceinline__ double* PV<double>(const DevPlan& P) { return P.pval; }
 template <> __device__ __forceinline__ float* LV<float>(const DevPlan& P) { return P.lval32; }
 template <> __device__ __forceinline__ float* PV<float>(const DevPlan& P) { return P.pval32; }
+template <typename T> __device__ __forceinline__ T* SPA(const DevPlan& P);
+template <> __device__ __forceinline__ double* SPA<double>(const DevPlan& P) { return P.spa64; }
+template <> __device__ __forceinline__ float* SPA<float>(const DevPlan& P) { return P.spa32; }
 template <typename T> __device__ __forceinline__ T* DI(const DevPlan& P);
 template <> __device__ __forceinline__ double* DI<double>(const DevPlan& P) { return P.dinv; }
 template <> __device__ __forceinline__ float* DI<float>(const DevPlan& P) { return P.dinv32; }
@@ -118,8 +121,14 @@ template <> __device__ __forceinline__ float* DI<float>(const DevPlan& P) { retu
 // Per-warp shared memory of the factor kernel.
 constexpr int FWARPS = 4;          // warps per block of the factor kernel (one per SM sub-partition)
 constexpr int PANEL_BYTES = 4096;  // U part of the row being updated
-constexpr int PF = 4;              // leading tail entries prefetched per source
+constexpr int PF = 16;             // leading tail entries prefetched per source
 constexpr int UNR = 8;             // independent 32-entry batches in flight
+constexpr int UNR_TAIL = 8;        // the same for the tails of standalone sources
+constexpr int DENSE_L_MIN = 256;   // rows with longer L lists use the dense per-warp L vector
+#ifndef HYLU_HEAVY_WPB
+#define HYLU_HEAVY_WPB 2
+#endif
+constexpr int HEAVY_WPB = HYLU_HEAVY_WPB;   // warps of each block that drain the heavy-row queue first
 template <typename T>
 struct WarpSmem {
     T lb[SN_SMEM];            // source supernode: l by position
@@ -175,24 +184,25 @@ struct Panel {
 // before any update so that their latencies overlap.
 template <typename T>
 __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, const T* __restrict__ U1,
-                                           int j0, int nTS, T l, int r, const int* pos, T* xl,
+                                           int j0, int nTS, T l, int r, const int* pos, T* xl, T* spa,
                                            const Panel<T>& pn, int lane) {
-    for (int jb = j0; jb < nTS; jb += 32 * UNR) {
-        int c[UNR];
-        T u[UNR];
+    for (int jb = j0; jb < nTS; jb += 32 * UNR_TAIL) {
+        int c[UNR_TAIL];
+        T u[UNR_TAIL];
 #pragma unroll
-        for (int m = 0; m < UNR; ++m) {
+        for (int m = 0; m < UNR_TAIL; ++m) {
             const int j = jb + m * 32 + lane;
             c[m] = (j < nTS) ? __ldg(tcS + j) : -1;
-            u[m] = (j < nTS) ? __ldg(U1 + j) : T(0);
+            u[m] = (j < nTS) ? U1[j] : T(0);   // written in this launch: coherent loads
         }
-        int ix[UNR];
+        int ix[UNR_TAIL];
 #pragma unroll
-        for (int m = 0; m < UNR; ++m) ix[m] = (c[m] >= r) ? pn.idx(pos, c[m]) : ((c[m] >= 0) ? pos[c[m]] : -1);
+        for (int m = 0; m < UNR_TAIL; ++m)
+            ix[m] = (c[m] >= r) ? pn.idx(pos, c[m]) : ((c[m] >= 0 && !spa) ? pos[c[m]] : -1);
 #pragma unroll
-        for (int m = 0; m < UNR; ++m) {
+        for (int m = 0; m < UNR_TAIL; ++m) {
             if (c[m] < 0) continue;
-            if (c[m] < r) atomicAdd(xl + ix[m], -l * u[m]);
+            if (c[m] < r) atomicAdd(spa ? spa + c[m] : xl + ix[m], -l * u[m]);
             else pn.x[ix[m]] -= l * u[m];
         }
     }
@@ -212,13 +222,32 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
     int* pos_warp = P.pos + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.pos_n;
     const double amax = __longlong_as_double(*reinterpret_cast<const long long*>(P.status + ST_AMAX));
     const double tau = tau_rel * amax;
+    // Rows are claimed from two queues, each in dependency-level order.  The
+    // first hcap heavy rows form a queue of their own, taken only by the first
+    // HEAVY_WPB warps of each block (at most hcap rows, so they are all claimed
+    // at once); every other row comes from the level-ordered main queue, which
+    // skips those hcap rows.  Progress holds: a claimed row waits only on rows
+    // of lower levels, heavy-queue rows never wait to be claimed, and the main
+    // queue's warps hold only rows at or below the lowest unfinished level.
+    const int hcap = min(P.n_heavy, HEAVY_WPB * (int)gridDim.x);
+    bool heavy_open = (wid < HEAVY_WPB) && (hcap > 0);
     for (;;) {
-        int qi = 0;
-        if (lane == 0) qi = atomicAdd(P.status + ST_CNT_F, 1);
-        qi = __shfl_sync(FULL, qi, 0);
-        if (qi >= P.n) return;
+        int i = -1;
+        if (lane == 0) {
+            if (heavy_open) {
+                const int h = atomicAdd(P.status + ST_CNT_H, 1);
+                if (h < hcap) i = P.heavy_order[h]; else heavy_open = false;
+            }
+            while (i < 0) {
+                const int qi = atomicAdd(P.status + ST_CNT_F, 1);
+                if (qi >= P.n) { i = P.n; break; }
+                const int c = P.row_order[qi];
+                if (hcap == 0 || P.heavy_rank[c] >= hcap) i = c;
+            }
+        }
+        i = __shfl_sync(FULL, i, 0);
+        if (i >= P.n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
-        const int i = P.row_order[qi];
         if (P.trace && lane == 0) P.trace[4 * (int64_t)i] = gtimer();
         unsigned long long waited = 0;
         unsigned long long* wp = P.trace ? &waited : nullptr;
@@ -252,9 +281,15 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
         //      The first 32 L slots start in the shared-memory window; later
         //      L slots accumulate in global memory and are found through pos[]
         //      (also used by a panel kept in global memory).
-        const bool need_pos = (nL > 32) || (pn.mode == 2);
+        //      A row with a long L list keeps its pending L values in a dense
+        //      per-warp vector indexed by column instead (no slot lookup).
+        T* spa = (nL > DENSE_L_MIN && SPA<T>(P)) ? SPA<T>(P) + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.pos_n
+                                                      - (P.node_base ? P.node_base[D] : 0)
+                                                 : nullptr;
+        const bool need_pos = (!spa && nL > 32) || (pn.mode == 2);
         win[lane] = T(0);
-        for (int t = 32 + lane; t < nL; t += 32) xl[t] = T(0);
+        if (spa) { for (int t = 32 + lane; t < nL; t += 32) spa[lc[t]] = T(0); }
+        else     { for (int t = 32 + lane; t < nL; t += 32) xl[t] = T(0); }
         if (need_pos) for (int t = lane; t < nL; t += 32) pos[lc[t]] = t;
         for (int t = lane; t < range; t += 32) pn.x[t] = T(0);
         if (pn.mode == 1) {
@@ -268,7 +303,9 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
             // scaling in FP64, then rounded to the factor precision
             const T v = (T)(vals[P.ah_src[q]] * P.ah_scale[q]);
             if (sl < nL) {
-                if (sl < 32) win[sl] = v; else xl[sl] = v;
+                if (sl < 32) win[sl] = v;
+                else if (spa) spa[lc[sl]] = v;
+                else xl[sl] = v;
             } else {
                 const int us = sl - nL;
                 pn.x[us < s ? us : pn.tail_idx(tc, us - s)] = v;
@@ -302,7 +339,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
                         ws->pfu[lane][m] = (m < nTq) ? PV<T>(P)[pq0 + 1 + m] : T(0);
                     }
                 }
-                if (t > 0) win[lane] = xl[tq];
+                if (t > 0) win[lane] = spa ? spa[kq] : xl[tq];
                 wcol[lane] = kq;
             }
             const unsigned rmask = __ballot_sync(FULL, okq);
@@ -367,13 +404,16 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
                 if (pl >= nTS) continue;
                 const int64_t tS = __shfl_sync(FULL, tq0, qq);
                 const int64_t pS = __shfl_sync(FULL, pq0, qq);
-                apply_tail<T>(P.tcols + tS, PV<T>(P) + pS + 1, pl, nTS, win[qq], r, pos, xl, pn, lane);
+                apply_tail<T>(P.tcols + tS, PV<T>(P) + pS + 1, pl, nTS, win[qq], r, pos, xl, spa, pn, lane);
                 __syncwarp();
             }
             // any L slot past this window may have received atomic adds
             if (t + cend < nL) pending = true;
             // ---- close the window: multipliers (and untouched values) back to L
-            if (lane < cend) xl[tq] = win[lane];
+            if (lane < cend) {
+                xl[tq] = win[lane];
+                if (spa && qs < cend) spa[kq] = win[lane];   // the sup-row below reads by column
+            }
             __syncwarp();
             if (qs == cend) { t += cend; continue; }
             __threadfence();
@@ -398,7 +438,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
                 for (int p = lane; p < sS; p += 32) {
                     const int lab = P.piv[rS + p] - rS;
                     pb[p] = lab;
-                    lb[p] = xl[tt + lab];
+                    lb[p] = spa ? spa[rS + lab] : xl[tt + lab];
                 }
                 __syncwarp();
                 for (int p = 0; p < sS; ++p) {
@@ -412,18 +452,27 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
                 for (int j = lane; j < nTS; j += 32) {
                     const T* Uj = U + sS + j;
                     const int c = tcS[j];
-                    T acc0 = T(0), acc1 = T(0);
+                    // 8 independent accumulators: 8 loads of the column in flight
+                    T ac[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) ac[u] = T(0);
                     int p = 0;
-                    for (; p + 1 < sS; p += 2) {
-                        acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
-                        acc1 = fma(lb[p + 1], Uj[(int64_t)(p + 1) * wS], acc1);
+                    for (; p + 8 <= sS; p += 8) {
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) ac[u] = fma(lb[p + u], Uj[(int64_t)(p + u) * wS], ac[u]);
                     }
-                    if (p < sS) acc0 = fma(lb[p], Uj[(int64_t)p * wS], acc0);
+                    for (; p < sS; ++p) ac[0] = fma(lb[p], Uj[(int64_t)p * wS], ac[0]);
+                    const T acc0 = ((ac[0] + ac[1]) + (ac[2] + ac[3])) + ((ac[4] + ac[5]) + (ac[6] + ac[7]));
+                    const T acc1 = T(0);
                     if (c < r) {
                         // later L slot of this row: through pos[], or, for a row
                         // whose L list fits one window, among the window columns
-                        const int sl = need_pos ? pos[c] : t + bsearch_sm(wcol, cend, c);
-                        atomicAdd(xl + sl, -(acc0 + acc1));
+                        if (spa) {
+                            atomicAdd(spa + c, -(acc0 + acc1));
+                        } else {
+                            const int sl = need_pos ? pos[c] : t + bsearch_sm(wcol, cend, c);
+                            atomicAdd(xl + sl, -(acc0 + acc1));
+                        }
                     } else {
                         pn.x[pn.idx(pos, c)] -= acc0 + acc1;
                     }
@@ -1053,6 +1102,7 @@ static int check(const char* what) {
 }
 
 int warps_per_block() { return FWARPS; }
+int dense_l_min() { return DENSE_L_MIN; }
 
 int factor_grid(int device) {
     int sms = 0, per = 0;

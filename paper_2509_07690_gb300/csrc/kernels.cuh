@@ -14,8 +14,9 @@ namespace hylu {
 //   [6..7] max |Ahat| as the bit pattern of a non-negative double.
 //   [8..11] substitution: forward / backward claim counters, forward /
 //   backward level watermarks (levels whose nodes are all complete).
+//   [12] task counter of the factor kernel's heavy-row queue.
 enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_AMAX = 6, ST_CNT_FWD = 8,
-       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_WORDS = 12 };
+       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_CNT_H = 12, ST_WORDS = 14 };
 
 struct DevPlan {
     int32_t n, nnodes;
@@ -63,8 +64,13 @@ struct DevPlan {
     int32_t* pos;                  // per-warp column -> slot maps, pos_n each
     int32_t pos_n;                 // largest system of the plan (n for one system)
     const int32_t* node_base;      // per node: first row of its instance (null = 0)
+    double* spa64;                 // per-warp dense L vectors (pos_n each) for long L lists,
+    float* spa32;                  // in the factor precision; null when no row needs one
     double* dinv;                  // 1 / u_ii by position (row)
     const int32_t* row_order;      // claim order of the factor kernel (by level)
+    const int32_t* heavy_order;    // heavy rows by level (claimed first), null if none
+    const int32_t* heavy_rank;     // per row: rank in heavy_order, INT32_MAX if not heavy
+    int32_t n_heavy;
     unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, warp<<8|mode)
     int32_t* status;
 };
@@ -90,6 +96,7 @@ int launch_axpy(int32_t n, double* x, const double* d, int nrhs, int ld, cudaStr
 int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t n, cudaStream_t st);
 int factor_grid(int device);   // blocks of the persistent kernels
 int warps_per_block();
+int dense_l_min();
 int64_t launches();
 int measure_fp64_peak(double* gflops, cudaStream_t st);
 void count_launch();

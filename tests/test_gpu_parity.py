@@ -91,9 +91,11 @@ def test_random_dense_blocks(seed):
     run_case(synth.from_coo(n, r, c, a[r, c]))
 
 
-def test_circuit_20k_heavy_rows():
-    """Hub rows land in the heavy queue (panel in the large shared buffer)."""
-    run_case(synth.circuit(20000, seed=77))
+@pytest.mark.parametrize("heavy_ratio", [0.0, 32.0, 1.0])
+def test_circuit_20k_heavy_rows(heavy_ratio):
+    """Hub rows with long L lists (dense per-warp L vector); with a ratio > 0
+    they are claimed first from the heavy-row queue."""
+    run_case(synth.circuit(20000, seed=77), heavy_ratio=heavy_ratio)
 
 
 def test_dense_600_one_heavy_panel():

@@ -186,3 +186,27 @@ def test_error_codes():
         capi.hylu_solve(h, 1, 1, 1, A.n, 0)
     assert e.value.code == -7
     capi.hylu_destroy(h)
+
+
+# ------------------------------------------------- heavy-row claim queue
+def test_heavy_rows_selection():
+    """Circuit hub rows (dense rows ordered last, most sources finished early)
+    are picked for the factor kernel's heavy-row queue; nested-dissection top
+    separators (sources finishing late) are not; ratio 0 switches it off and a
+    smaller ratio never picks fewer rows."""
+    A = synth.circuit(20000, seed=77)
+    counts = {}
+    for r in (0.0, 1.0, 32.0):
+        s = Solver(A.n, A.rowptr, A.col, A.val, heavy_ratio=r)
+        counts[r] = s.get_info().nheavy
+        s.close()
+    assert counts[0.0] == 0
+    assert counts[32.0] > 0
+    assert counts[1.0] >= counts[32.0]
+    B = synth.convdiff3d(16)
+    s = Solver(B.n, B.rowptr, B.col, B.val, ordering=1)
+    assert s.get_info().nheavy == 0
+    s.close()
+    with pytest.raises(capi.HyluError) as e:
+        capi.hylu_analyze(A.n, A.rowptr, A.col, A.val, None, capi.default_options(heavy_ratio=-1.0))
+    assert e.value.code == -1
