@@ -73,7 +73,7 @@ typedef struct {
                               check in FP64) with FP64 iterative refinement on every solve */
     double heavy_ratio;    /* rows whose update work is at least heavy_ratio x the mean row (and
                               at least 1e6 flops) are claimed first, from a queue of their own,
-                              by one warp in four; 0 disables (32) */
+                              by the warps of a subset of the SMs; 0 disables (32) */
 } hylu_options;
 
 typedef struct {
@@ -85,7 +85,7 @@ typedef struct {
     int32_t nsupernodes;    /* nodes of more than one row                   */
     int32_t rows_in_supernodes;
     int32_t max_supernode;
-    int32_t ntasks;
+    int32_t ntasks;         /* tasks of the factor kernel: rows plus supernode tail tasks */
     double flops;           /* unpadded symbolic flop count (Sec. 2.1)      */
     double flops_padded;    /* flops on the padded pattern                  */
     int32_t nperturb;       /* perturbed pivots of the last factorization   */
@@ -244,8 +244,11 @@ int hylu_solve_static(hylu_handle* h, const double* d_b, double* d_x, void* stre
 /* Diagnostics: when the handle was analysed with (opt.debug & 2), copy the
  * per-row trace of the last factorization to the HOST array out[4 * n]:
  * for row i, out[4i] = claim time, out[4i+1] = updates from earlier nodes
- * done, out[4i+2] = published (ns, %globaltimer), out[4i+3] = (warp << 8) |
- * panel mode.  HYLU_ERR_STATE when tracing is off. */
+ * done, out[4i+2] = published (a supernode row with a U tail: its
+ * diagonal-block step published), all in ns of %globaltimer; out[4i+3] =
+ * for the last row of a supernode with a U tail, the time its tail tasks
+ * completed the node, else (ns waited on other nodes << 32) | ns waited on
+ * the own supernode.  HYLU_ERR_STATE when tracing is off. */
 int hylu_debug_trace(hylu_handle* h, unsigned long long* out);
 
 /* Number of kernel launches this library has issued since it was loaded. */

@@ -33,7 +33,6 @@ struct hylu_handle {
     double* d_colsum = nullptr;
     double* h_norms = nullptr;   // pinned
     int32_t* h_status = nullptr; // pinned
-    int32_t gen_factor = 0, gen_solve = 0;
     int grid = 0;
     cudaStream_t last = nullptr;
     int32_t nperturb = 0, refine_iters = 0, device_status = 0, failed_node = -1;
@@ -121,6 +120,18 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     TRY(dalloc(h, &d.piv, P.n));
     TRY(dalloc(h, &d.pinv, P.n));
     TRY(dalloc(h, &d.ready, P.n));
+    TRY(dalloc(h, &d.dready, P.n));
+    TRY(dalloc(h, &d.gens, 2));
+    if (cudaMemsetAsync(d.gens, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    TRY(dalloc(h, &d.node_done, std::max<int32_t>(1, P.nnodes)));
+    d.n_tasks = P.n_tasks;
+    {
+        int32_t *tn, *tch, *nnt;
+        TRY(upload(h, &nnt, P.node_ntask, st));
+        TRY(upload(h, &tn, P.task_node, st));
+        TRY(upload(h, &tch, P.task_chunk, st));
+        d.node_ntask = nnt; d.task_node = tn; d.task_chunk = tch;
+    }
     {
         int32_t *fo, *bo, *fl, *bl, *fc, *bc;
         TRY(upload(h, &fo, P.fwd_order, st));
@@ -178,6 +189,7 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
         }
     }
     if (cudaMemsetAsync(d.ready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(d.dready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.fwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.bwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     TRY(dalloc(h, &h->d_avals, P.nnz_a));
@@ -227,9 +239,8 @@ int do_factor(hylu_handle* h, const double* d_vals, cudaStream_t st) {
     TRY(ensure_uploaded(h, st));
     if (cudaMemcpyAsync(h->d_avals, d_vals, sizeof(double) * h->P.nnz_a, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return HYLU_ERR_CUDA;
-    TRY(hylu::launch_reset(h->dp.status, h->dp.piv, h->dp.pinv, h->P.n, st));
-    ++h->gen_factor;
-    TRY(hylu::launch_factor(h->dp, h->d_avals, h->P.nnz_a, h->gen_factor, h->opt.pivot_tau,
+    TRY(hylu::launch_reset(h->dp.status, h->dp.piv, h->dp.pinv, h->dp.gens, h->P.n, st));
+    TRY(hylu::launch_factor(h->dp, h->d_avals, h->P.nnz_a, h->opt.pivot_tau,
                             h->opt.spin_limit, h->grid, st, h->opt.timing ? h->ev[0] : nullptr,
                             h->opt.timing ? h->ev[1] : nullptr));
     if (h->opt.timing) h->timed_factor = true;
@@ -260,9 +271,8 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
     // no refinement and no synchronization (the call stays asynchronous).
     if (h->opt.refine >= 0) TRY(read_status(h, st));
     hylu::DevPlan& P = h->dp;
-    ++h->gen_solve;
     TRY(hylu::launch_solve(P, d_b, d_x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
-                           nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st,
+                           nrhs, ld, h->opt.spin_limit, h->grid, st,
                            h->opt.timing ? h->ev[2] : nullptr, h->opt.timing ? h->ev[3] : nullptr));
     if (h->opt.timing) h->timed_solve = true;
     h->refine_iters = 0;
@@ -282,9 +292,8 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
         if (be <= h->opt.refine_tol) return HYLU_OK;
         if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
         be_prev = be;
-        ++h->gen_solve;
-        TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
-                               h->d_dc, nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st));
+            TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
+                               h->d_dc, nrhs, ld, h->opt.spin_limit, h->grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
         ++h->refine_iters;
     }
@@ -297,9 +306,8 @@ int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs,
     TRY(ensure_rhs(h, nrhs, ld));
     TRY(read_status(h, st));
     hylu::DevPlan& P = h->dp;
-    ++h->gen_solve;
     TRY(hylu::launch_solve_transpose(P, d_b, d_x, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc, nrhs, ld,
-                                     h->gen_solve, h->opt.spin_limit, h->grid, st));
+                                     h->opt.spin_limit, h->grid, st));
     h->refine_iters = 0;
     h->backward_error = -1.0;
     h->last = st;
@@ -316,9 +324,8 @@ int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs,
         if (be <= h->opt.refine_tol) return HYLU_OK;
         if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
         be_prev = be;
-        ++h->gen_solve;
-        TRY(hylu::launch_solve_transpose(P, h->d_r, h->d_d, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
-                                         nrhs, ld, h->gen_solve, h->opt.spin_limit, h->grid, st));
+            TRY(hylu::launch_solve_transpose(P, h->d_r, h->d_d, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
+                                         nrhs, ld, h->opt.spin_limit, h->grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
         ++h->refine_iters;
     }
@@ -334,10 +341,9 @@ int32_t handle_n(const hylu_handle* h) { return h->P.n; }
 
 int solve_into(hylu_handle* h, const double* d_b, double* d_x, double* z, double* xh, cudaStream_t st) {
     if (!h->factored || !h->uploaded) return HYLU_ERR_STATE;
-    ++h->gen_solve;
     h->last = st;
     return launch_solve(h->dp, d_b, d_x, z, xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc, 1, h->P.n,
-                        h->gen_solve, h->opt.spin_limit, h->grid, st);
+                        h->opt.spin_limit, h->grid, st);
 }
 }  // namespace hylu
 
@@ -446,7 +452,7 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->nsupernodes = ns;
     info->rows_in_supernodes = rs;
     info->max_supernode = mx;
-    info->ntasks = P.n;
+    info->ntasks = P.n + P.n_tasks;
     info->nheavy = (int32_t)P.heavy_order.size();
     info->flops = P.flops_unpadded;
     info->flops_padded = P.flops_padded;

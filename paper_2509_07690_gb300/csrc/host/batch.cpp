@@ -130,19 +130,31 @@ int combine(const std::vector<const Plan*>& sys, int32_t nsets, Plan& C, BatchLa
     }
     C.sn_start.push_back(C.n);
     C.node_panel_off.push_back(p_off);
-    // claim orders, merged level by level across instances
+    // claim orders, merged level by level across instances: rows keep their
+    // instance's levels; tail tasks (entry C.n + t) come first inside a level
     {
-        std::vector<const std::vector<int32_t>*> rl;
-        std::vector<std::vector<int32_t>> row_levels_as_nodes(Q);
-        // factor: per-row levels -> treat each row as a "node" of one row
         int32_t ml = 0;
         for (size_t q = 0; q < Q; ++q) ml = std::max(ml, inst[q]->row_levels);
+        C.node_ntask.clear();
+        C.task_node.clear();
+        C.task_chunk.clear();
+        C.task_level.clear();
+        for (size_t q = 0; q < Q; ++q) {
+            const Plan& P = *inst[q];
+            C.node_ntask.insert(C.node_ntask.end(), P.node_ntask.begin(), P.node_ntask.end());
+            append_shifted<int32_t>(C.task_node, P.task_node, 0, P.task_node.size(), nbase[q]);
+            C.task_chunk.insert(C.task_chunk.end(), P.task_chunk.begin(), P.task_chunk.end());
+            C.task_level.insert(C.task_level.end(), P.task_level.begin(), P.task_level.end());
+        }
+        C.n_tasks = (int32_t)C.task_node.size();
         std::vector<int64_t> start(ml + 2, 0);
+        for (int32_t t = 0; t < C.n_tasks; ++t) start[C.task_level[t] + 1]++;
         for (size_t q = 0; q < Q; ++q)
             for (int32_t i = 0; i < inst[q]->n; ++i) start[inst[q]->row_level[i] + 1]++;
         for (int32_t l = 0; l <= ml; ++l) start[l + 1] += start[l];
-        C.row_order.assign(C.n, 0);
+        C.row_order.assign((size_t)C.n + C.n_tasks, 0);
         C.row_level.assign(C.n, 0);
+        for (int32_t t = 0; t < C.n_tasks; ++t) C.row_order[start[C.task_level[t]]++] = C.n + t;
         for (size_t q = 0; q < Q; ++q)
             for (int32_t i = 0; i < inst[q]->n; ++i) {
                 const int32_t l = inst[q]->row_level[i];

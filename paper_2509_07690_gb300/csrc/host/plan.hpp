@@ -38,9 +38,17 @@ struct Plan {
     int64_t nnz_l = 0, nnz_panel = 0, nnz_store = 0, nnz_f = 0;
     double flops_unpadded = 0.0, flops_padded = 0.0;
     std::vector<double> row_flops;      // padded flops of each row
-    // claim order of the factor kernel: rows sorted by dependency level (a row
-    // depends on the last row of each source node and on the earlier rows of
-    // its own supernode), ties by row index
+    // tail tasks of the in-supernode step (Sec. 2.2, the triangular solve of
+    // a supernode's U tail by its unit lower diagonal block): a supernode with
+    // s > 1 rows and a tail gets node_ntask[D] tasks; task t solves the 32-column
+    // groups task_chunk[t], + node_ntask, ... of node task_node[t]
+    std::vector<int32_t> node_ntask, task_node, task_chunk, task_level;
+    int32_t n_tasks = 0;
+    // claim order of the factor kernel: rows (entries < n) and tail tasks
+    // (entry n + t) sorted by dependency level.  A row depends on its source
+    // nodes being complete (last row, or the node's tail tasks) and on the
+    // diagonal-block step of the earlier rows of its own supernode; a tail
+    // task on the diagonal-block step of its node's last row.
     std::vector<int32_t> row_order;
     // heavy rows (see split_heavy_rows), by level, and each row's rank there
     // (INT32_MAX for the others); the factor kernel claims the first ones from

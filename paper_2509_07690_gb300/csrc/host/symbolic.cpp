@@ -150,29 +150,57 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
     P.flops_unpadded = fu;
     P.flops_padded = fp;
     P.nnz_f = frp[n];
-    // dependency levels (Sec. 2.2.1: the task graph is levelized so that rows
-    // of one level are independent); claiming rows level by level keeps the
-    // claimed rows close to ready
+    // tail tasks: a 32-column group costs s^2 / 2 multiply-adds per lane; a
+    // task takes about 512 of them (one group from s = 32 up), at most one
+    // task per group
+    P.node_ntask.assign(nn, 0);
+    for (int32_t D = 0; D < nn; ++D) {
+        const int64_t sz = P.sn_start[D + 1] - P.sn_start[D];
+        const int64_t nT = P.node_tail_off[D + 1] - P.node_tail_off[D];
+        if (sz < 2 || nT == 0) continue;
+        const int64_t ng = (nT + 31) / 32;
+        const int64_t want = (sz * sz * ng + 1023) / 1024;
+        P.node_ntask[D] = (int32_t)std::max<int64_t>(1, std::min<int64_t>(want, ng));
+    }
+    // dependency levels (Sec. 2.2.1: the task graph is levelized so that tasks
+    // of one level are independent); claiming level by level keeps the claimed
+    // tasks close to ready
     std::vector<int32_t> lev(n, 0);
+    auto done_level = [&](int32_t S) {
+        return lev[P.sn_start[S + 1] - 1] + (P.node_ntask[S] > 0 ? 1 : 0);
+    };
     int32_t maxl = 0;
     for (int32_t i = 0; i < n; ++i) {
         const int32_t D = P.node_of[i], r = P.sn_start[D];
         int32_t l = (i > r) ? lev[i - 1] + 1 : 0;
         for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
             const int32_t S = P.node_of[P.lcols[t]];
-            const int32_t eS = P.sn_start[S + 1] - 1;
-            l = std::max(l, lev[eS] + 1);
+            l = std::max(l, done_level(S) + 1);
             t += P.sn_start[S + 1] - P.sn_start[S];   // whole segment of S
         }
         lev[i] = l;
         maxl = std::max(maxl, l);
     }
+    P.task_node.clear();
+    P.task_chunk.clear();
+    P.task_level.clear();
+    for (int32_t D = 0; D < nn; ++D)
+        for (int32_t c = 0; c < P.node_ntask[D]; ++c) {
+            P.task_node.push_back(D);
+            P.task_chunk.push_back(c);
+            P.task_level.push_back(done_level(D));
+            maxl = std::max(maxl, done_level(D));
+        }
+    P.n_tasks = (int32_t)P.task_node.size();
     P.row_levels = maxl + 1;
     P.row_level = lev;
+    // tasks first inside a level: they complete nodes and never wait long
     std::vector<int32_t> cnt(maxl + 2, 0);
     for (int32_t i = 0; i < n; ++i) cnt[lev[i] + 1]++;
+    for (int32_t t = 0; t < P.n_tasks; ++t) cnt[P.task_level[t] + 1]++;
     for (int32_t l = 0; l <= maxl; ++l) cnt[l + 1] += cnt[l];
-    P.row_order.assign(n, 0);
+    P.row_order.assign((size_t)n + P.n_tasks, 0);
+    for (int32_t t = 0; t < P.n_tasks; ++t) P.row_order[cnt[P.task_level[t]]++] = n + t;
     for (int32_t i = 0; i < n; ++i) P.row_order[cnt[lev[i]]++] = i;
 
     // ---- substitution schedules
@@ -277,9 +305,9 @@ void split_heavy_rows(Plan& P, double heavy_ratio) {
         const int32_t nT = (int32_t)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
         for (int32_t i = P.sn_start[D]; i < P.sn_start[D + 1]; ++i) ulen[i] = (P.sn_start[D + 1] - i) + nT;
     }
-    for (int32_t q = 0; q < n; ++q) {
+    for (size_t q = 0; q < P.row_order.size(); ++q) {
         const int32_t i = P.row_order[q];
-        if (P.row_flops[i] < cut) continue;
+        if (i >= n || P.row_flops[i] < cut) continue;
         const int32_t lam = P.row_level[i] / 2;
         double early = 0.0;
         for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) {

@@ -53,6 +53,12 @@ __device__ __forceinline__ void st_release(int* p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
+    int old;
+    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // All lanes wait (bounded) until *flag == gen.  Returns false when the limit
 // expired or another warp already raised an error; the first expiry records
 // HYLU_ERR_DEVICE_TIMEOUT and the row/node waited on.
@@ -83,7 +89,8 @@ __device__ __forceinline__ bool warp_wait(const int* flag, int gen, int* status,
 }
 
 // -------------------------------------------------------------- reset
-__global__ void reset_kernel(int32_t* piv, int32_t* pinv, int32_t n) {
+__global__ void reset_kernel(int32_t* piv, int32_t* pinv, int32_t n, int32_t* gens) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) gens[0] += 1;   // factor generation of this call
     for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         piv[i] = i;
         pinv[i] = i;
@@ -125,10 +132,6 @@ constexpr int PF = 16;             // leading tail entries prefetched per source
 constexpr int UNR = 8;             // independent 32-entry batches in flight
 constexpr int UNR_TAIL = 8;        // the same for the tails of standalone sources
 constexpr int DENSE_L_MIN = 256;   // rows with longer L lists use the dense per-warp L vector
-#ifndef HYLU_HEAVY_WPB
-#define HYLU_HEAVY_WPB 2
-#endif
-constexpr int HEAVY_WPB = HYLU_HEAVY_WPB;   // warps of each block that drain the heavy-row queue first
 template <typename T>
 struct WarpSmem {
     T lb[SN_SMEM];            // source supernode: l by position
@@ -208,10 +211,94 @@ __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, cons
     }
 }
 
+// Tail task of a supernode (the in-supernode step, Sec. 2.2).  Once the
+// node's diagonal block is factored (every row's pivot and multipliers
+// known), its U tail is U_T = L_DD^-1 X_T: X_T the rows' tails after the
+// updates from earlier nodes, L_DD the unit lower multipliers by position
+// (row q keeps l_qk at the label of position k).  Lanes own tail columns and
+// hold a block of rows of their column in registers: first the finished rows above
+// the block (8 at a time, multipliers staged in shared memory), then the
+// triangle inside the block, so every entry takes its updates in ascending k
+// as in the row-by-row elimination.  The last task of the node publishes it.
 template <typename T>
-__global__ void __launch_bounds__(FWARPS * 32)
-factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, int gen,
+__device__ __noinline__ bool tail_task(const DevPlan& P, int t, int gen, long long limit, WarpSmem<T>* ws, int lane) {
+    const int D = P.task_node[t];
+    const int nck = P.node_ntask[D];
+    const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+    const int nT = (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+    const int64_t w = s + nT;
+    const T* Ub = PV<T>(P) + P.node_panel_off[D];
+    T* Uw = PV<T>(P) + P.node_panel_off[D];
+    if (!warp_wait(P.dready + e, gen, P.status, e, limit)) return false;
+    int* pb = ws->pb;
+    // rows per register block (16 keeps the task within the kernel's 128
+    // registers); RB x RB staging area: the prefetch buffers and the panel,
+    // unused here
+    constexpr int RB = 16;
+    T* Ls = reinterpret_cast<T*>(&ws->pfu[0][0]);
+    static_assert(sizeof(ws->pfu) + PANEL_BYTES >= RB * RB * sizeof(T), "staging area");
+    for (int q = lane; q < s; q += 32) pb[q] = P.piv[r + q] - r;
+    __syncwarp();
+    for (int g = P.task_chunk[t]; g * 32 < nT; g += nck) {
+        const int j = g * 32 + lane;
+        const bool on = j < nT;
+        T* col = Uw + s + (on ? j : 0);
+        for (int q0 = 0; q0 < s; q0 += RB) {
+            const int m = min(RB, s - q0);
+            T x[RB];
+#pragma unroll
+            for (int u = 0; u < RB; ++u) x[u] = (on && u < m) ? col[(int64_t)(q0 + u) * w] : T(0);
+            for (int k0 = 0; k0 < q0; k0 += 8) {
+                __syncwarp();
+                for (int idx = lane; idx < 8 * RB; idx += 32) {
+                    const int kk = idx / RB, u = idx % RB;
+                    Ls[idx] = (u < m) ? Ub[(int64_t)(q0 + u) * w + pb[k0 + kk]] : T(0);
+                }
+                T uk[8];
+#pragma unroll
+                for (int kk = 0; kk < 8; ++kk) uk[kk] = on ? col[(int64_t)(k0 + kk) * w] : T(0);
+                __syncwarp();
+#pragma unroll
+                for (int u = 0; u < RB; ++u) {
+                    if (u >= m) break;   // m is the same in every lane
+#pragma unroll
+                    for (int kk = 0; kk < 8; ++kk) x[u] -= Ls[kk * RB + u] * uk[kk];
+                }
+            }
+            __syncwarp();
+            for (int idx = lane; idx < RB * RB; idx += 32) {
+                const int u = idx / RB, v = idx % RB;
+                Ls[idx] = (v < u && u < m) ? Ub[(int64_t)(q0 + u) * w + pb[q0 + v]] : T(0);
+            }
+            __syncwarp();
+#pragma unroll
+            for (int u = 1; u < RB; ++u) {
+                if (u >= m) break;
+                T a = x[u];
+#pragma unroll
+                for (int v = 0; v < u; ++v) a -= Ls[u * RB + v] * x[v];
+                x[u] = a;
+            }
+#pragma unroll
+            for (int u = 0; u < RB; ++u)
+                if (on && u < m) col[(int64_t)(q0 + u) * w] = x[u];
+        }
+    }
+    __threadfence();
+    __syncwarp();
+    if (lane == 0 && atom_add_acq_rel(P.node_done + D, 1) == nck - 1) {
+        for (int k = r; k <= e; ++k) st_release(P.ready + k, gen);
+        if (P.trace) P.trace[4 * (int64_t)e + 3] = gtimer();   // node complete
+    }
+    __syncwarp();
+    return true;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(FWARPS * 32, 4)
+factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
               double tau_rel, long long limit) {
+    const int gen = P.gens[0];
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem<T>* ws = reinterpret_cast<WarpSmem<T>*>(smem_raw) + wid;
@@ -223,14 +310,20 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
     const double amax = __longlong_as_double(*reinterpret_cast<const long long*>(P.status + ST_AMAX));
     const double tau = tau_rel * amax;
     // Rows are claimed from two queues, each in dependency-level order.  The
-    // first hcap heavy rows form a queue of their own, taken only by the first
-    // HEAVY_WPB warps of each block (at most hcap rows, so they are all claimed
-    // at once); every other row comes from the level-ordered main queue, which
-    // skips those hcap rows.  Progress holds: a claimed row waits only on rows
-    // of lower levels, heavy-queue rows never wait to be claimed, and the main
-    // queue's warps hold only rows at or below the lowest unfinished level.
-    const int hcap = min(P.n_heavy, HEAVY_WPB * (int)gridDim.x);
-    bool heavy_open = (wid < HEAVY_WPB) && (hcap > 0);
+    // heavy rows form a queue of their own, served by every warp of a subset
+    // of the SMs sized to hold them all at once (at most half of the SMs), so
+    // that their FP64 work does not share pipes with the dependency chain the
+    // other SMs run; every other row comes from the level-ordered main queue,
+    // which skips the heavy rows.  Progress holds: a claimed row waits only on
+    // rows of lower levels, and the lowest-level unfinished row is either
+    // claimed, or next in its queue, whose claimed rows are all ready.
+    unsigned smid, nsmid;
+    asm("mov.u32 %0, %%smid;" : "=r"(smid));
+    asm("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
+    const int64_t nwarps = (int64_t)gridDim.x * FWARPS;
+    const int64_t hsm = min((int64_t)nsmid / 2, ((int64_t)P.n_heavy * nsmid + nwarps - 1) / nwarps);
+    bool heavy_open = (P.n_heavy > 0) && ((int64_t)smid < hsm);
+    const int hcap = P.n_heavy;
     for (;;) {
         int i = -1;
         if (lane == 0) {
@@ -240,14 +333,18 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
             }
             while (i < 0) {
                 const int qi = atomicAdd(P.status + ST_CNT_F, 1);
-                if (qi >= P.n) { i = P.n; break; }
+                if (qi >= P.n + P.n_tasks) { i = INT_MAX; break; }
                 const int c = P.row_order[qi];
-                if (hcap == 0 || P.heavy_rank[c] >= hcap) i = c;
+                if (c >= P.n || hcap == 0 || P.heavy_rank[c] >= hcap) i = c;
             }
         }
         i = __shfl_sync(FULL, i, 0);
-        if (i >= P.n) return;
+        if (i == INT_MAX) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
+        if (i >= P.n) {
+            if (!tail_task<T>(P, i - P.n, gen, limit, ws, lane)) return;
+            continue;
+        }
         if (P.trace && lane == 0) P.trace[4 * (int64_t)i] = gtimer();
         unsigned long long waited = 0;
         unsigned long long* wp = P.trace ? &waited : nullptr;
@@ -486,31 +583,29 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
         }
         if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 1] = gtimer();
         const unsigned long long waited_ext = waited;
+        const bool has_tasks = (s > 1) && (nT > 0);
+        if (has_tasks && pn.mode != 2) {
+            // the tail leaves the row here (the tail tasks finish it)
+            for (int j = lane; j < nT; j += 32) xu[s + j] = pn.x[pn.tail_idx(tc, j)];
+        }
+        // the diagonal block (by label) of the row: lb for a supernode row,
+        // the panel (one entry) for a standalone row
+        T* xd = (s > 1) ? lb : pn.x;
         if (s > 1) {
-            // ---- earlier rows of the own supernode, each as soon as it is ready
+            for (int c = lane; c < s; c += 32) lb[c] = pn.x[c];
+            __syncwarp();
+            // ---- diagonal-block step: earlier rows of the own supernode, each
+            //      as soon as its own diagonal-block step is published
             const T* Ub = PV<T>(P) + P.node_panel_off[D];
             for (int k = r; k < i; ++k) {
-                if (!warp_wait(P.ready + k, gen, P.status, k, limit, wp)) return;
+                if (!warp_wait(P.dready + k, gen, P.status, k, limit, wp)) return;
                 const int lab = ld_relaxed(P.piv + k) - r;
                 const T* Uk = Ub + (int64_t)(k - r) * w;
-                const T l = pn.x[lab] * dinv[k];
+                const T l = lb[lab] * dinv[k];
                 for (int c = lane; c < s; c += 32)
-                    if (c != lab && ld_relaxed(P.pinv + r + c) > k) pn.x[c] -= l * Uk[c];
-                for (int jb = 0; jb < nT; jb += 32 * UNR) {
-                    T u[UNR];
-                    int ix[UNR];
-#pragma unroll
-                    for (int m = 0; m < UNR; ++m) {
-                        const int j = jb + m * 32 + lane;
-                        u[m] = (j < nT) ? Uk[s + j] : T(0);
-                        ix[m] = (j < nT) ? pn.tail_idx(tc, j) : -1;
-                    }
-#pragma unroll
-                    for (int m = 0; m < UNR; ++m)
-                        if (ix[m] >= 0) pn.x[ix[m]] -= l * u[m];
-                }
+                    if (c != lab && ld_relaxed(P.pinv + r + c) > k) lb[c] -= l * Uk[c];
                 __syncwarp();
-                if (lane == 0) pn.x[lab] = l;
+                if (lane == 0) lb[lab] = l;
                 __syncwarp();
             }
             // ---- supernode diagonal pivoting: largest |x| among positions i..e,
@@ -518,7 +613,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
             double best = -1.0;
             int bp = i;
             for (int p = i + lane; p <= e; p += 32) {
-                const double a = fabs((double)pn.x[P.piv[p] - r]);
+                const double a = fabs((double)lb[P.piv[p] - r]);
                 if (a > best) { best = a; bp = p; }
             }
             for (int off = 16; off; off >>= 1) {
@@ -538,22 +633,32 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
         if (lane == 0) {
             const int dl = (s > 1) ? (P.piv[i] - r) : 0;
             // the small-pivot check is taken in FP64 whatever the factor precision
-            double u = (double)pn.x[dl];
+            double u = (double)xd[dl];
             if (fabs(u) < tau) {
                 u = (u >= 0.0) ? tau : -tau;
-                pn.x[dl] = (T)u;
+                xd[dl] = (T)u;
                 atomicAdd(P.status + ST_NPERT, 1);
             }
-            dinv[i] = (T)(1.0 / (double)pn.x[dl]);
+            dinv[i] = (T)(1.0 / (double)xd[dl]);
         }
         __syncwarp();
-        // ---- write the U part back from shared memory, publish
-        if (pn.mode != 2) {
+        // ---- write the row back, publish
+        if (s > 1) {
+            for (int c = lane; c < s; c += 32) xu[c] = lb[c];
+            if (!has_tasks && pn.mode != 2)
+                for (int j = lane; j < nT; j += 32) xu[s + j] = pn.x[pn.tail_idx(tc, j)];
+        } else if (pn.mode != 2) {
             for (int c = lane; c < s; c += 32) xu[c] = pn.x[c];
             for (int j = lane; j < nT; j += 32) xu[s + j] = pn.x[pn.tail_idx(tc, j)];
         }
         __threadfence();
         __syncwarp();
+        if (s > 1 && lane == 0) st_release(P.dready + i, gen);
+        if (has_tasks) {
+            // trace word 3 of such a row: when its node completed (tail tasks)
+            if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 2] = gtimer();
+            continue;   // the node's last tail task publishes the row
+        }
         if (lane == 0) st_release(P.ready + i, gen);
         if (P.trace && lane == 0) {
             P.trace[4 * (int64_t)i + 2] = gtimer();
@@ -565,7 +670,8 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv, 
 // -------------------------------------------------------------- solve
 __global__ void permute_in_kernel(int32_t n, const int32_t* __restrict__ rowperm,
                                   const double* __restrict__ dr, const double* __restrict__ b,
-                                  double* __restrict__ bh, int nrhs, int ld) {
+                                  double* __restrict__ bh, int nrhs, int ld, int32_t* gens) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) gens[1] += 1;   // substitution generation of this call
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n * nrhs;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(q / n), i = (int)(q % n);
@@ -646,11 +752,6 @@ __device__ __forceinline__ bool wait_level(const int* wm, int need, int& cached,
     return true;
 }
 
-__device__ __forceinline__ int atom_add_acq_rel(int* p, int v) {
-    int old;
-    asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
-}
 
 // called by lane 0 after the node's results are written and fenced
 __device__ __forceinline__ void node_complete(int* done, const int* count, int L, int* wm) {
@@ -752,7 +853,8 @@ __device__ void block_backward(const T* __restrict__ Ub, int w, int r, int s, co
 // external part.  Right-hand sides are columns of z (stride n).
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
-fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit) {
+fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
+    const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
     int cached = 0;
@@ -801,7 +903,8 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, int gen, long long limit
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
-           double* __restrict__ xh, int nrhs, int gen, long long limit) {
+           double* __restrict__ xh, int nrhs, long long limit) {
+    const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
     int cached = 0;
@@ -863,7 +966,8 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
 // has received every contribution before it is read.
 __global__ void permute_in_t_kernel(int32_t n, const int32_t* __restrict__ piv, const int32_t* __restrict__ colperm,
                                     const double* __restrict__ dc, const double* __restrict__ g,
-                                    double* __restrict__ hh, int nrhs, int ld) {
+                                    double* __restrict__ hh, int nrhs, int ld, int32_t* gens) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) gens[1] += 1;   // substitution generation of this call
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n * nrhs;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(q / n), p = (int)(q % n);
@@ -885,7 +989,8 @@ __global__ void permute_out_t_kernel(int32_t n, const int32_t* __restrict__ rowp
 // U^T v = h by position (h is overwritten by v)
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
-ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit) {
+ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
+    const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
     int cached = 0;
@@ -944,7 +1049,8 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit)
 // L^T u = v by position (h holds v on entry, u on exit)
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
-lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, int gen, long long limit) {
+lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
+    const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
     int cached = 0;
@@ -1115,25 +1221,27 @@ int factor_grid(int device) {
     return sms * per;
 }
 
-int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t n, cudaStream_t st) {
+int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t* gens, int32_t n, cudaStream_t st) {
     if (cudaMemsetAsync(status, 0, sizeof(int32_t) * ST_WORDS, st) != cudaSuccess) return HYLU_ERR_CUDA;
     int blocks = (int)std::min<int64_t>(4096, ((int64_t)n + 255) / 256 + 1);
-    reset_kernel<<<blocks, 256, 0, st>>>(piv, pinv, n);
+    reset_kernel<<<blocks, 256, 0, st>>>(piv, pinv, n, gens);
     count_launch();
     return check("reset");
 }
 
-int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t gen,
+int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a,
                   double tau_rel, long long spin_limit, int grid, cudaStream_t st, cudaEvent_t e0,
                   cudaEvent_t e1) {
+    if (P.n_tasks > 0 && cudaMemsetAsync(P.node_done, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess)
+        return HYLU_ERR_CUDA;
     int blocks = (int)std::min<int64_t>(2048, (nnz_a + 255) / 256 + 1);
     amax_kernel<<<blocks, 256, 0, st>>>(d_vals, P.ah_src, P.ah_scale, nnz_a, P.status);
     count_launch();
     if (e0) cudaEventRecord(e0, st);
     if (P.lval32)
-        factor_kernel<float><<<grid, FWARPS * 32, factor_smem<float>(), st>>>(P, d_vals, P.dinv32, gen, tau_rel, spin_limit);
+        factor_kernel<float><<<grid, FWARPS * 32, factor_smem<float>(), st>>>(P, d_vals, P.dinv32, tau_rel, spin_limit);
     else
-        factor_kernel<double><<<grid, FWARPS * 32, factor_smem<double>(), st>>>(P, d_vals, P.dinv, gen, tau_rel, spin_limit);
+        factor_kernel<double><<<grid, FWARPS * 32, factor_smem<double>(), st>>>(P, d_vals, P.dinv, tau_rel, spin_limit);
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     return check("factor");
@@ -1141,22 +1249,22 @@ int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t
 
 int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, double* d_xh,
                  const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
-                 int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st,
+                 int nrhs, int ld, long long spin_limit, int grid, cudaStream_t st,
                  cudaEvent_t e0, cudaEvent_t e1) {
     const int64_t tot = (int64_t)P.n * nrhs;
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
     if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.fwd_done, 0, sizeof(int32_t) * P.n_fwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.bwd_done, 0, sizeof(int32_t) * P.n_bwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
-    permute_in_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld);
+    permute_in_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld, P.gens);
     count_launch();
     const int blocks = grid;
     if (e0) cudaEventRecord(e0, st);
-    if (P.lval32) fwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, gen, spin_limit);
-    else fwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, gen, spin_limit);
+    if (P.lval32) fwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, spin_limit);
+    else fwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, spin_limit);
     count_launch();
-    if (P.lval32) bwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv32, d_z, d_xh, nrhs, gen, spin_limit);
-    else bwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv, d_z, d_xh, nrhs, gen, spin_limit);
+    if (P.lval32) bwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv32, d_z, d_xh, nrhs, spin_limit);
+    else bwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv, d_z, d_xh, nrhs, spin_limit);
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     permute_out_kernel<<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);
@@ -1166,19 +1274,19 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
 
 int launch_solve_transpose(const DevPlan& P, const double* d_b, double* d_x, double* d_h,
                            const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
-                           int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st) {
+                           int nrhs, int ld, long long spin_limit, int grid, cudaStream_t st) {
     const int64_t tot = (int64_t)P.n * nrhs;
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
     if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.ut_done, 0, sizeof(int32_t) * P.n_ut_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.lt_done, 0, sizeof(int32_t) * P.n_lt_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
-    permute_in_t_kernel<<<eb, 256, 0, st>>>(P.n, P.piv, colperm, dc, d_b, d_h, nrhs, ld);
+    permute_in_t_kernel<<<eb, 256, 0, st>>>(P.n, P.piv, colperm, dc, d_b, d_h, nrhs, ld, P.gens);
     count_launch();
-    if (P.lval32) ut_kernel<float><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
-    else ut_kernel<double><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    if (P.lval32) ut_kernel<float><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, spin_limit);
+    else ut_kernel<double><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, spin_limit);
     count_launch();
-    if (P.lval32) lt_kernel<float><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
-    else lt_kernel<double><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, gen, spin_limit);
+    if (P.lval32) lt_kernel<float><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, spin_limit);
+    else lt_kernel<double><<<grid, WARPS * 32, 0, st>>>(P, d_h, nrhs, spin_limit);
     count_launch();
     permute_out_t_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_h, d_x, nrhs, ld);
     count_launch();

@@ -38,7 +38,13 @@ struct DevPlan {
     const double* ah_scale;
     int32_t* piv;                  // position -> label
     int32_t* pinv;                 // label -> position
-    int32_t* ready;                // per row, factor generation
+    int32_t* ready;                // per row, factor generation: the row (for a supernode, the whole node) is final
+    int32_t* dready;               // per supernode row: its diagonal-block step is done (pivot, multipliers)
+    int32_t* node_done;            // per node: tail tasks finished (zeroed before each factor)
+    const int32_t* node_ntask;     // per node: tail tasks (0: the rows publish themselves)
+    const int32_t* task_node;      // per tail task: node
+    const int32_t* task_chunk;     // per tail task: first 32-column group
+    int32_t n_tasks;
     // substitution schedules (rows in level order, node levels, nodes per
     // level) and per-level completion counters (reset by every solve)
     const int32_t* fwd_order;
@@ -71,20 +77,24 @@ struct DevPlan {
     const int32_t* heavy_order;    // heavy rows by level (claimed first), null if none
     const int32_t* heavy_rank;     // per row: rank in heavy_order, INT32_MAX if not heavy
     int32_t n_heavy;
-    unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, warp<<8|mode)
+    unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, waits / node complete)
     int32_t* status;
+    // [0] factor generation, [1] substitution generation: the flags above
+    // compare against them.  The first kernel of every factor / substitution
+    // bumps its word on the device, so a replayed CUDA graph advances them too.
+    int32_t* gens;
 };
 
-int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a, int32_t gen,
+int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a,
                   double tau_rel, long long spin_limit, int grid, cudaStream_t st,
                   cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, double* d_xh,
                  const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
-                 int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st,
+                 int nrhs, int ld, long long spin_limit, int grid, cudaStream_t st,
                  cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr);
 int launch_solve_transpose(const DevPlan& P, const double* d_b, double* d_x, double* d_h,
                            const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
-                           int nrhs, int ld, int32_t gen, long long spin_limit, int grid, cudaStream_t st);
+                           int nrhs, int ld, long long spin_limit, int grid, cudaStream_t st);
 int launch_residual_transpose(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* y,
                               const double* g, double* r, double* colsum, double* norms, int nrhs, int ld,
                               cudaStream_t st);
@@ -93,7 +103,7 @@ int launch_grad_values(int32_t n, const int64_t* rp, const int32_t* ci, const do
 int launch_residual(int32_t n, const int64_t* rp, const int32_t* ci, const double* v, const double* x,
                     const double* b, double* r, double* norms, int nrhs, int ld, cudaStream_t st);
 int launch_axpy(int32_t n, double* x, const double* d, int nrhs, int ld, cudaStream_t st);
-int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t n, cudaStream_t st);
+int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t* gens, int32_t n, cudaStream_t st);
 int factor_grid(int device);   // blocks of the persistent kernels
 int warps_per_block();
 int dense_l_min();

@@ -86,4 +86,19 @@ def test_batch_matches_single_systems_and_graph_replay():
                     rb = bs.row_base[v * k + q]
                     for r in range(nrhs):
                         assert _be(m, value_sets[v][q], xg[r, rb:rb + m.n], b[r, rb:rb + m.n]) <= bound
+        # new values in the captured buffer: a replay that skipped a wait
+        # would reuse the previous replay's factors
+        new_sets = [[synth.circuit_values(m.rowptr, m.col, 300 + 10 * v + q) if q < k - 1 else 2.0 * m.val
+                     for q, m in enumerate(mats)] for v in range(nsets)]
+        vals.copy_(torch.from_numpy(bs.concat_values(new_sets)).cuda())
+        dx.zero_()
+        bs.graph_launch(stream=side)
+        side.synchronize()
+        xg = dx.cpu().numpy()
+        bound = 1e-12 if bs.get_info().nperturb == 0 else 1e-7
+        for v in range(nsets):
+            for q, m in enumerate(mats):
+                rb = bs.row_base[v * k + q]
+                for r in range(nrhs):
+                    assert _be(m, new_sets[v][q], xg[r, rb:rb + m.n], b[r, rb:rb + m.n]) <= bound
     bs.close()
