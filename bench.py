@@ -54,6 +54,8 @@ def parse():
                     help="circuit_100k is the headline configuration; 'circuit' with --n is the same "
                          "generator at another size (profiling cases)")
     ap.add_argument("--n", type=int, default=30000, help="size for --workload circuit")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
+                    help="fp32: the precision form (FP32 factors, FP64 refinement on every solve)")
     args = ap.parse_args()
     global WORKLOAD
     WORKLOAD = args.workload
@@ -220,10 +222,10 @@ def kernel_hash() -> str:
     return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
 
 
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, fp32: bool = False):
     """DRAM bytes per factor-kernel launch from the committed ncu summary, if
     it was taken on the current kernel source."""
-    p = os.path.join(ROOT, "profiles", f"factor_kernel_{workload}.txt")
+    p = os.path.join(ROOT, "profiles", f"factor_kernel_{workload}{'_fp32' if fp32 else ''}.txt")
     if not os.path.exists(p):
         return None
     kv = {}
@@ -275,7 +277,8 @@ def run_hylu(args, ws, rank, local):
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     A, sets, b = make_inputs(args.n)
-    s = Solver(A.n, A.rowptr, A.col, A.val, timing=1, ordering=ordering_for(WORKLOAD))
+    fp32 = args.precision == "fp32"
+    s = Solver(A.n, A.rowptr, A.col, A.val, timing=1, ordering=ordering_for(WORKLOAD), precision=1 if fp32 else 0)
     info = s.info
     flops = info.flops
     d_sets = [torch.from_numpy(v.val).to(dev) for v in sets]
@@ -287,7 +290,13 @@ def run_hylu(args, ws, rank, local):
         s.factor(d_sets[k % VALUE_SETS])
         s.solve(d_b, d_x)
     torch.cuda.synchronize()
-    peak_gflops = capi.hylu_measure_fp64_peak(stream.cuda_stream)
+    if fp32:
+        # FP32 FMA units x max SM clock: 152 SMs x 128 lanes x 2 flops x 2070 MHz
+        peak_gflops = 152 * 128 * 2 * 2.070
+        peak_source = "FP32 ALU: 152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz (unit counts, max clock)"
+    else:
+        peak_gflops = capi.hylu_measure_fp64_peak(stream.cuda_stream)
+        peak_source = "FP64 FMA throughput measured live (hylu_measure_fp64_peak)"
     # ---------------- device-resident timed region
     clocks = Clocks(local, os.path.join(tempfile.gettempdir(), f"hylu_clocks_{os.getpid()}.csv")) if rank == 0 else None
     barrier(ws)
@@ -355,9 +364,10 @@ def run_hylu(args, ws, rank, local):
         out = {
             "metric": metric_name(), "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": False,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD if WORKLOAD != "circuit" else f"circuit_{A.n}", "n": A.n,
                        "nnz": A.nnz, "ordering": "ND" if ordering_for(WORKLOAD) else "AMD",
+                       "precision": "FP32 factors + FP64 refinement" if fp32 else "FP64",
                        "value_sets": VALUE_SETS, "flops": flops, "nnz_lu": info.nnz_lu,
                        "nnz_store": info.nnz_store, "supernodes": info.nsupernodes,
                        "rows_in_supernodes": info.rows_in_supernodes,
@@ -367,10 +377,11 @@ def run_hylu(args, ws, rank, local):
             "backward_error": max(be, be_e2e),
             "solve_ms": statistics.mean(solve_ms),
             "nperturb": inf.nperturb,
+            "refine_iters": inf.refine_iters,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gflops / 1e3,
                          "unit": "TFLOP/s", "frac": achieved * 1e3 / peak_gflops,
-                         "traffic": profiled_traffic(WORKLOAD), "kernel": "factor_kernel",
-                         "peak_source": "FP64 FMA throughput measured live (hylu_measure_fp64_peak)",
+                         "traffic": profiled_traffic(WORKLOAD, fp32), "kernel": "factor_kernel",
+                         "peak_source": peak_source,
                          "kernel_ms": kmean},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(A.nnz * 8 + A.n * 8),

@@ -152,13 +152,16 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
     P.nnz_f = frp[n];
     // tail tasks: a 32-column group costs s^2 / 2 multiply-adds per lane; a
     // task takes about 512 of them (one group from s = 32 up), at most one
-    // task per group
+    // task per group.  A node whose whole tail is about one task's work (or
+    // less) gets none: its last row solves the tail after its own
+    // diagonal-block step, saving a claim and a hand-off.
     P.node_ntask.assign(nn, 0);
     for (int32_t D = 0; D < nn; ++D) {
         const int64_t sz = P.sn_start[D + 1] - P.sn_start[D];
         const int64_t nT = P.node_tail_off[D + 1] - P.node_tail_off[D];
         if (sz < 2 || nT == 0) continue;
         const int64_t ng = (nT + 31) / 32;
+        if (sz * sz * ng <= 1024) continue;
         const int64_t want = (sz * sz * ng + 1023) / 1024;
         P.node_ntask[D] = (int32_t)std::max<int64_t>(1, std::min<int64_t>(want, ng));
     }

@@ -211,25 +211,23 @@ __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, cons
     }
 }
 
-// Tail task of a supernode (the in-supernode step, Sec. 2.2).  Once the
-// node's diagonal block is factored (every row's pivot and multipliers
-// known), its U tail is U_T = L_DD^-1 X_T: X_T the rows' tails after the
-// updates from earlier nodes, L_DD the unit lower multipliers by position
-// (row q keeps l_qk at the label of position k).  Lanes own tail columns and
-// hold a block of rows of their column in registers: first the finished rows above
-// the block (8 at a time, multipliers staged in shared memory), then the
-// triangle inside the block, so every entry takes its updates in ascending k
-// as in the row-by-row elimination.  The last task of the node publishes it.
+// Tail of a supernode (the in-supernode step, Sec. 2.2), 32-column groups
+// g0, g0 + gstep, ...  Once the node's diagonal block is factored (every
+// row's pivot and multipliers known), its U tail is U_T = L_DD^-1 X_T: X_T
+// the rows' tails after the updates from earlier nodes, L_DD the unit lower
+// multipliers by position (row q keeps l_qk at the label of position k).
+// Lanes own tail columns and hold a block of rows of their column in
+// registers: first the finished rows above the block (8 at a time,
+// multipliers staged in shared memory), then the triangle inside the block,
+// so every entry takes its updates in ascending k as in the row-by-row
+// elimination.
 template <typename T>
-__device__ __noinline__ bool tail_task(const DevPlan& P, int t, int gen, long long limit, WarpSmem<T>* ws, int lane) {
-    const int D = P.task_node[t];
-    const int nck = P.node_ntask[D];
+__device__ __noinline__ void tail_solve(const DevPlan& P, int D, int g0, int gstep, WarpSmem<T>* ws, int lane) {
     const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
     const int nT = (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
     const int64_t w = s + nT;
     const T* Ub = PV<T>(P) + P.node_panel_off[D];
     T* Uw = PV<T>(P) + P.node_panel_off[D];
-    if (!warp_wait(P.dready + e, gen, P.status, e, limit)) return false;
     int* pb = ws->pb;
     // rows per register block (16 keeps the task within the kernel's 128
     // registers); RB x RB staging area: the prefetch buffers and the panel,
@@ -239,7 +237,7 @@ __device__ __noinline__ bool tail_task(const DevPlan& P, int t, int gen, long lo
     static_assert(sizeof(ws->pfu) + PANEL_BYTES >= RB * RB * sizeof(T), "staging area");
     for (int q = lane; q < s; q += 32) pb[q] = P.piv[r + q] - r;
     __syncwarp();
-    for (int g = P.task_chunk[t]; g * 32 < nT; g += nck) {
+    for (int g = g0; g * 32 < nT; g += gstep) {
         const int j = g * 32 + lane;
         const bool on = j < nT;
         T* col = Uw + s + (on ? j : 0);
@@ -284,6 +282,17 @@ __device__ __noinline__ bool tail_task(const DevPlan& P, int t, int gen, long lo
                 if (on && u < m) col[(int64_t)(q0 + u) * w] = x[u];
         }
     }
+}
+
+// One tail task: waits for the node's last diagonal-block step, solves its
+// column groups, and the node's last task to finish publishes every row.
+template <typename T>
+__device__ bool tail_task(const DevPlan& P, int t, int gen, long long limit, WarpSmem<T>* ws, int lane) {
+    const int D = P.task_node[t];
+    const int nck = P.node_ntask[D];
+    const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1;
+    if (!warp_wait(P.dready + e, gen, P.status, e, limit)) return false;
+    tail_solve<T>(P, D, P.task_chunk[t], nck, ws, lane);
     __threadfence();
     __syncwarp();
     if (lane == 0 && atom_add_acq_rel(P.node_done + D, 1) == nck - 1) {
@@ -293,6 +302,7 @@ __device__ __noinline__ bool tail_task(const DevPlan& P, int t, int gen, long lo
     __syncwarp();
     return true;
 }
+
 
 template <typename T>
 __global__ void __launch_bounds__(FWARPS * 32, 4)
@@ -583,6 +593,8 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         }
         if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 1] = gtimer();
         const unsigned long long waited_ext = waited;
+        // a supernode with a U tail finishes it after the diagonal-block
+        // step: by tail tasks, or (small nodes) by its last row right here
         const bool has_tasks = (s > 1) && (nT > 0);
         if (has_tasks && pn.mode != 2) {
             // the tail leaves the row here (the tail tasks finish it)
@@ -657,7 +669,19 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         if (has_tasks) {
             // trace word 3 of such a row: when its node completed (tail tasks)
             if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 2] = gtimer();
-            continue;   // the node's last tail task publishes the row
+            if (P.node_ntask[D] == 0 && i == e) {
+                // small node: every row's multipliers and tail are in (the
+                // diagonal-block waits above acquired them); solve the tail here
+                tail_solve<T>(P, D, 0, 1, ws, lane);
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) {
+                    for (int k = r; k <= e; ++k) st_release(P.ready + k, gen);
+                    if (P.trace) P.trace[4 * (int64_t)e + 3] = gtimer();
+                }
+                __syncwarp();
+            }
+            continue;   // the node's last tail task (or last row) publishes the row
         }
         if (lane == 0) st_release(P.ready + i, gen);
         if (P.trace && lane == 0) {
