@@ -158,6 +158,28 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
         d.n_lt_levels = (int32_t)P.lt_count.size();
         TRY(dalloc(h, &d.ut_done, P.ut_count.size()));
         TRY(dalloc(h, &d.lt_done, P.lt_count.size()));
+        // instances and their slices of the level counts (one for a single system)
+        const int32_t ni = P.node_inst.empty() ? 1 : (int32_t)P.fwd_off.size() - 1;
+        d.n_inst = ni;
+        d.node_inst = nullptr;
+        if (!P.node_inst.empty()) {
+            int32_t* nin;
+            TRY(upload(h, &nin, P.node_inst, st));
+            d.node_inst = nin;
+        }
+        auto slice = [&](const std::vector<int32_t>& off, const std::vector<int32_t>& cnt, const int32_t** out) {
+            std::vector<int32_t> o = off.empty() ? std::vector<int32_t>{0, (int32_t)cnt.size()} : off;
+            int32_t* dp;
+            int rc = upload(h, &dp, o, st);
+            *out = dp;
+            return rc;
+        };
+        TRY(slice(P.fwd_off, P.fwd_count, &d.fwd_off));
+        TRY(slice(P.bwd_off, P.bwd_count, &d.bwd_off));
+        TRY(slice(P.ut_off, P.ut_count, &d.ut_off));
+        TRY(slice(P.lt_off, P.lt_count, &d.lt_off));
+        TRY(dalloc(h, &d.wm_f, ni));
+        TRY(dalloc(h, &d.wm_b, ni));
     }
     TRY(dalloc(h, &d.fwd_row, P.n));
     TRY(dalloc(h, &d.bwd_row, P.n));

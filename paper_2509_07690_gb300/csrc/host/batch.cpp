@@ -174,6 +174,22 @@ int combine(const std::vector<const Plan*>& sys, int32_t nsets, Plan& C, BatchLa
     merge_by_level(inst, B.row_base, nbase, lv, false, C.ut_order, nodes_per_level, C.ut_count);
     for (size_t q = 0; q < Q; ++q) lv[q] = &inst[q]->lt_level;
     merge_by_level(inst, B.row_base, nbase, lv, true, C.lt_order, nodes_per_level, C.lt_count);
+    // per-instance level counts (each instance has its own watermark)
+    auto slices = [&](std::vector<int32_t> Plan::*cnt, std::vector<int32_t>& out, std::vector<int32_t>& off) {
+        out.clear();
+        off.assign(1, 0);
+        for (size_t q = 0; q < Q; ++q) {
+            const std::vector<int32_t>& c = inst[q]->*cnt;
+            out.insert(out.end(), c.begin(), c.end());
+            off.push_back((int32_t)out.size());
+        }
+    };
+    slices(&Plan::fwd_count, C.fwd_count, C.fwd_off);
+    slices(&Plan::bwd_count, C.bwd_count, C.bwd_off);
+    slices(&Plan::ut_count, C.ut_count, C.ut_off);
+    slices(&Plan::lt_count, C.lt_count, C.lt_off);
+    C.node_inst.clear();
+    for (size_t q = 0; q < Q; ++q) C.node_inst.insert(C.node_inst.end(), inst[q]->nnodes, (int32_t)q);
     for (size_t q = 0; q < Q; ++q) {
         C.fwd_level.insert(C.fwd_level.end(), inst[q]->fwd_level.begin(), inst[q]->fwd_level.end());
         C.bwd_level.insert(C.bwd_level.end(), inst[q]->bwd_level.begin(), inst[q]->bwd_level.end());

@@ -64,6 +64,11 @@ struct Plan {
     // transpose substitution (U^T forward, then L^T backward), push form:
     // node levels, rows in claim order, rows per level
     std::vector<int32_t> ut_order, lt_order, ut_level, lt_level, ut_count, lt_count;
+    // independent instances (a batch): every instance has its own level
+    // watermark; node_inst maps a node to its instance (empty: one instance)
+    // and the *_off arrays give each instance's slice of the per-level
+    // count arrays above (empty: one slice, the whole array)
+    std::vector<int32_t> node_inst, fwd_off, bwd_off, ut_off, lt_off;
     int32_t max_row = 0;                // longest row pattern (L + block + tail)
     int32_t max_sn = 1;
     double analyze_ms = 0.0;

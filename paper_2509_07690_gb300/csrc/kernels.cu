@@ -323,8 +323,9 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
     // heavy rows form a queue of their own, served by every warp of a subset
     // of the SMs sized to hold them all at once (at most half of the SMs), so
     // that their FP64 work does not share pipes with the dependency chain the
-    // other SMs run; every other row comes from the level-ordered main queue,
-    // which skips the heavy rows.  Progress holds: a claimed row waits only on
+    // other SMs run, and by any warp that finds the main queue drained; every
+    // other row comes from the level-ordered main queue, which skips the
+    // heavy rows.  Progress holds: a claimed row waits only on
     // rows of lower levels, and the lowest-level unfinished row is either
     // claimed, or next in its queue, whose claimed rows are all ready.
     unsigned smid, nsmid;
@@ -333,7 +334,12 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
     const int64_t nwarps = (int64_t)gridDim.x * FWARPS;
     const int64_t hsm = min((int64_t)nsmid / 2, ((int64_t)P.n_heavy * nsmid + nwarps - 1) / nwarps);
     bool heavy_open = (P.n_heavy > 0) && ((int64_t)smid < hsm);
-    const int hcap = P.n_heavy;
+    bool main_open = true;
+    // early claiming pays only when every heavy row gets a warp at once; with
+    // more heavy rows than half the warps (batches of many systems) they would
+    // hold warps while waiting on their own chains: plain level order instead
+    const int hcap = ((int64_t)P.n_heavy <= nwarps / 2) ? P.n_heavy : 0;
+    heavy_open = heavy_open && hcap > 0;
     for (;;) {
         int i = -1;
         if (lane == 0) {
@@ -341,11 +347,16 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                 const int h = atomicAdd(P.status + ST_CNT_H, 1);
                 if (h < hcap) i = P.heavy_order[h]; else heavy_open = false;
             }
-            while (i < 0) {
+            while (i < 0 && main_open) {
                 const int qi = atomicAdd(P.status + ST_CNT_F, 1);
-                if (qi >= P.n + P.n_tasks) { i = INT_MAX; break; }
+                if (qi >= P.n + P.n_tasks) { main_open = false; break; }
                 const int c = P.row_order[qi];
                 if (c >= P.n || hcap == 0 || P.heavy_rank[c] >= hcap) i = c;
+            }
+            if (i < 0) {
+                // main queue drained: help with the heavy rows that are left
+                const int h = hcap > 0 ? atomicAdd(P.status + ST_CNT_H, 1) : hcap;
+                i = (h < hcap) ? P.heavy_order[h] : INT_MAX;
             }
         }
         i = __shfl_sync(FULL, i, 0);
@@ -757,6 +768,42 @@ __device__ __forceinline__ double sparse_dot(const T* __restrict__ v, const int3
     return a;
 }
 
+// Warp-wide sums out[u] = sum_t v[t] * x[u * ldx + c[t]], t < m, for up to
+// RB right-hand sides u < nr at once: every L entry is loaded once and its
+// gathers for all right-hand sides are in flight together.  The results are
+// valid in every lane.
+template <typename T, int RB>
+__device__ __forceinline__ void sparse_dot_rhs(const T* __restrict__ v, const int32_t* __restrict__ c, int m,
+                                               const double* __restrict__ x, int64_t ldx, int nr, int lane,
+                                               double* out) {
+    double acc[RB];
+#pragma unroll
+    for (int u = 0; u < RB; ++u) acc[u] = 0.0;
+    for (int t0 = 0; t0 < m; t0 += 64) {
+        int cc[2];
+        T vv[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+            const int t = t0 + b * 32 + lane;
+            cc[b] = (t < m) ? __ldg(c + t) : -1;
+            vv[b] = (t < m) ? __ldg(v + t) : T(0);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (cc[b] >= 0) {
+#pragma unroll
+                for (int u = 0; u < RB; ++u)
+                    if (u < nr) acc[u] = fma((double)vv[b], x[u * ldx + cc[b]], acc[u]);
+            }
+    }
+#pragma unroll
+    for (int u = 0; u < RB; ++u) {
+        double a = acc[u];
+        for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
+        out[u] = a;
+    }
+}
+
 // Level watermark of the substitution (bulk mode, Sec. 2.2.1 / 2.3): nodes
 // are grouped by dependency level; rows are claimed level by level, and a row
 // of level L only waits until the watermark (levels whose nodes are all
@@ -881,7 +928,7 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
-    int cached = 0;
+    int cached = 0, cq = 0;
     for (;;) {
         int qi = 0;
         if (lane == 0) qi = atomicAdd(P.status + ST_CNT_FWD, 1);
@@ -892,17 +939,27 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         const int D = P.node_of[i];
         const int L = P.fwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
-        if (!__all_sync(FULL, wait_level(P.status + ST_WM_F, L, cached, P.status, limit))) return;
+        const int q = P.node_inst ? P.node_inst[D] : 0;
+        if (q != cq) { cq = q; cached = 0; }
+        if (!__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
         const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
-        for (int rr = 0; rr < nrhs; ++rr) {
-            double* zr = z + (int64_t)rr * n;
-            const double a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), zr, lane);
-            if (lane == 0) zr[i] -= a;
+        if (nrhs == 1) {
+            const double a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), z, lane);
+            if (lane == 0) z[i] -= a;
+        } else {
+            for (int r0 = 0; r0 < nrhs; r0 += 8) {
+                double a[8];
+                const int nr = min(8, nrhs - r0);
+                sparse_dot_rhs<T, 8>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), z + (int64_t)r0 * n, n, nr,
+                                     lane, a);
+                if (lane == 0)
+                    for (int u = 0; u < nr; ++u) z[(int64_t)(r0 + u) * n + i] -= a[u];
+            }
         }
         __threadfence();
         __syncwarp();
         if (s == 1) {
-            if (lane == 0) node_complete(P.fwd_done, P.fwd_count, L, P.status + ST_WM_F);
+            if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
             continue;
         }
         if (lane == 0) st_release(P.fwd_row + i, gen);
@@ -916,7 +973,7 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         for (int rr = 0; rr < nrhs; ++rr) block_forward<T>(Ub, w, r, s, P.piv, z + (int64_t)rr * n, lane);
         __threadfence();
         __syncwarp();
-        if (lane == 0) node_complete(P.fwd_done, P.fwd_count, L, P.status + ST_WM_F);
+        if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
     }
 }
 
@@ -931,7 +988,7 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
-    int cached = 0;
+    int cached = 0, cq = 0;
     for (;;) {
         int qi = 0;
         if (lane == 0) qi = atomicAdd(P.status + ST_CNT_BWD, 1);
@@ -947,20 +1004,25 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         const int w = s + nT;
         const int32_t* tc = P.tcols + t0;
         const T* Ui = PV<T>(P) + P.node_panel_off[D] + (int64_t)(i - r) * w;
-        if (!__all_sync(FULL, wait_level(P.status + ST_WM_B, L, cached, P.status, limit))) return;
-        for (int rr = 0; rr < nrhs; ++rr) {
-            double* zr = z + (int64_t)rr * n;
-            const double* xr = xh + (int64_t)rr * n;
-            const double a = sparse_dot<T>(Ui + s, tc, nT, xr, lane);
-            if (lane == 0) {
-                if (s == 1) xh[(int64_t)rr * n + i] = (zr[i] - a) * (double)dinv[i];
-                else zr[i] -= a;
-            }
+        const int q = P.node_inst ? P.node_inst[D] : 0;
+        if (q != cq) { cq = q; cached = 0; }
+        if (!__all_sync(FULL, wait_level(P.wm_b + q, L, cached, P.status, limit))) return;
+        for (int r0 = 0; r0 < nrhs; r0 += 8) {
+            double a[8];
+            const int nr = min(8, nrhs - r0);
+            if (nr == 1) a[0] = sparse_dot<T>(Ui + s, tc, nT, xh + (int64_t)r0 * n, lane);
+            else sparse_dot_rhs<T, 8>(Ui + s, tc, nT, xh + (int64_t)r0 * n, n, nr, lane, a);
+            if (lane == 0)
+                for (int u = 0; u < nr; ++u) {
+                    const int64_t o = (int64_t)(r0 + u) * n + i;
+                    if (s == 1) xh[o] = (z[o] - a[u]) * (double)dinv[i];
+                    else z[o] -= a[u];
+                }
         }
         __threadfence();
         __syncwarp();
         if (s == 1) {
-            if (lane == 0) node_complete(P.bwd_done, P.bwd_count, L, P.status + ST_WM_B);
+            if (lane == 0) node_complete(P.bwd_done + P.bwd_off[q], P.bwd_count + P.bwd_off[q], L, P.wm_b + q);
             continue;
         }
         if (lane == 0) st_release(P.bwd_row + i, gen);
@@ -978,7 +1040,7 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) node_complete(P.bwd_done, P.bwd_count, L, P.status + ST_WM_B);
+        if (lane == 0) node_complete(P.bwd_done + P.bwd_off[q], P.bwd_count + P.bwd_off[q], L, P.wm_b + q);
     }
 }
 
@@ -1017,7 +1079,7 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
-    int cached = 0;
+    int cached = 0, cq = 0;
     for (;;) {
         int qi = 0;
         if (lane == 0) qi = atomicAdd(P.status + ST_CNT_FWD, 1);
@@ -1032,7 +1094,9 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
         const int nT = (int)(P.node_tail_off[D + 1] - t0);
         const int w = s + nT;
         const T* Ub = PV<T>(P) + P.node_panel_off[D];
-        if (!__all_sync(FULL, wait_level(P.status + ST_WM_F, L, cached, P.status, limit))) return;
+        const int q = P.node_inst ? P.node_inst[D] : 0;
+        if (q != cq) { cq = q; cached = 0; }
+        if (!__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
         if (s == 1) {
             if (lane == 0) for (int rr = 0; rr < nrhs; ++rr) h[(int64_t)rr * n + i] *= (double)DI<T>(P)[i];
             __syncwarp();
@@ -1066,7 +1130,7 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) node_complete(P.ut_done, P.ut_count, L, P.status + ST_WM_F);
+        if (lane == 0) node_complete(P.ut_done + P.ut_off[q], P.ut_count + P.ut_off[q], L, P.wm_f + q);
     }
 }
 
@@ -1077,7 +1141,7 @@ lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
-    int cached = 0;
+    int cached = 0, cq = 0;
     for (;;) {
         int qi = 0;
         if (lane == 0) qi = atomicAdd(P.status + ST_CNT_BWD, 1);
@@ -1088,7 +1152,9 @@ lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
         const int D = P.node_of[i];
         const int L = P.lt_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
-        if (!__all_sync(FULL, wait_level(P.status + ST_WM_B, L, cached, P.status, limit))) return;
+        const int q = P.node_inst ? P.node_inst[D] : 0;
+        if (q != cq) { cq = q; cached = 0; }
+        if (!__all_sync(FULL, wait_level(P.wm_b + q, L, cached, P.status, limit))) return;
         if (s > 1) {
             if (i == e) {
                 // the block: u_k = v_k - sum_{j in (k, e]} L(j, pos k) u_j
@@ -1122,7 +1188,7 @@ lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
         }
         __threadfence();
         __syncwarp();
-        if (lane == 0) node_complete(P.lt_done, P.lt_count, L, P.status + ST_WM_B);
+        if (lane == 0) node_complete(P.lt_done + P.lt_off[q], P.lt_count + P.lt_off[q], L, P.wm_b + q);
     }
 }
 
@@ -1279,6 +1345,8 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
     if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.fwd_done, 0, sizeof(int32_t) * P.n_fwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.wm_f, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.wm_b, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.bwd_done, 0, sizeof(int32_t) * P.n_bwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     permute_in_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld, P.gens);
     count_launch();
@@ -1303,6 +1371,8 @@ int launch_solve_transpose(const DevPlan& P, const double* d_b, double* d_x, dou
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
     if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.ut_done, 0, sizeof(int32_t) * P.n_ut_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.wm_f, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.wm_b, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.lt_done, 0, sizeof(int32_t) * P.n_lt_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     permute_in_t_kernel<<<eb, 256, 0, st>>>(P.n, P.piv, colperm, dc, d_b, d_h, nrhs, ld, P.gens);
     count_launch();

@@ -12,8 +12,7 @@ namespace hylu {
 //   expired, [2] perturbed pivots, [3] task counter of the factor kernel,
 //   [4] task counter of the forward solve, [5] of the backward solve,
 //   [6..7] max |Ahat| as the bit pattern of a non-negative double.
-//   [8..11] substitution: forward / backward claim counters, forward /
-//   backward level watermarks (levels whose nodes are all complete).
+//   [8..9] substitution: forward / backward claim counters ([10..11] unused).
 //   [12] task counter of the factor kernel's heavy-row queue.
 enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_AMAX = 6, ST_CNT_FWD = 8,
        ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_CNT_H = 12, ST_WORDS = 14 };
@@ -64,7 +63,18 @@ struct DevPlan {
     const int32_t* lt_count;
     int32_t* ut_done;
     int32_t* lt_done;
-    int32_t n_ut_levels, n_lt_levels;
+    int32_t n_ut_levels, n_lt_levels;     // lengths of the count / done arrays
+    // instances with their own level watermarks (a batch; one otherwise):
+    // node -> instance (null: all 0), each instance's slice of the count and
+    // done arrays, and the forward / backward watermarks per instance
+    const int32_t* node_inst;
+    const int32_t* fwd_off;
+    const int32_t* bwd_off;
+    const int32_t* ut_off;
+    const int32_t* lt_off;
+    int32_t* wm_f;
+    int32_t* wm_b;
+    int32_t n_inst;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
     int32_t* pos;                  // per-warp column -> slot maps, pos_n each
