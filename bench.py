@@ -55,6 +55,8 @@ def parse():
                     help="circuit_100k is the headline configuration; 'circuit' with --n is the same "
                          "generator at another size (profiling cases)")
     ap.add_argument("--n", type=int, default=30000, help="size for --workload circuit")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="grid workloads: grid side x scale (profiling cases; 1 is the configuration)")
     ap.add_argument("--batch-systems", type=int, default=512,
                     help="circuit_batch_512: systems in the batch (512 is the configuration)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
@@ -108,7 +110,7 @@ def allsum(ws, v: float) -> float:
 
 
 # ----------------------------------------------------------------- inputs
-def make_inputs(n_circuit: int = 30000):
+def make_inputs(n_circuit: int = 30000, scale: float = 1.0):
     """The workload matrix, VALUE_SETS value sets on its pattern (fresh values
     for the circuit generator, the matrix itself otherwise) and b = A x_true."""
     from paper_2509_07690_gb300 import synth
@@ -117,7 +119,7 @@ def make_inputs(n_circuit: int = 30000):
         A = synth.circuit(n_circuit, seed=1000 + idx)
     else:
         idx = synth.WORKLOADS[WORKLOAD]["index"]
-        A = synth.workload(WORKLOAD)
+        A = synth.workload(WORKLOAD, scale)
     if WORKLOAD.startswith("circuit"):
         sets = [synth.circuit_value_set(A, 1002 + idx + j) for j in range(VALUE_SETS)]
     else:
@@ -401,7 +403,7 @@ def run_hylu(args, ws, rank, local):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
-    A, sets, b = make_inputs(args.n)
+    A, sets, b = make_inputs(args.n, args.scale)
     fp32 = args.precision == "fp32"
     s = Solver(A.n, A.rowptr, A.col, A.val, timing=1, ordering=ordering_for(WORKLOAD), precision=1 if fp32 else 0)
     info = s.info
@@ -490,7 +492,8 @@ def run_hylu(args, ws, rank, local):
             "metric": metric_name(), "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_total / args.steps, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if fp32 else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD if WORKLOAD != "circuit" else f"circuit_{A.n}", "n": A.n,
+            "config": {"workload": (WORKLOAD if args.scale == 1.0 else f"{WORKLOAD}_x{args.scale}")
+                       if WORKLOAD != "circuit" else f"circuit_{A.n}", "n": A.n,
                        "nnz": A.nnz, "ordering": "ND" if ordering_for(WORKLOAD) else "AMD",
                        "precision": "FP32 factors + FP64 refinement" if fp32 else "FP64",
                        "value_sets": VALUE_SETS, "flops": flops, "nnz_lu": info.nnz_lu,

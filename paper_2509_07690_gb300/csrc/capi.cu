@@ -183,6 +183,8 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     }
     TRY(dalloc(h, &d.fwd_row, P.n));
     TRY(dalloc(h, &d.bwd_row, P.n));
+    TRY(dalloc(h, &d.tile_f, P.n));
+    TRY(dalloc(h, &d.tile_b, P.n));
     TRY(dalloc(h, &d.dinv, P.n));
     TRY(dalloc(h, &d.status, hylu::ST_WORDS));
     h->grid = hylu::factor_grid(h->device);
@@ -214,6 +216,8 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     if (cudaMemsetAsync(d.dready, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.fwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(d.bwd_row, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(d.tile_f, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(d.tile_b, 0, sizeof(int32_t) * P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
     TRY(dalloc(h, &h->d_avals, P.nnz_a));
     TRY(upload(h, &h->d_arp, P.a_rp, st));
     TRY(upload(h, &h->d_aci, P.a_ci, st));

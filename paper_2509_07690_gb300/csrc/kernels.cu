@@ -809,18 +809,28 @@ __device__ __forceinline__ void sparse_dot_rhs(const T* __restrict__ v, const in
 // of level L only waits until the watermark (levels whose nodes are all
 // complete) reaches L.  The last node to complete a level raises it.
 __device__ __forceinline__ bool wait_level(const int* wm, int need, int& cached, int* status, long long limit) {
+    // one lane polls (with a short sleep once the wait is not immediate) and
+    // the warp takes its answer: thousands of waiting warps would otherwise
+    // keep the watermark's line busy in L2
+    const int lane = threadIdx.x & 31;
     if (cached >= need) return true;
-    long long it = 0;
-    int v;
-    while ((v = ld_acquire(wm)) < need) {
-        if (++it > limit) {
-            if (atomicCAS(status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0) status[ST_FAILED] = -need;
-            return false;
+    int ok = 1, v = 0;
+    if (lane == 0) {
+        long long it = 0;
+        while ((v = ld_acquire(wm)) < need) {
+            if (++it > limit) {
+                if (atomicCAS(status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0) status[ST_FAILED] = -need;
+                ok = 0;
+                break;
+            }
+            if ((it & 255) == 0 && ld_relaxed(status + ST_ERR) != 0) { ok = 0; break; }
+            if (it > 8) __nanosleep(64);
         }
-        if ((it & 255) == 0 && ld_relaxed(status + ST_ERR) != 0) return false;
     }
-    cached = v;
-    return true;
+    ok = __shfl_sync(FULL, ok, 0);
+    v = __shfl_sync(FULL, v, 0);
+    if (ok) cached = v;
+    return ok != 0;
 }
 
 
@@ -829,91 +839,87 @@ __device__ __forceinline__ void node_complete(int* done, const int* count, int L
     if (atom_add_acq_rel(done + L, 1) + 1 == count[L]) st_release(wm, L + 1);
 }
 
-// Dense block of a supernode in the substitution, by 32-row tiles with lanes
-// over rows: the tile's own triangle is solved from registers with shuffles,
-// then its 32 results are applied to the remaining rows with independent
-// loads (about s/32 dependent steps instead of s).  The block is stored by
-// label: entry (i, position p) of row i is Ub[(i - r) * w + piv[p] - r].
+// Dense block of a supernode in the substitution, by 32-row tiles.  The
+// block is stored by label: entry (row i, position p) is
+// Ub[(i - r) * w + piv[p] - r].  Right-hand side u is z + u * ldz (up to 8
+// are handled per pass).  On this GPU one FP64 warp instruction holds its
+// sub-partition's FP64 pipe for ~64 cycles whatever the active lanes, so the
+// layout keeps every lane busy: lanes own rows and loop over the 32 columns.
+//
+// tile_apply: rows [R0, R0 + nr_rows) take the finished results of the 32
+// positions [P0, P0 + nt) (z there already final): z_row -= sum_c
+// B(row, P0 + c) z_{P0 + c}.  Each lane loads its row's 32 entries first (all
+// loads in flight together), then one FMA chain per right-hand side.
 template <typename T>
-__device__ void block_forward(const T* __restrict__ Ub, int w, int r, int s, const int32_t* __restrict__ piv,
-                              double* __restrict__ z, int lane) {
-    for (int T0 = 0; T0 < s; T0 += 32) {
-        const int nt = min(32, s - T0);
-        const int lp = (lane < nt) ? piv[r + T0 + lane] - r : 0;      // label offset of tile column `lane`
-        // the tile's own strictly lower triangle
-        double my = (lane < nt) ? z[r + T0 + lane] : 0.0;
-        T Lrow[32];
-        const T* Ui = Ub + (int64_t)(T0 + lane) * w;
+__device__ void tile_apply(const T* __restrict__ Ub, int w, int r, int R0, int nr_rows, int P0, int nt,
+                           const int32_t* __restrict__ piv, double* __restrict__ z, int64_t ldz, int nrhs,
+                           int lane) {
+    const int lp = (lane < nt) ? piv[P0 + lane] - r : 0;
+    const int row = R0 + lane;
+    const bool ok = lane < nr_rows;
+    const T* Ur = Ub + (int64_t)((ok ? row : R0) - r) * w;
+    T Rrow[32];
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const int lc = __shfl_sync(FULL, lp, c);
-            Lrow[c] = (lane < nt && c < lane) ? Ui[lc] : T(0);
-        }
+    for (int c = 0; c < 32; ++c) {
+        const int lc = __shfl_sync(FULL, lp, c);
+        Rrow[c] = (ok && c < nt) ? Ur[lc] : T(0);
+    }
+    for (int u = 0; u < nrhs; ++u) {
+        const double zt = (lane < nt) ? z[u * ldz + P0 + lane] : 0.0;
+        double a = 0.0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) a = fma((double)Rrow[c], __shfl_sync(FULL, zt, c), a);
+        if (ok) z[u * ldz + row] -= a;
+    }
+}
+
+// tile_lower: unit lower triangle of the tile at positions [T0, T0 + nt)
+// (rows T0 .. too), forward substitution in place.
+template <typename T>
+__device__ void tile_lower(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
+                           double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+    const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
+    T Lrow[32];
+    const T* Ui = Ub + (int64_t)(T0 - r + (lane < nt ? lane : 0)) * w;
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+        const int lc = __shfl_sync(FULL, lp, c);
+        Lrow[c] = (lane < nt && c < lane) ? Ui[lc] : T(0);
+    }
+    for (int u = 0; u < nrhs; ++u) {
+        double my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
 #pragma unroll
         for (int c = 0; c < 32; ++c) {
             const double zc = __shfl_sync(FULL, my, c);
             if (c < lane) my -= (double)Lrow[c] * zc;
         }
-        if (lane < nt) z[r + T0 + lane] = my;
-        // the rows below the tile
-        for (int R0 = T0 + 32; R0 < s; R0 += 32) {
-            // every lane runs the same shuffles; only the loads and the
-            // update of rows past the block's end are switched off
-            const int row = R0 + lane;
-            const bool ok = row < s;
-            const T* Ur = Ub + (int64_t)(ok ? row : 0) * w;
-            double a = 0.0;
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const int lc = __shfl_sync(FULL, lp, c);
-                const double zc = __shfl_sync(FULL, my, c);
-                if (ok && c < nt) a = fma((double)Ur[lc], zc, a);
-            }
-            if (ok) z[r + row] -= a;
-        }
-        __syncwarp();
+        if (lane < nt) z[u * ldz + T0 + lane] = my;
     }
 }
 
+// tile_upper: upper triangle of the tile (pivots through dinv), backward
+// substitution in place.
 template <typename T>
-__device__ void block_backward(const T* __restrict__ Ub, int w, int r, int s, const int32_t* __restrict__ piv,
-                               const T* __restrict__ dinv, double* __restrict__ z, int lane) {
-    const int ntiles = (s + 31) / 32;
-    for (int tix = ntiles - 1; tix >= 0; --tix) {
-        const int T0 = tix * 32;
-        const int nt = min(32, s - T0);
-        const int lp = (lane < nt) ? piv[r + T0 + lane] - r : 0;
-        double my = (lane < nt) ? z[r + T0 + lane] : 0.0;
-        const double di = (lane < nt) ? (double)dinv[r + T0 + lane] : 0.0;
-        T Urow[32];
-        const T* Ui = Ub + (int64_t)(T0 + lane) * w;
+__device__ void tile_upper(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
+                           const T* __restrict__ dinv, double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+    const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
+    const double di = (lane < nt) ? (double)dinv[T0 + lane] : 0.0;
+    T Urow[32];
+    const T* Ui = Ub + (int64_t)(T0 - r + (lane < nt ? lane : 0)) * w;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-            const int lc = __shfl_sync(FULL, lp, c);
-            Urow[c] = (lane < nt && c > lane && c < nt) ? Ui[lc] : T(0);
-        }
-        // upper triangle of the tile, last row first
+    for (int c = 0; c < 32; ++c) {
+        const int lc = __shfl_sync(FULL, lp, c);
+        Urow[c] = (lane < nt && c > lane && c < nt) ? Ui[lc] : T(0);
+    }
+    for (int u = 0; u < nrhs; ++u) {
+        double my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
 #pragma unroll
         for (int c = 31; c >= 0; --c) {
             if (lane == c) my *= di;
             const double wc = __shfl_sync(FULL, my, c);
             if (lane < c) my -= (double)Urow[c] * wc;
         }
-        if (lane < nt) z[r + T0 + lane] = my;
-        // the rows above the tile
-        for (int R0 = 0; R0 < T0; R0 += 32) {
-            const int row = R0 + lane;          // R0 + 32 <= T0: every lane has a row
-            const T* Ur = Ub + (int64_t)row * w;
-            double a = 0.0;
-#pragma unroll
-            for (int c = 0; c < 32; ++c) {
-                const int lc = __shfl_sync(FULL, lp, c);
-                const double wc = __shfl_sync(FULL, my, c);
-                if (c < nt) a = fma((double)Ur[lc], wc, a);
-            }
-            z[r + row] -= a;
-        }
-        __syncwarp();
+        if (lane < nt) z[u * ldz + T0 + lane] = my;
     }
 }
 
@@ -936,12 +942,19 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         if (qi >= n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
         const int i = P.fwd_order[qi];
+        const unsigned long long tc0 = P.trace ? gtimer() : 0ull;
         const int D = P.node_of[i];
         const int L = P.fwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int q = P.node_inst ? P.node_inst[D] : 0;
         if (q != cq) { cq = q; cached = 0; }
         if (!__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
+        if (P.trace && lane == 0) {
+            // solve trace (debug): claim, level open, done, level
+            P.trace[4 * (int64_t)i] = tc0;
+            P.trace[4 * (int64_t)i + 1] = gtimer();
+            P.trace[4 * (int64_t)i + 3] = (unsigned long long)L;
+        }
         const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
         if (nrhs == 1) {
             const double a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), z, lane);
@@ -958,21 +971,34 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         }
         __threadfence();
         __syncwarp();
+        if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 2] = gtimer();
         if (s == 1) {
             if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
             continue;
         }
         if (lane == 0) st_release(P.fwd_row + i, gen);
-        if (i != e) continue;
-        // last row of the supernode: block solve once every row has its external part
+        // 32-row tiles of the block: the warp of a tile's last row owns it
+        const int T0 = r + ((i - r) & ~31);
+        const int tlast = min(T0 + 31, e);
+        if (i != tlast) continue;
+        const int nt = tlast - T0 + 1;
         int ok = 1;
-        for (int k = r + lane; k < e && ok; k += 32) ok = lane_wait(P.fwd_row + k, gen, P.status, k, limit);
+        for (int k = T0 + lane; k < tlast && ok; k += 32) ok = lane_wait(P.fwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
         const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
         const T* Ub = PV<T>(P) + P.node_panel_off[D];
-        for (int rr = 0; rr < nrhs; ++rr) block_forward<T>(Ub, w, r, s, P.piv, z + (int64_t)rr * n, lane);
+        // earlier tiles, each once its owner has published it
+        for (int K0 = r; K0 < T0; K0 += 32) {
+            if (!warp_wait(P.tile_f + K0 + 31, gen, P.status, K0 + 31, limit)) return;
+            tile_apply<T>(Ub, w, r, T0, nt, K0, 32, P.piv, z, n, nrhs, lane);
+        }
+        __syncwarp();
+        tile_lower<T>(Ub, w, r, T0, nt, P.piv, z, n, nrhs, lane);
         __threadfence();
         __syncwarp();
+        if (lane == 0) st_release(P.tile_f + tlast, gen);
+        if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 2] = gtimer();
+        if (tlast != e) continue;
         if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
     }
 }
@@ -1026,20 +1052,29 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
             continue;
         }
         if (lane == 0) st_release(P.bwd_row + i, gen);
-        if (i != r) continue;
+        // 32-row tiles of the block: the warp of a tile's first row owns it
+        const int T0 = r + ((i - r) & ~31);
+        if (i != T0) continue;
+        const int tl = min(T0 + 31, e);
+        const int nt = tl - T0 + 1;
         int ok = 1;
-        for (int k = r + 1 + lane; k <= e && ok; k += 32) ok = lane_wait(P.bwd_row + k, gen, P.status, k, limit);
+        for (int k = T0 + 1 + lane; k <= tl && ok; k += 32) ok = lane_wait(P.bwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
         const T* Ub = PV<T>(P) + P.node_panel_off[D];
-        for (int rr = 0; rr < nrhs; ++rr) {
-            double* zr = z + (int64_t)rr * n;
-            double* xr = xh + (int64_t)rr * n;
-            block_backward<T>(Ub, w, r, s, P.piv, dinv, zr, lane);
-            for (int p = r + lane; p <= e; p += 32) xr[P.piv[p]] = zr[p];
-            __syncwarp();
+        // later tiles, last first, each once its owner has published it
+        for (int K0 = r + ((e - r) & ~31); K0 > T0; K0 -= 32) {
+            if (!warp_wait(P.tile_b + K0, gen, P.status, K0, limit)) return;
+            tile_apply<T>(Ub, w, r, T0, nt, K0, min(32, e - K0 + 1), P.piv, z, n, nrhs, lane);
         }
+        __syncwarp();
+        tile_upper<T>(Ub, w, r, T0, nt, P.piv, dinv, z, n, nrhs, lane);
+        __syncwarp();
+        for (int rr = 0; rr < nrhs; ++rr)
+            if (lane < nt) xh[(int64_t)rr * n + P.piv[T0 + lane]] = z[(int64_t)rr * n + T0 + lane];
         __threadfence();
         __syncwarp();
+        if (lane == 0) st_release(P.tile_b + T0, gen);
+        if (T0 != r) continue;
         if (lane == 0) node_complete(P.bwd_done + P.bwd_off[q], P.bwd_count + P.bwd_off[q], L, P.wm_b + q);
     }
 }

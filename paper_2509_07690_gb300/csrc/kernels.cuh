@@ -77,6 +77,8 @@ struct DevPlan {
     int32_t n_inst;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
+    int32_t* tile_f;               // per 32-row tile of a supernode block (at its owner row):
+    int32_t* tile_b;               //   solved in the forward / backward substitution
     int32_t* pos;                  // per-warp column -> slot maps, pos_n each
     int32_t pos_n;                 // largest system of the plan (n for one system)
     const int32_t* node_base;      // per node: first row of its instance (null = 0)
