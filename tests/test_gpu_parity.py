@@ -20,7 +20,7 @@ def _torch():
     return torch
 
 
-def run_case(A, tol_factor=1e-10, nrhs=1, **opts):
+def run_case(A, tol_factor=1e-10, nrhs=1, expect_perturbed=False, **opts):
     torch = _torch()
     from paper_2509_07690_gb300 import Solver
     s = Solver(A.n, A.rowptr, A.col, A.val, **opts)
@@ -46,6 +46,8 @@ def run_case(A, tol_factor=1e-10, nrhs=1, **opts):
     info = s.get_info()
     assert info.device_status == 0
     assert info.nperturb == o.nperturb
+    if expect_perturbed:
+        assert info.nperturb > 0
     s.close()
     return rel
 
@@ -79,6 +81,25 @@ def test_sn_max_variants(sn_max):
 
 def test_multi_rhs():
     run_case(synth.grid5(20), nrhs=4)
+
+
+def test_eleven_rhs_tiled_blocks():
+    """More right-hand sides than one pass takes (8) through 256-row
+    supernode blocks solved by 32-row tiles."""
+    run_case(synth.convdiff3d(16), ordering=1, nrhs=11)
+
+
+def test_zero_pivots_perturbed():
+    """Natural order without matching: a tridiagonal matrix with a zero
+    diagonal meets an exact zero first pivot (Sec. 2.2 perturbation); the
+    count and the perturbed factors match the oracle, refinement recovers
+    the solution."""
+    n = 50
+    r = np.concatenate([np.arange(n - 1), np.arange(1, n), np.arange(n)])
+    c = np.concatenate([np.arange(1, n), np.arange(n - 1), np.arange(n)])
+    v = np.concatenate([np.ones(n - 1), np.ones(n - 1), np.zeros(n)])
+    A = synth.from_coo(n, r, c, v)
+    rel = run_case(A, static_pivot=0, ordering=2, sn_max=1, expect_perturbed=True)
 
 
 @pytest.mark.parametrize("seed", range(6))
