@@ -73,7 +73,7 @@ typedef struct {
                               check in FP64) with FP64 iterative refinement on every solve */
     double heavy_ratio;    /* rows whose update work is at least heavy_ratio x the mean row (and
                               at least 1e6 flops) are claimed first, from a queue of their own,
-                              by the warps of a subset of the SMs; 0 disables (32) */
+                              by two warps of every block; 0 disables (32) */
 } hylu_options;
 
 typedef struct {

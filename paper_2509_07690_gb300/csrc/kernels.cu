@@ -132,6 +132,7 @@ constexpr int PF = 16;             // leading tail entries prefetched per source
 constexpr int UNR = 8;             // independent 32-entry batches in flight
 constexpr int UNR_TAIL = 8;        // the same for the tails of standalone sources
 constexpr int DENSE_L_MIN = 256;   // rows with longer L lists use the dense per-warp L vector
+constexpr int HEAVY_WPB = 2;       // warps of every block that take the heavy rows first
 template <typename T>
 struct WarpSmem {
     T lb[SN_SMEM];            // source supernode: l by position
@@ -320,25 +321,19 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
     const double amax = __longlong_as_double(*reinterpret_cast<const long long*>(P.status + ST_AMAX));
     const double tau = tau_rel * amax;
     // Rows are claimed from two queues, each in dependency-level order.  The
-    // heavy rows form a queue of their own, served by every warp of a subset
-    // of the SMs sized to hold them all at once (at most half of the SMs), so
-    // that their FP64 work does not share pipes with the dependency chain the
-    // other SMs run, and by any warp that finds the main queue drained; every
-    // other row comes from the level-ordered main queue, which skips the
-    // heavy rows.  Progress holds: a claimed row waits only on
-    // rows of lower levels, and the lowest-level unfinished row is either
-    // claimed, or next in its queue, whose claimed rows are all ready.
-    unsigned smid, nsmid;
-    asm("mov.u32 %0, %%smid;" : "=r"(smid));
-    asm("mov.u32 %0, %%nsmid;" : "=r"(nsmid));
-    const int64_t nwarps = (int64_t)gridDim.x * FWARPS;
-    const int64_t hsm = min((int64_t)nsmid / 2, ((int64_t)P.n_heavy * nsmid + nwarps - 1) / nwarps);
-    bool heavy_open = (P.n_heavy > 0) && ((int64_t)smid < hsm);
+    // heavy rows form a queue of their own, served first by HEAVY_WPB warps of
+    // every block (spread over all SMs: a heavy row is bound by its
+    // sub-partition's FP64 pipe) and by any warp that finds the main queue
+    // drained; every other row comes from the level-ordered main queue, which
+    // skips the heavy rows.  Progress holds: a claimed row waits only on rows
+    // of lower levels, and the lowest-level unfinished row is either claimed,
+    // or next in its queue, whose claimed rows are all ready.
+    bool heavy_open = (P.n_heavy > 0) && (wid < HEAVY_WPB);
     bool main_open = true;
     // early claiming pays only when every heavy row gets a warp at once; with
-    // more heavy rows than half the warps (batches of many systems) they would
+    // more heavy rows than heavy warps (batches of many systems) they would
     // hold warps while waiting on their own chains: plain level order instead
-    const int hcap = ((int64_t)P.n_heavy <= nwarps / 2) ? P.n_heavy : 0;
+    const int hcap = ((int64_t)P.n_heavy <= (int64_t)HEAVY_WPB * gridDim.x) ? P.n_heavy : 0;
     heavy_open = heavy_open && hcap > 0;
     for (;;) {
         int i = -1;
@@ -567,6 +562,47 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                     if (lane == 0) lb[p] = lp;
                     __syncwarp();
                 }
+                // scatter one GEMV result into the row: a later L slot (by
+                // column in the dense L vector, through pos[], or, for a row
+                // whose L list fits one window, among the window columns) or
+                // the U part
+                auto put = [&](int c, T acc) {
+                    if (c < r) {
+                        if (spa) {
+                            atomicAdd(spa + c, -acc);
+                        } else {
+                            const int sl = need_pos ? pos[c] : t + bsearch_sm(wcol, cend, c);
+                            atomicAdd(xl + sl, -acc);
+                        }
+                    } else {
+                        pn.x[pn.idx(pos, c)] -= acc;
+                    }
+                };
+                if (sS <= 16) {
+                    // small source: 4 columns per lane, rows unrolled by 4, so
+                    // about 16 loads are in flight per lane
+                    for (int j0 = lane; j0 < nTS; j0 += 128) {
+                        T acc[4];
+                        const T* Uj[4];
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int j = j0 + 32 * jj;
+                            Uj[jj] = U + sS + (j < nTS ? j : j0);
+                            acc[jj] = T(0);
+                        }
+#pragma unroll 4
+                        for (int p = 0; p < sS; ++p) {
+                            const T lp = lb[p];
+#pragma unroll
+                            for (int jj = 0; jj < 4; ++jj) acc[jj] = fma(lp, Uj[jj][(int64_t)p * wS], acc[jj]);
+                        }
+#pragma unroll
+                        for (int jj = 0; jj < 4; ++jj) {
+                            const int j = j0 + 32 * jj;
+                            if (j < nTS) put(tcS[j], acc[jj]);
+                        }
+                    }
+                } else
                 for (int j = lane; j < nTS; j += 32) {
                     const T* Uj = U + sS + j;
                     const int c = tcS[j];
@@ -580,20 +616,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                         for (int u = 0; u < 8; ++u) ac[u] = fma(lb[p + u], Uj[(int64_t)(p + u) * wS], ac[u]);
                     }
                     for (; p < sS; ++p) ac[0] = fma(lb[p], Uj[(int64_t)p * wS], ac[0]);
-                    const T acc0 = ((ac[0] + ac[1]) + (ac[2] + ac[3])) + ((ac[4] + ac[5]) + (ac[6] + ac[7]));
-                    const T acc1 = T(0);
-                    if (c < r) {
-                        // later L slot of this row: through pos[], or, for a row
-                        // whose L list fits one window, among the window columns
-                        if (spa) {
-                            atomicAdd(spa + c, -(acc0 + acc1));
-                        } else {
-                            const int sl = need_pos ? pos[c] : t + bsearch_sm(wcol, cend, c);
-                            atomicAdd(xl + sl, -(acc0 + acc1));
-                        }
-                    } else {
-                        pn.x[pn.idx(pos, c)] -= acc0 + acc1;
-                    }
+                    put(c, ((ac[0] + ac[1]) + (ac[2] + ac[3])) + ((ac[4] + ac[5]) + (ac[6] + ac[7])));
                 }
                 for (int p = lane; p < sS; p += 32) xl[tt + p] = lb[p];
                 __threadfence();
