@@ -578,45 +578,29 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                         pn.x[pn.idx(pos, c)] -= acc;
                     }
                 };
-                if (sS <= 16) {
-                    // small source: 4 columns per lane, rows unrolled by 4, so
-                    // about 16 loads are in flight per lane
-                    for (int j0 = lane; j0 < nTS; j0 += 128) {
-                        T acc[4];
-                        const T* Uj[4];
+                // GEMV x[T_S] -= l U_S,T_S: 4 columns per lane, rows unrolled
+                // by 4, so about 16 loads are in flight per lane (the FP64
+                // instruction count is the same whatever the shape)
+                for (int j0 = lane; j0 < nTS; j0 += 128) {
+                    T acc[4];
+                    const T* Uj[4];
 #pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const int j = j0 + 32 * jj;
-                            Uj[jj] = U + sS + (j < nTS ? j : j0);
-                            acc[jj] = T(0);
-                        }
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = j0 + 32 * jj;
+                        Uj[jj] = U + sS + (j < nTS ? j : j0);
+                        acc[jj] = T(0);
+                    }
 #pragma unroll 4
-                        for (int p = 0; p < sS; ++p) {
-                            const T lp = lb[p];
+                    for (int p = 0; p < sS; ++p) {
+                        const T lp = lb[p];
 #pragma unroll
-                            for (int jj = 0; jj < 4; ++jj) acc[jj] = fma(lp, Uj[jj][(int64_t)p * wS], acc[jj]);
-                        }
-#pragma unroll
-                        for (int jj = 0; jj < 4; ++jj) {
-                            const int j = j0 + 32 * jj;
-                            if (j < nTS) put(tcS[j], acc[jj]);
-                        }
+                        for (int jj = 0; jj < 4; ++jj) acc[jj] = fma(lp, Uj[jj][(int64_t)p * wS], acc[jj]);
                     }
-                } else
-                for (int j = lane; j < nTS; j += 32) {
-                    const T* Uj = U + sS + j;
-                    const int c = tcS[j];
-                    // 8 independent accumulators: 8 loads of the column in flight
-                    T ac[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) ac[u] = T(0);
-                    int p = 0;
-                    for (; p + 8 <= sS; p += 8) {
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) ac[u] = fma(lb[p + u], Uj[(int64_t)(p + u) * wS], ac[u]);
+                    for (int jj = 0; jj < 4; ++jj) {
+                        const int j = j0 + 32 * jj;
+                        if (j < nTS) put(tcS[j], acc[jj]);
                     }
-                    for (; p < sS; ++p) ac[0] = fma(lb[p], Uj[(int64_t)p * wS], ac[0]);
-                    put(c, ((ac[0] + ac[1]) + (ac[2] + ac[3])) + ((ac[4] + ac[5]) + (ac[6] + ac[7])));
                 }
                 for (int p = lane; p < sS; p += 32) xl[tt + p] = lb[p];
                 __threadfence();
