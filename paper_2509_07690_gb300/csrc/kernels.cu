@@ -1114,6 +1114,75 @@ __global__ void permute_out_t_kernel(int32_t n, const int32_t* __restrict__ rowp
     }
 }
 
+// Transpose blocks by 32-position tiles, lanes over the destination tile's
+// positions: entry B(p, k) of U^T or L^T (k a source position) is row k of
+// the panel at the label of p, so each lane reads along the source rows
+// (Ub[(k - r) * w + piv[p] - r]).  Right-hand side u is h + u * ldh.
+//
+// tileT_apply: positions [T0, T0 + nt) take the finished values of the
+// source positions [K0, K0 + nk): h_p -= sum_c B(p, K0 + c) h_{K0 + c}.
+template <typename T>
+__device__ void tileT_apply(const T* __restrict__ Ub, int w, int r, int T0, int nt, int K0, int nk,
+                            const int32_t* __restrict__ piv, double* __restrict__ h, int64_t ldh, int nrhs,
+                            int lane) {
+    const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
+    T Rrow[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        Rrow[c] = (lane < nt && c < nk) ? Ub[(int64_t)(K0 + c - r) * w + lp] : T(0);
+    for (int u = 0; u < nrhs; ++u) {
+        const double vt = (lane < nk) ? h[u * ldh + K0 + lane] : 0.0;
+        double a = 0.0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) a = fma((double)Rrow[c], __shfl_sync(FULL, vt, c), a);
+        if (lane < nt) h[u * ldh + T0 + lane] -= a;
+    }
+}
+
+// tileT_lower: U^T on the tile (lower in positions, pivots 1 / u_pp by
+// position in dinv), forward substitution in place.
+template <typename T>
+__device__ void tileT_lower(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
+                            const T* __restrict__ dinv, double* __restrict__ h, int64_t ldh, int nrhs, int lane) {
+    const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
+    const double di = (lane < nt) ? (double)dinv[T0 + lane] : 0.0;
+    T Trow[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        Trow[c] = (lane < nt && c < lane) ? Ub[(int64_t)(T0 + c - r) * w + lp] : T(0);
+    for (int u = 0; u < nrhs; ++u) {
+        double my = (lane < nt) ? h[u * ldh + T0 + lane] : 0.0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+            if (lane == c) my *= di;
+            const double vc = __shfl_sync(FULL, my, c);
+            if (lane > c) my -= (double)Trow[c] * vc;
+        }
+        if (lane < nt) h[u * ldh + T0 + lane] = my;
+    }
+}
+
+// tileT_upper: L^T on the tile (upper in positions, unit diagonal), backward
+// substitution in place.
+template <typename T>
+__device__ void tileT_upper(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
+                            double* __restrict__ h, int64_t ldh, int nrhs, int lane) {
+    const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
+    T Trow[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+        Trow[c] = (lane < nt && c > lane && c < nt) ? Ub[(int64_t)(T0 + c - r) * w + lp] : T(0);
+    for (int u = 0; u < nrhs; ++u) {
+        double my = (lane < nt) ? h[u * ldh + T0 + lane] : 0.0;
+#pragma unroll
+        for (int c = 31; c >= 0; --c) {
+            const double uc = __shfl_sync(FULL, my, c);
+            if (lane < c) my -= (double)Trow[c] * uc;
+        }
+        if (lane < nt) h[u * ldh + T0 + lane] = my;
+    }
+}
+
 // U^T v = h by position (h is overwritten by v)
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
@@ -1142,24 +1211,26 @@ ut_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
         if (s == 1) {
             if (lane == 0) for (int rr = 0; rr < nrhs; ++rr) h[(int64_t)rr * n + i] *= (double)DI<T>(P)[i];
             __syncwarp();
-        } else if (i == r) {
-            // the block: v_p = (h_p - sum_{k in [r,p)} U(k, pos p) v_k) / u_pp
-            for (int rr = 0; rr < nrhs; ++rr) {
-                double* hr = h + (int64_t)rr * n;
-                for (int p = r; p <= e; ++p) {
-                    const int lp = P.piv[p] - r;
-                    double a = 0.0;
-                    for (int k = r + lane; k < p; k += 32) a = fma((double)Ub[(int64_t)(k - r) * w + lp], hr[k], a);
-                    for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                    if (lane == 0) hr[p] = (hr[p] - a) * (double)DI<T>(P)[p];
-                    __syncwarp();
-                }
-            }
-            __threadfence();
-            __syncwarp();
-            if (lane == 0) st_release(P.fwd_row + r, gen);
         } else {
-            if (!__all_sync(FULL, lane_wait(P.fwd_row + r, gen, P.status, r, limit))) return;
+            // the block by 32-position tiles: the warp of a tile's first row
+            // applies the finished earlier tiles and solves its triangle,
+            // v_p = (h_p - sum_{k in [r,p)} U(k, pos p) v_k) / u_pp; the other
+            // rows of the tile wait for it
+            const int T0 = r + ((i - r) & ~31);
+            const int nt = min(T0 + 31, e) - T0 + 1;
+            if (i == T0) {
+                for (int K0 = r; K0 < T0; K0 += 32) {
+                    if (!warp_wait(P.tile_f + K0, gen, P.status, K0, limit)) return;
+                    tileT_apply<T>(Ub, w, r, T0, nt, K0, 32, P.piv, h, n, nrhs, lane);
+                }
+                __syncwarp();
+                tileT_lower<T>(Ub, w, r, T0, nt, P.piv, DI<T>(P), h, n, nrhs, lane);
+                __threadfence();
+                __syncwarp();
+                if (lane == 0) st_release(P.tile_f + T0, gen);
+            } else {
+                if (!warp_wait(P.tile_f + T0, gen, P.status, T0, limit)) return;
+            }
         }
         // push row i's U tail: h[pos of label c] -= U(i, c) v_i
         const T* Ui = Ub + (int64_t)(i - r) * w + s;
@@ -1198,26 +1269,28 @@ lt_kernel(DevPlan P, double* __restrict__ h, int nrhs, long long limit) {
         if (q != cq) { cq = q; cached = 0; }
         if (!__all_sync(FULL, wait_level(P.wm_b + q, L, cached, P.status, limit))) return;
         if (s > 1) {
-            if (i == e) {
-                // the block: u_k = v_k - sum_{j in (k, e]} L(j, pos k) u_j
+            // the block by 32-position tiles, last tile first: the warp of a
+            // tile's last row applies the finished later tiles and solves its
+            // triangle, u_k = v_k - sum_{j in (k, e]} L(j, pos k) u_j; the
+            // other rows of the tile wait for it
+            const int T0 = r + ((i - r) & ~31);
+            const int tl = min(T0 + 31, e);
+            if (i == tl) {
                 const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
                 const T* Ub = PV<T>(P) + P.node_panel_off[D];
-                for (int rr = 0; rr < nrhs; ++rr) {
-                    double* hr = h + (int64_t)rr * n;
-                    for (int k = e - 1; k >= r; --k) {
-                        const int lk = P.piv[k] - r;
-                        double a = 0.0;
-                        for (int j = k + 1 + lane; j <= e; j += 32) a = fma((double)Ub[(int64_t)(j - r) * w + lk], hr[j], a);
-                        for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
-                        if (lane == 0) hr[k] -= a;
-                        __syncwarp();
-                    }
+                const int nt = tl - T0 + 1;
+                for (int K0 = r + ((e - r) & ~31); K0 > T0; K0 -= 32) {
+                    const int kl = min(K0 + 31, e);
+                    if (!warp_wait(P.tile_b + kl, gen, P.status, kl, limit)) return;
+                    tileT_apply<T>(Ub, w, r, T0, nt, K0, kl - K0 + 1, P.piv, h, n, nrhs, lane);
                 }
+                __syncwarp();
+                tileT_upper<T>(Ub, w, r, T0, nt, P.piv, h, n, nrhs, lane);
                 __threadfence();
                 __syncwarp();
-                if (lane == 0) st_release(P.bwd_row + e, gen);
+                if (lane == 0) st_release(P.tile_b + tl, gen);
             } else {
-                if (!__all_sync(FULL, lane_wait(P.bwd_row + e, gen, P.status, e, limit))) return;
+                if (!warp_wait(P.tile_b + tl, gen, P.status, tl, limit)) return;
             }
         }
         // push row i's L list: h[c] -= L(i, c) u_i (c by position)
