@@ -223,8 +223,14 @@ class Clocks:
 
 
 def kernel_hash() -> str:
+    """Hash of the source that determines the factor kernel: kernels.cu up to
+    its substitution section, plus launch_factor."""
     p = os.path.join(ROOT, "paper_2509_07690_gb300", "csrc", "kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    src = open(p).read()
+    i = src.index("// -------------------------------------------------------------- solve")
+    j = src.index("int launch_factor(")
+    k = src.index("\n}\n", j) + 3
+    return hashlib.sha256((src[:i] + src[j:k]).encode()).hexdigest()[:16]
 
 
 def profiled_traffic(workload: str, fp32: bool = False):
@@ -238,7 +244,7 @@ def profiled_traffic(workload: str, fp32: bool = False):
         if ":" in line and not line.startswith("#"):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip()
-    if kv.get("kernels_cu_sha256_16") != kernel_hash():
+    if kv.get("factor_source_sha256_16") != kernel_hash():
         return None
     try:
         return float(kv["dram_bytes_per_launch"])
