@@ -222,6 +222,16 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def measured_hbm_gbs() -> float:
+    """Measured HBM copy bandwidth of the target GPU (MEASURED_PEAKS.json at
+    the repository root), else 6.8 TB/s."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return float(json.load(open(p))["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6800.0
+
+
 def kernel_hash() -> str:
     """Hash of the source that determines the factor kernel: kernels.cu up to
     its substitution section, plus launch_factor."""
@@ -463,7 +473,12 @@ def run_hylu(args, ws, rank, local):
     t_total = allmax(ws, total_ms)
     value = t_fact / (ws * args.steps)
     kmean = statistics.mean(kern_ms)
+    smean = statistics.mean(solve_ms)
     achieved = flops / (kmean * 1e-3) / 1e12
+    hbm_peak = measured_hbm_gbs()
+    vbytes = 4 if fp32 else 8
+    hbm_factor_bytes = 6.0 * flops + 16.0 * A.nnz + (vbytes + 4.0) * info.nnz_store
+    solve_bytes = (vbytes + 4.0) * info.nnz_store + 6.0 * 8.0 * A.n
     # ---------------- end to end through host buffers
     h_vals = [torch.from_numpy(v.val).pin_memory() for v in sets]
     h_b = torch.from_numpy(b).pin_memory()
@@ -517,6 +532,18 @@ def run_hylu(args, ws, rank, local):
                          "traffic": profiled_traffic(WORKLOAD, fp32), "kernel": "factor_kernel",
                          "peak_source": peak_source,
                          "kernel_ms": kmean},
+            # the same factor kernel against HBM (12 B per U entry an update
+            # touches, 2 flops each, plus A in and the factors out), and the
+            # substitution kernels (each stored entry read once: value + index,
+            # plus six n-vectors per right-hand side)
+            "roofline_hbm": {"bound": "hbm", "kernel": "factor_kernel",
+                             "achieved": hbm_factor_bytes / (kmean * 1e-3) / 1e9, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": hbm_factor_bytes / (kmean * 1e-3) / 1e9 / hbm_peak,
+                             "bytes_per_launch": hbm_factor_bytes},
+            "solve_roofline": {"bound": "hbm", "kernel": "fwd_kernel+bwd_kernel",
+                               "achieved": solve_bytes / (smean * 1e-3) / 1e9, "peak": hbm_peak,
+                               "unit": "GB/s", "frac": solve_bytes / (smean * 1e-3) / 1e9 / hbm_peak,
+                               "bytes_per_solve": solve_bytes, "solve_kernel_ms": smean},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": int(A.nnz * 8 + A.n * 8),
                     "d2h_bytes_per_step": int(A.n * 8)},

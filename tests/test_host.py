@@ -210,3 +210,23 @@ def test_heavy_rows_selection():
     with pytest.raises(capi.HyluError) as e:
         capi.hylu_analyze(A.n, A.rowptr, A.col, A.val, None, capi.default_options(heavy_ratio=-1.0))
     assert e.value.code == -1
+
+
+def test_batch_plan_counts_sum_over_instances():
+    """The combined plan of a batch holds every instance (system x value set)
+    as its own block: rows, stored entries, flops and factor-kernel tasks
+    (rows plus supernode tail tasks) are the sums over the instances."""
+    from paper_2509_07690_gb300 import BatchSolver
+    mats = [synth.circuit(n, seed=600 + n) for n in (300, 1200, 2500)] + [synth.convdiff3d(8)]
+    singles = [Solver(m.n, m.rowptr, m.col, m.val) for m in mats]
+    nsets = 3
+    bs = BatchSolver([(m.n, m.rowptr, m.col, m.val) for m in mats], nsets)
+    info = bs.get_info()
+    assert info.n == nsets * sum(m.n for m in mats)
+    assert info.nnz_store == nsets * sum(s.info.nnz_store for s in singles)
+    assert info.flops == nsets * sum(s.info.flops for s in singles)
+    assert info.ntasks == nsets * sum(s.info.ntasks for s in singles)
+    assert info.ntasks > info.n or all(s.info.ntasks == s.info.n for s in singles)
+    for s in singles:
+        s.close()
+    bs.close()
