@@ -520,6 +520,8 @@ def run_hylu(args, ws, rank, local):
                        "value_sets": VALUE_SETS, "flops": flops, "nnz_lu": info.nnz_lu,
                        "nnz_store": info.nnz_store, "supernodes": info.nsupernodes,
                        "rows_in_supernodes": info.rows_in_supernodes,
+                       "critical_path_levels": {"factor": info.factor_levels, "forward": info.fwd_levels,
+                                                "backward": info.bwd_levels},
                        "l2": f"factor storage {info.nnz_store * 8 / 1e9:.2f} GB > 126 MB L2, no flush",
                        "parallelism": f"replicas x{ws}"},
             "gflops": flops / (value * 1e-3) / 1e9,

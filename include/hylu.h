@@ -97,6 +97,9 @@ typedef struct {
     double factor_kernel_ms; /* last factorization kernel (opt.timing = 1), else -1 */
     double solve_kernel_ms;  /* last substitution kernels (opt.timing = 1), else -1  */
     int32_t nheavy;          /* rows the factor kernel claims first (see heavy_ratio) */
+    int32_t factor_levels;   /* dependency levels of the factor kernel's tasks (critical-path length) */
+    int32_t fwd_levels;      /* node levels of the forward / backward substitution (for a batch, */
+    int32_t bwd_levels;      /*   the largest over its instances)                                 */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */

@@ -46,7 +46,8 @@ class Info(C.Structure):
                 ("backward_error", C.c_double), ("device_status", C.c_int32),
                 ("failed_node", C.c_int32), ("analyze_ms", C.c_double),
                 ("factor_kernel_ms", C.c_double), ("solve_kernel_ms", C.c_double),
-                ("nheavy", C.c_int32)]
+                ("nheavy", C.c_int32), ("factor_levels", C.c_int32), ("fwd_levels", C.c_int32),
+                ("bwd_levels", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

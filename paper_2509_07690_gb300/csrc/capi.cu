@@ -480,6 +480,15 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->max_supernode = mx;
     info->ntasks = P.n + P.n_tasks;
     info->nheavy = (int32_t)P.heavy_order.size();
+    info->factor_levels = P.row_levels;
+    auto levels = [](const std::vector<int32_t>& off, const std::vector<int32_t>& cnt) {
+        if (off.size() < 2) return (int32_t)cnt.size();
+        int32_t m = 0;
+        for (size_t q = 0; q + 1 < off.size(); ++q) m = std::max(m, off[q + 1] - off[q]);
+        return m;
+    };
+    info->fwd_levels = levels(P.fwd_off, P.fwd_count);
+    info->bwd_levels = levels(P.bwd_off, P.bwd_count);
     info->flops = P.flops_unpadded;
     info->flops_padded = P.flops_padded;
     info->analyze_ms = P.analyze_ms;

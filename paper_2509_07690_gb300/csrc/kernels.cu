@@ -949,19 +949,12 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         if (qi >= n) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
         const int i = P.fwd_order[qi];
-        const unsigned long long tc0 = P.trace ? gtimer() : 0ull;
         const int D = P.node_of[i];
         const int L = P.fwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int q = P.node_inst ? P.node_inst[D] : 0;
         if (q != cq) { cq = q; cached = 0; }
         if (!__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
-        if (P.trace && lane == 0) {
-            // solve trace (debug): claim, level open, done, level
-            P.trace[4 * (int64_t)i] = tc0;
-            P.trace[4 * (int64_t)i + 1] = gtimer();
-            P.trace[4 * (int64_t)i + 3] = (unsigned long long)L;
-        }
         const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
         if (nrhs == 1) {
             const double a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), z, lane);
@@ -978,7 +971,6 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         }
         __threadfence();
         __syncwarp();
-        if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 2] = gtimer();
         if (s == 1) {
             if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
             continue;
@@ -1004,7 +996,6 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(P.tile_f + tlast, gen);
-        if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 2] = gtimer();
         if (tlast != e) continue;
         if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
     }
