@@ -233,14 +233,20 @@ def measured_hbm_gbs() -> float:
 
 
 def kernel_hash() -> str:
-    """Hash of the source that determines the factor kernel: kernels.cu up to
-    its substitution section, plus launch_factor."""
+    """Hash of the code that determines the factor kernel: kernels.cu up to
+    its substitution section, plus launch_factor, without comments and blank
+    lines."""
     p = os.path.join(ROOT, "paper_2509_07690_gb300", "csrc", "kernels.cu")
     src = open(p).read()
     i = src.index("// -------------------------------------------------------------- solve")
     j = src.index("int launch_factor(")
     k = src.index("\n}\n", j) + 3
-    return hashlib.sha256((src[:i] + src[j:k]).encode()).hexdigest()[:16]
+    code = []
+    for line in (src[:i] + src[j:k]).splitlines():
+        line = line.split("//", 1)[0].rstrip()
+        if line:
+            code.append(line)
+    return hashlib.sha256("\n".join(code).encode()).hexdigest()[:16]
 
 
 def profiled_traffic(workload: str, fp32: bool = False):

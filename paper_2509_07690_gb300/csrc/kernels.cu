@@ -1,24 +1,27 @@
 // Numeric factorization and substitution kernels for sm_103a (HYLU Sec. 2.2,
 // 2.2.1 and 2.3).
 //
-// Factorization: one persistent kernel; every warp claims the next row in
-// ascending order from an atomic counter and runs the up-looking update of
-// that row (Sec. 2.2, Fig. 1):
+// Factorization: one persistent kernel whose warps claim tasks from two
+// dependency-level-ordered queues (heavy rows first on two warps of every
+// block, everything else from the main queue).  A row task runs the
+// up-looking update of its row (Sec. 2.2, Fig. 1):
 //   - Ahat(i,:) is scattered (scaled) straight into the row's storage;
 //   - each source in the row's L list, in ascending order, is waited for on
 //     its ready flag and applied: a standalone source row is a row-row update
 //     (one multiplier, a sparse axpy over its U tail), a source supernode is
 //     a sup-row update (a triangular solve with its dense diagonal block, then
 //     a dense matrix-vector product with its U tail);
-//   - a row inside a supernode then takes the updates of the earlier rows of
-//     its own supernode as soon as each is ready (the pipelined "dual mode"
-//     of Sec. 2.2.1 at row granularity), exchanges the largest entry of its
-//     diagonal block to the diagonal (supernode diagonal pivoting, Sec. 2.2)
-//     and perturbs a pivot below tau (Sec. 2.2);
-//   - the row publishes its ready flag with release semantics.
-// Claiming in ascending order makes every wait target a row that a running
-// warp has already claimed, so the schedule cannot deadlock; every wait is
-// still bounded by an iteration limit and reports HYLU_ERR_DEVICE_TIMEOUT.
+//   - a row inside a supernode then takes the diagonal-block updates of the
+//     earlier rows of its own supernode as soon as each is published (the
+//     pipelined mode of Sec. 2.2.1 at row granularity), exchanges the largest
+//     entry of its diagonal block to the diagonal (supernode diagonal
+//     pivoting) and perturbs a pivot below tau (Sec. 2.2);
+//   - the supernode's U tail is then solved by the unit lower diagonal block
+//     in tail tasks (or by the last row for a small node), which publish the
+//     node; a standalone row publishes itself.
+// A claimed task waits only on tasks of lower levels, so the schedule cannot
+// deadlock; every wait is still bounded by an iteration limit and reports
+// HYLU_ERR_DEVICE_TIMEOUT.
 //
 // Storage: row i's L values (by position) are contiguous; every node (a
 // supernode or a standalone row) keeps a dense panel s x (s + |tail|) whose
@@ -932,9 +935,10 @@ __device__ void tile_upper(const T* __restrict__ Ub, int w, int r, int T0, int n
 
 // Forward substitution L z = bhat (unit L, by position); z holds bhat on
 // entry.  Each warp claims the next row in level order, waits for the lower
-// levels, subtracts the row's L list; the warp of the LAST row of a supernode
-// then solves the unit lower block once all rows of the supernode have their
-// external part.  Right-hand sides are columns of z (stride n).
+// levels of its instance, subtracts the row's L list; the warp of the last
+// row of each 32-row tile of a supernode then solves the tile (tile_apply /
+// tile_lower) once its rows have their external part and the earlier tiles
+// are published.  Right-hand sides are columns of z (stride n).
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
@@ -1003,8 +1007,9 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
 
 // Backward substitution U w = z by position; the solution is written by
 // label: xh[piv[p]] = w_p.  Rows are claimed level by level (descending inside
-// a level); each subtracts its U tail, and the warp of the FIRST row of a
-// supernode then back-substitutes the block.  z is overwritten.
+// a level); each subtracts its U tail, and the warp of the first row of each
+// 32-row tile of a supernode then back-substitutes the tile once the later
+// tiles are published.  z is overwritten.
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
