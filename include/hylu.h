@@ -182,7 +182,10 @@ int hylu_batch_layout(hylu_handle* h, int32_t* row_base, int64_t* val_base, int3
  * previous hylu_factor and hylu_solve with at least nrhs right-hand sides (so
  * that nothing is allocated during capture), and a created stream (the legacy
  * default stream cannot be captured: HYLU_ERR_ARG).  The pointers are baked
- * into the graph. */
+ * into the graph; the values behind them are read afresh by every replay (the
+ * kernels' readiness generations live in device memory and advance on each
+ * replay), so new values written into d_vals / d_b between replays are
+ * factored and solved. */
 int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
                        void* stream);
 int hylu_graph_launch(hylu_handle* h, void* stream);
