@@ -187,12 +187,14 @@ struct Panel {
 // Update x with entries j in [j0, nTS) of a standalone source's tail, all with
 // multiplier l; entries with columns below r go to the L part (atomic adds to
 // global memory: no one reads them before the window moves past them and a
-// fence is taken), the others to the panel.  Loads of UNR batches are issued
-// before any update so that their latencies overlap.
+// fence is taken), the others to the panel, or, when spau is set (a row with
+// a dense L vector and a panel in global memory), to the dense vector by
+// column as well.  Loads of UNR batches are issued before any update so that
+// their latencies overlap.
 template <typename T>
 __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, const T* __restrict__ U1,
                                            int j0, int nTS, T l, int r, const int* pos, T* xl, T* spa,
-                                           const Panel<T>& pn, int lane) {
+                                           T* spau, const Panel<T>& pn, int lane) {
     for (int jb = j0; jb < nTS; jb += 32 * UNR_TAIL) {
         int c[UNR_TAIL];
         T u[UNR_TAIL];
@@ -205,11 +207,12 @@ __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, cons
         int ix[UNR_TAIL];
 #pragma unroll
         for (int m = 0; m < UNR_TAIL; ++m)
-            ix[m] = (c[m] >= r) ? pn.idx(pos, c[m]) : ((c[m] >= 0 && !spa) ? pos[c[m]] : -1);
+            ix[m] = (c[m] >= r) ? (spau ? -1 : pn.idx(pos, c[m])) : ((c[m] >= 0 && !spa) ? pos[c[m]] : -1);
 #pragma unroll
         for (int m = 0; m < UNR_TAIL; ++m) {
             if (c[m] < 0) continue;
             if (c[m] < r) atomicAdd(spa ? spa + c[m] : xl + ix[m], -l * u[m]);
+            else if (spau) atomicAdd(spau + c[m], -l * u[m]);
             else pn.x[ix[m]] -= l * u[m];
         }
     }
@@ -402,17 +405,27 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         T* spa = (nL > DENSE_L_MIN && SPA<T>(P)) ? SPA<T>(P) + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.pos_n
                                                       - (P.node_base ? P.node_base[D] : 0)
                                                  : nullptr;
-        const bool need_pos = (!spa && nL > 32) || (pn.mode == 2);
+        //      Such a row with its U part in global memory (mode 2) also
+        //      accumulates the U part in the dense vector (fire-and-forget
+        //      reductions, no slot lookup, no load before the store) and
+        //      gathers it into the panel after the last external update.
+        T* spau = (spa && pn.mode == 2) ? spa : nullptr;
+        const bool need_pos = (!spa && nL > 32) || (pn.mode == 2 && !spau);
         win[lane] = T(0);
         if (spa) { for (int t = 32 + lane; t < nL; t += 32) spa[lc[t]] = T(0); }
         else     { for (int t = 32 + lane; t < nL; t += 32) xl[t] = T(0); }
         if (need_pos) for (int t = lane; t < nL; t += 32) pos[lc[t]] = t;
-        for (int t = lane; t < range; t += 32) pn.x[t] = T(0);
+        if (spau) {
+            for (int c = lane; c < s; c += 32) spau[r + c] = T(0);
+            for (int j = lane; j < nT; j += 32) spau[tc[j]] = T(0);
+        } else {
+            for (int t = lane; t < range; t += 32) pn.x[t] = T(0);
+        }
         if (pn.mode == 1) {
             int* sc = const_cast<int*>(pn.scols);
             for (int j = lane; j < nT; j += 32) sc[j] = tc[j];
         }
-        if (pn.mode == 2) for (int j = lane; j < nT; j += 32) pos[tc[j]] = nL + s + j;
+        if (pn.mode == 2 && !spau) for (int j = lane; j < nT; j += 32) pos[tc[j]] = nL + s + j;
         __syncwarp();
         for (int64_t q = P.ah_rp[i] + lane; q < P.ah_rp[i + 1]; q += 32) {
             const int sl = P.ah_slot[q];
@@ -424,7 +437,8 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                 else xl[sl] = v;
             } else {
                 const int us = sl - nL;
-                pn.x[us < s ? us : pn.tail_idx(tc, us - s)] = v;
+                if (spau) spau[us < s ? r + us : tc[us - s]] = v;
+                else pn.x[us < s ? us : pn.tail_idx(tc, us - s)] = v;
             }
         }
         __syncwarp();
@@ -520,7 +534,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                 if (pl >= nTS) continue;
                 const int64_t tS = __shfl_sync(FULL, tq0, qq);
                 const int64_t pS = __shfl_sync(FULL, pq0, qq);
-                apply_tail<T>(P.tcols + tS, PV<T>(P) + pS + 1, pl, nTS, win[qq], r, pos, xl, spa, pn, lane);
+                apply_tail<T>(P.tcols + tS, PV<T>(P) + pS + 1, pl, nTS, win[qq], r, pos, xl, spa, spau, pn, lane);
                 __syncwarp();
             }
             // any L slot past this window may have received atomic adds
@@ -577,6 +591,8 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                             const int sl = need_pos ? pos[c] : t + bsearch_sm(wcol, cend, c);
                             atomicAdd(xl + sl, -acc);
                         }
+                    } else if (spau) {
+                        atomicAdd(spau + c, -acc);
                     } else {
                         pn.x[pn.idx(pos, c)] -= acc;
                     }
@@ -611,6 +627,15 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                 t = tt + sS;
                 pending = false;
             }
+        }
+        if (spau) {
+            // every reduction into the dense vector is complete (and read
+            // from L2, bypassing any line this warp cached for an earlier row)
+            __threadfence();
+            __syncwarp();
+            for (int c = lane; c < s; c += 32) pn.x[c] = __ldcg(spau + r + c);
+            for (int j = lane; j < nT; j += 32) pn.x[s + j] = __ldcg(spau + tc[j]);
+            __syncwarp();
         }
         if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 1] = gtimer();
         const unsigned long long waited_ext = waited;
