@@ -1,0 +1,56 @@
+"""bench.py's host-side helpers: the factor-code hash ignores comments and
+blank lines but not code, and the committed traffic profile is used only
+while that hash matches."""
+import os
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def _hash_of(src, tmp_path, monkeypatch):
+    d = tmp_path / "paper_2509_07690_gb300" / "csrc"
+    d.mkdir(parents=True)
+    (d / "kernels.cu").write_text(src)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    return bench.kernel_hash()
+
+
+SRC = """int a = 1;
+// -------------------------------------------------------------- solve
+int b = 2;
+int launch_factor(int x) {
+    return x;
+}
+"""
+
+
+def test_factor_hash_ignores_comments_not_code(tmp_path, monkeypatch):
+    h0 = _hash_of(SRC, tmp_path / "a", monkeypatch)
+    h1 = _hash_of(SRC.replace("int a = 1;", "// note\nint a = 1;  // one\n\n"), tmp_path / "b", monkeypatch)
+    h2 = _hash_of(SRC.replace("int a = 1;", "int a = 2;"), tmp_path / "c", monkeypatch)
+    h3 = _hash_of(SRC.replace("int b = 2;", "int b = 3;"), tmp_path / "d", monkeypatch)
+    assert h0 == h1                 # comments and blank lines do not count
+    assert h0 != h2                 # factor code does
+    assert h0 == h3                 # the substitution section does not
+
+
+def test_traffic_only_with_matching_hash(tmp_path, monkeypatch):
+    h = _hash_of(SRC, tmp_path, monkeypatch)
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    f = prof / "factor_kernel_w.txt"
+    f.write_text(f"# c\nfactor_source_sha256_16: {h}\ndram_bytes_per_launch: 123\n")
+    assert bench.profiled_traffic("w") == 123.0
+    f.write_text("factor_source_sha256_16: 0000000000000000\ndram_bytes_per_launch: 123\n")
+    assert bench.profiled_traffic("w") is None
+    assert bench.profiled_traffic("absent") is None
+
+
+def test_measured_hbm_peak_read_or_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_hbm_gbs() == 6800.0
+    (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6787.6}')
+    assert bench.measured_hbm_gbs() == 6787.6
