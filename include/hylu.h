@@ -204,6 +204,12 @@ int hylu_get_info(hylu_handle* h, hylu_info* info);
 int hylu_export_perm(hylu_handle* h, int32_t* rowperm, int32_t* colperm, double* dr, double* dc,
                      int32_t* sn_start);
 
+/* Claim schedule of the factor kernel (HOST arrays, any may be NULL; for
+ * analysis and tests): order int32[info.ntasks] (entries < n are rows, entry
+ * n + t is tail task t), heavy int32[info.nheavy] (the heavy-row queue),
+ * task_node int32[info.ntasks - n] (the supernode each tail task solves). */
+int hylu_export_schedule(hylu_handle* h, int32_t* order, int32_t* heavy, int32_t* task_node);
+
 /* Padded storage pattern in CSR form (HOST arrays, any may be NULL):
  * rowptr int64[n+1], col int32[info.nnz_store]; columns sorted per row. */
 int hylu_export_pattern(hylu_handle* h, int64_t* rowptr, int32_t* col);

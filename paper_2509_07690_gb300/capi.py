@@ -79,6 +79,7 @@ def load():
     lib.hylu_get_info.argtypes = [H, C.POINTER(Info)]
     lib.hylu_export_perm.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hylu_export_pattern.argtypes = [H, C.c_void_p, C.c_void_p]
+    lib.hylu_export_schedule.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hylu_export_factors.argtypes = [H, C.c_void_p, C.c_void_p]
     lib.hylu_destroy.argtypes = [H]
     lib.hylu_launch_count.restype = C.c_int64
@@ -166,6 +167,14 @@ def hylu_export_pattern(h: int, n: int, nnz_store: int):
     ci = np.empty(nnz_store, np.int32)
     _check(load().hylu_export_pattern(h, _ptr(rp), _ptr(ci)), "hylu_export_pattern")
     return rp, ci
+
+
+def hylu_export_schedule(h: int, n: int, ntasks: int, nheavy: int):
+    order = np.empty(ntasks, np.int32)
+    heavy = np.empty(max(nheavy, 0), np.int32)
+    task_node = np.empty(ntasks - n, np.int32)
+    _check(load().hylu_export_schedule(h, _ptr(order), _ptr(heavy), _ptr(task_node)), "hylu_export_schedule")
+    return order, heavy, task_node
 
 
 def hylu_export_factors(h: int, n: int, nnz_store: int):

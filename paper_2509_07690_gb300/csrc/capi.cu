@@ -519,6 +519,15 @@ int hylu_export_perm(hylu_handle* h, int32_t* rowperm, int32_t* colperm, double*
     return HYLU_OK;
 }
 
+int hylu_export_schedule(hylu_handle* h, int32_t* order, int32_t* heavy, int32_t* task_node) {
+    if (!h) return HYLU_ERR_ARG;
+    const hylu::Plan& P = h->P;
+    if (order) std::memcpy(order, P.row_order.data(), sizeof(int32_t) * P.row_order.size());
+    if (heavy) std::memcpy(heavy, P.heavy_order.data(), sizeof(int32_t) * P.heavy_order.size());
+    if (task_node) std::memcpy(task_node, P.task_node.data(), sizeof(int32_t) * P.task_node.size());
+    return HYLU_OK;
+}
+
 int hylu_export_pattern(hylu_handle* h, int64_t* rowptr, int32_t* col) {
     if (!h) return HYLU_ERR_ARG;
     const hylu::Plan& P = h->P;
