@@ -62,9 +62,11 @@ void amd_order(const CsrPattern& g, std::vector<int32_t>& perm, double dense_fac
     std::vector<std::vector<int32_t>> E(n), A(n), L(n);
     std::vector<int8_t> st(n, VAR);
     std::vector<int32_t> nv(n, 1), parent(n, -1), chain_next(n, -1), chain_last(n);
-    std::vector<int64_t> lw(n, 0);          // weighted |L_e| of element e
-    std::vector<int64_t> w(n, 0);
-    std::vector<int32_t> wflag(n, -1), mark(n, -1);
+    // per element e: lw = weighted |L_e|, w = |L_e \ L_p| while flag == the
+    // current stamp (one record, so an element costs one cache line)
+    struct ElemW { int32_t lw, w, flag; };
+    std::vector<ElemW> ew(n, ElemW{0, 0, -1});
+    std::vector<int32_t> mark(n, -1);
     std::vector<int32_t> elim_order;        // pivots (principal variables) in order
     for (int32_t i = 0; i < n; ++i) chain_last[i] = i;
 
@@ -116,20 +118,25 @@ void amd_order(const CsrPattern& g, std::vector<int32_t>& perm, double dense_fac
         for (int32_t j : Lp) {
             for (int32_t e : E[j]) {
                 if (st[e] != ELEM || e == p) continue;
-                if (wflag[e] != stamp) { wflag[e] = stamp; w[e] = lw[e] - nv[j]; }
-                else w[e] -= nv[j];
+                ElemW& x = ew[e];
+                if (x.flag != stamp) { x.flag = stamp; x.w = x.lw - nv[j]; }
+                else x.w -= nv[j];
             }
         }
         // ---- degree update, pruning, aggressive absorption
+        //      (the supervariable hash, the sum of the pruned E_j and A_j, is
+        //      taken in the same pass)
         for (int32_t j : Lp) {
-            int64_t sum = 0;
+            int64_t sum = 0, h = p;
             std::vector<int32_t>& Ej = E[j];
             size_t k = 0;
             for (int32_t e : Ej) {
                 if (st[e] != ELEM || e == p) continue;
-                int64_t we = (wflag[e] == stamp) ? w[e] : lw[e];
+                const ElemW& x = ew[e];
+                int64_t we = (x.flag == stamp) ? x.w : x.lw;
                 if (we == 0) { st[e] = DEAD; parent[e] = p; std::vector<int32_t>().swap(L[e]); continue; }
                 sum += we;
+                h += e;
                 Ej[k++] = e;
             }
             Ej.resize(k);
@@ -139,21 +146,17 @@ void amd_order(const CsrPattern& g, std::vector<int32_t>& perm, double dense_fac
             for (int32_t a : Aj) {
                 if (st[a] != VAR || mark[a] == stamp) continue;   // in L_p, p itself, merged, dense
                 sum += nv[a];
+                h += a;
                 Aj[k++] = a;
             }
             Aj.resize(k);
+            hashv[j] = h;
             int64_t ext = degp - nv[j];
             int64_t d = std::min<int64_t>({nleft - nv[j], (int64_t)bk.deg[j] + ext, sum + ext});
             if (d < 0) d = 0;
             bk.deg[j] = (int32_t)d;
         }
         // ---- supervariable detection among L_p
-        for (int32_t j : Lp) {
-            int64_t h = 0;
-            for (int32_t e : E[j]) h += e;
-            for (int32_t a : A[j]) h += a;
-            hashv[j] = h;
-        }
         std::vector<int32_t> order(Lp);
         std::sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
             return hashv[a] != hashv[b] ? hashv[a] < hashv[b] : a < b;
@@ -165,6 +168,12 @@ void amd_order(const CsrPattern& g, std::vector<int32_t>& perm, double dense_fac
                 int32_t i = order[a];
                 if (st[i] != VAR) continue;
                 ++stamp;
+                bool cand = false;              // mark only when a candidate could match
+                for (size_t b = a + 1; b < t && !cand; ++b) {
+                    int32_t j = order[b];
+                    cand = st[j] == VAR && E[j].size() == E[i].size() && A[j].size() == A[i].size();
+                }
+                if (!cand) continue;
                 for (int32_t e : E[i]) mark[e] = stamp;
                 for (int32_t x : A[i]) mark[x] = stamp;
                 for (size_t b = a + 1; b < t; ++b) {
@@ -189,15 +198,16 @@ void amd_order(const CsrPattern& g, std::vector<int32_t>& perm, double dense_fac
         }
         // ---- element p, reinsert principal variables
         std::vector<int32_t>& Le = L[p];
-        lw[p] = 0;
+        int64_t lwp = 0;
         for (int32_t j : Lp) {
             if (st[j] != VAR) continue;
             Le.push_back(j);
-            lw[p] += nv[j];
+            lwp += nv[j];
             int32_t d = bk.deg[j];
             if (d > nleft) d = (int32_t)nleft;
             bk.insert(j, d);
         }
+        ew[p].lw = (int32_t)lwp;
         stamp += 1;
     }
     // ---- postorder of the assembly tree (element parent = absorbing pivot)
