@@ -89,11 +89,10 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
         }
     }
     // ---- symbolic factorization, supernodes, padded nodes
-    std::vector<int64_t> frp, fdiag;
-    std::vector<int32_t> fci;
-    symbolic_rows(ah, frp, fci, fdiag);
-    supernode_partition(n, frp, fci, fdiag, std::max(1, opt.sn_max), P.sn_start);
-    build_nodes(P, frp, fci, fdiag);
+    SymbolicRows F;
+    symbolic_rows(ah, F);
+    supernode_partition(n, F, std::max(1, opt.sn_max), P.sn_start);
+    build_nodes(P, F);
     split_heavy_rows(P, opt.heavy_ratio);
     // ---- Ahat entries -> slots of their row: [0, nL) the L list, then the
     //      node's block (s slots) and tail

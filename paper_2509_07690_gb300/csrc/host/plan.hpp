@@ -107,11 +107,19 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
 // level-ordered row_order.
 void split_heavy_rows(Plan& P, double heavy_ratio);
 
-void symbolic_rows(const CsrPattern& ahat, std::vector<int64_t>& frp, std::vector<int32_t>& fci,
-                   std::vector<int64_t>& fdiag);
-void supernode_partition(int32_t n, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
-                         const std::vector<int64_t>& fdiag, int32_t sn_max, std::vector<int32_t>& start);
-void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
-                 const std::vector<int64_t>& fdiag);
+// Unpadded structure of L and U (row i of the up-looking factorization):
+// U(i, >=i) sorted, starting with i itself, and L(i, <i) as sorted, disjoint
+// runs of consecutive columns [lrun_first, lrun_first + lrun_len).
+struct SymbolicRows {
+    std::vector<int64_t> urp;            // n + 1 into uci
+    std::vector<int32_t> uci;
+    std::vector<int64_t> lrp;            // n + 1 into the run arrays
+    std::vector<int32_t> lrun_first, lrun_len;
+    int64_t nnz_l = 0;                   // unpadded entries of L (strictly lower)
+};
+
+void symbolic_rows(const CsrPattern& ahat, SymbolicRows& F);
+void supernode_partition(int32_t n, const SymbolicRows& F, int32_t sn_max, std::vector<int32_t>& start);
+void build_nodes(Plan& P, const SymbolicRows& F);
 
 }  // namespace hylu

@@ -2,12 +2,19 @@
 // the node/task tables of the numeric phase (HYLU Sec. 2.1 and Sec. 2.2).
 //
 // Row structure (up-looking): row i holds Ahat(i,:), i, and for every k < i it
-// holds, U(k, >k).  Rows are found by depth-first search over the graph of U
-// from the lower entries of Ahat(i,:).  The search follows a pruned adjacency
-// (Eisenstat and Liu): once a row p with L(p,k) != 0 and U(k,p) != 0 has been
-// built, U(k, >p) is contained in U(p,:), so the search from k may stop at p.
-// This gives the same sets as the plain closure in far less time.
+// holds, U(k, >k).  Rows are found by a search over the graph of U from the
+// lower entries of Ahat(i,:), with two reductions that leave the sets as they
+// are:
+//   - symmetric pruning (Eisenstat and Liu): once a row p with L(p,k) != 0 and
+//     U(k,p) != 0 has been built, U(k, >p) is contained in U(p,:), so the
+//     search through k may stop at p;
+//   - chains: when U(k+1,:) = U(k,:) \ {k} for k = a..e-1, every U(k, >k) in
+//     the chain is {k+1..e} plus U(e, >e).  Reaching any k of it puts k..e
+//     into L(i,:) at once, and only U(e, >e) is searched.
+// L(i,:) is kept as runs of consecutive columns; U(i,:) is the union of the
+// sorted lists searched, merged.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <cstring>
 #include <vector>
@@ -16,70 +23,162 @@
 
 namespace hylu {
 
-void symbolic_rows(const CsrPattern& ahat, std::vector<int64_t>& frp, std::vector<int32_t>& fci,
-                   std::vector<int64_t>& fdiag) {
+void symbolic_rows(const CsrPattern& ahat, SymbolicRows& F) {
     const int32_t n = ahat.n;
-    frp.assign(n + 1, 0);
-    fci.clear();
-    fci.reserve((size_t)ahat.rp[n] * 4 + n);
-    fdiag.assign(n, 0);
-    std::vector<int64_t> prune_end(n, -1);     // end (exclusive) of the traversed part of U(k,:)
+    F.urp.assign(n + 1, 0);
+    F.uci.clear();
+    F.uci.reserve((size_t)ahat.rp[n] * 2 + n);
+    F.lrp.assign(n + 1, 0);
+    F.lrun_first.clear();
+    F.lrun_len.clear();
+    F.nnz_l = 0;
+    std::vector<int64_t>& urp = F.urp;
+    std::vector<int32_t>& uci = F.uci;
+    std::vector<int64_t> prune_end(n, -1);      // end (exclusive) of the searched part of U(k,:)
     std::vector<int32_t> mark(n, -1);
-    std::vector<int32_t> lset, uset;
-    std::vector<std::pair<int32_t, int64_t>> stack;
+    std::vector<int32_t> chain_first(n), chain_end(n);
+    std::vector<int32_t> uset, ubuf, ends, work, merged;
+    std::vector<std::pair<int32_t, int32_t>> runs;   // L runs: (first column, count)
+    std::vector<size_t> ucut, ncut;                  // boundaries of the sorted runs of uset
     for (int32_t i = 0; i < n; ++i) {
-        lset.clear(); uset.clear();
-        mark[i] = i; uset.push_back(i);
+        uset.clear(); runs.clear(); ends.clear(); work.clear(); ucut.clear();
+        mark[i] = i;
+        uset.push_back(i);
+        auto visit = [&](int32_t k) {                // k < i, not yet in row i
+            const int32_t e = chain_end[chain_first[k]];
+            int32_t j = k;
+            while (j <= e && mark[j] != i) mark[j++] = i;
+            runs.push_back({k, j - k});
+            if (j > e) { work.push_back(e); ends.push_back(e); }
+        };
         for (int64_t q = ahat.rp[i]; q < ahat.rp[i + 1]; ++q) {
-            int32_t c = ahat.ci[q];
+            const int32_t c = ahat.ci[q];
             if (mark[c] == i) continue;
-            mark[c] = i;
-            if (c > i) { uset.push_back(c); continue; }
-            // DFS from c over the pruned U graph, collecting nodes < i
-            lset.push_back(c);
-            stack.clear();
-            stack.push_back({c, fdiag[c] + 1});
-            while (!stack.empty()) {
-                int32_t k = stack.back().first;
-                int64_t& it = stack.back().second;
-                int64_t end = prune_end[k] >= 0 ? prune_end[k] : frp[k + 1];
-                bool pushed = false;
-                while (it < end) {
-                    int32_t j = fci[it++];
-                    if (mark[j] == i) continue;
-                    mark[j] = i;
-                    if (j < i) { lset.push_back(j); stack.push_back({j, fdiag[j] + 1}); pushed = true; break; }
-                    uset.push_back(j);
-                }
-                if (!pushed) stack.pop_back();
+            if (c > i) { mark[c] = i; uset.push_back(c); continue; }
+            visit(c);
+        }
+        ucut.push_back(0);
+        if (work.size() > 1) {                       // the longest list first: one long sorted run
+            size_t best = 0;
+            int64_t bl = -1;
+            for (size_t t = 0; t < work.size(); ++t) {
+                const int32_t e = work[t];
+                const int64_t len = (prune_end[e] >= 0 ? prune_end[e] : urp[e + 1]) - urp[e];
+                if (len > bl) { bl = len; best = t; }
+            }
+            std::swap(work[best], work.back());
+        }
+        while (!work.empty()) {
+            const int32_t e = work.back();
+            work.pop_back();
+            if (uset.size() != ucut.back()) ucut.push_back(uset.size());
+            const int64_t end = prune_end[e] >= 0 ? prune_end[e] : urp[e + 1];
+            for (int64_t it = urp[e] + 1; it < end; ++it) {
+                const int32_t j = uci[it];
+                if (mark[j] == i) continue;
+                if (j < i) { visit(j); continue; }
+                mark[j] = i;
+                uset.push_back(j);
             }
         }
-        std::sort(lset.begin(), lset.end());
-        std::sort(uset.begin(), uset.end());
-        fci.insert(fci.end(), lset.begin(), lset.end());
-        fdiag[i] = (int64_t)fci.size();
-        fci.insert(fci.end(), uset.begin(), uset.end());
-        frp[i + 1] = (int64_t)fci.size();
-        // symmetric pruning of the sources of row i
-        for (int32_t k : lset) {
-            if (prune_end[k] >= 0) continue;
-            const int32_t* b = fci.data() + fdiag[k] + 1;
-            const int32_t* e = fci.data() + frp[k + 1];
-            const int32_t* f = std::lower_bound(b, e, i);
-            if (f != e && *f == i) prune_end[k] = (int64_t)(f - fci.data()) + 1;
+        if (uset.size() != ucut.back()) ucut.push_back(uset.size());
+        // ---- L: disjoint runs, sorted by their first column (or read off the
+        //      marks when the row is dense in its range)
+        if (!runs.empty()) {
+            int32_t lo = i;
+            int64_t nl = 0;
+            for (auto& r : runs) { lo = std::min(lo, r.first); nl += r.second; }
+            const double rs = (double)runs.size();
+            if (rs * (std::log2(rs) + 1.0) * 4.0 > (double)(i - lo)) {
+                runs.clear();
+                for (int32_t j = lo; j < i; ++j) {
+                    if (mark[j] != i) continue;
+                    int32_t t = j;
+                    while (t < i && mark[t] == i) ++t;
+                    runs.push_back({j, t - j});
+                    j = t;
+                }
+            } else {
+                std::sort(runs.begin(), runs.end());
+            }
+            for (auto& r : runs) { F.lrun_first.push_back(r.first); F.lrun_len.push_back(r.second); }
+            F.nnz_l += nl;
         }
+        F.lrp[i + 1] = (int64_t)F.lrun_first.size();
+        // ---- U: one long run plus short ones, pairwise merges, or the marks
+        if (ucut.size() > 2) {
+            const size_t R = ucut.size() - 1;
+            const double m = (double)uset.size();
+            size_t big = 0, bsz = 0;
+            int32_t hi = i;
+            for (size_t r = 0; r < R; ++r) {
+                if (ucut[r + 1] - ucut[r] > bsz) { bsz = ucut[r + 1] - ucut[r]; big = r; }
+                hi = std::max(hi, uset[ucut[r + 1] - 1]);
+            }
+            const double rest = m - (double)bsz;
+            const double c_pair = m * std::log2((double)R), c_big = m + rest * std::log2(rest + 2.0);
+            if (R > 2 && c_pair * 4.0 > (double)(hi - i)) {
+                int32_t* o = uset.data();
+                for (int32_t j = i; j <= hi; ++j) if (mark[j] == i) *o++ = j;
+            } else if (c_big < c_pair) {
+                ubuf.clear();
+                for (size_t r = 0; r < R; ++r)
+                    if (r != big) ubuf.insert(ubuf.end(), uset.begin() + ucut[r], uset.begin() + ucut[r + 1]);
+                std::sort(ubuf.begin(), ubuf.end());
+                merged.resize(uset.size());
+                std::merge(uset.begin() + ucut[big], uset.begin() + ucut[big + 1], ubuf.begin(), ubuf.end(),
+                           merged.begin());
+                uset.swap(merged);
+            } else {
+                while (ucut.size() > 2) {
+                    ubuf.resize(uset.size());
+                    ncut.assign(1, 0);
+                    size_t r = 0;
+                    for (; r + 2 < ucut.size(); r += 2) {
+                        std::merge(uset.begin() + ucut[r], uset.begin() + ucut[r + 1], uset.begin() + ucut[r + 1],
+                                   uset.begin() + ucut[r + 2], ubuf.begin() + ucut[r]);
+                        ncut.push_back(ucut[r + 2]);
+                    }
+                    if (r + 1 < ucut.size()) {
+                        std::copy(uset.begin() + ucut[r], uset.begin() + ucut[r + 1], ubuf.begin() + ucut[r]);
+                        ncut.push_back(ucut[r + 1]);
+                    }
+                    uset.swap(ubuf);
+                    ucut.swap(ncut);
+                }
+            }
+        }
+        uci.insert(uci.end(), uset.begin(), uset.end());
+        urp[i + 1] = (int64_t)uci.size();
+        // ---- symmetric pruning of the searched chain ends
+        for (int32_t k : ends) {
+            if (prune_end[k] >= 0) continue;
+            const int32_t* b = uci.data() + urp[k] + 1;
+            const int32_t* e = uci.data() + urp[k + 1];
+            const int32_t* f = std::lower_bound(b, e, i);
+            if (f != e && *f == i) prune_end[k] = (int64_t)(f - uci.data()) + 1;
+        }
+        // ---- chains: row i continues row i-1 when U(i,:) = U(i-1,:) \ {i-1}
+        bool cont = false;
+        if (i > 0) {
+            const int64_t lp = urp[i] - urp[i - 1], li = urp[i + 1] - urp[i];
+            cont = (lp - 1 == li) &&
+                   std::memcmp(uci.data() + urp[i - 1] + 1, uci.data() + urp[i], sizeof(int32_t) * li) == 0;
+        }
+        if (cont) { chain_first[i] = chain_first[i - 1]; chain_end[chain_first[i]] = i; }
+        else { chain_first[i] = i; chain_end[i] = i; }
     }
 }
 
-void supernode_partition(int32_t n, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
-                         const std::vector<int64_t>& fdiag, int32_t sn_max, std::vector<int32_t>& start) {
+void supernode_partition(int32_t n, const SymbolicRows& F, int32_t sn_max, std::vector<int32_t>& start) {
     start.clear();
     start.push_back(0);
     int32_t cur = 0;
     for (int32_t r = 0; r + 1 < n; ++r) {
-        int64_t lr = frp[r + 1] - fdiag[r], ln = frp[r + 2] - fdiag[r + 1];
-        bool same = (lr - 1 == ln) &&
-                    std::memcmp(fci.data() + fdiag[r] + 1, fci.data() + fdiag[r + 1], sizeof(int32_t) * ln) == 0;
+        const int64_t lr = F.urp[r + 1] - F.urp[r], ln = F.urp[r + 2] - F.urp[r + 1];
+        const bool same = (lr - 1 == ln) &&
+                          std::memcmp(F.uci.data() + F.urp[r] + 1, F.uci.data() + F.urp[r + 1],
+                                      sizeof(int32_t) * ln) == 0;
         if (!same || (r + 1 - cur) >= sn_max) { cur = r + 1; start.push_back(r + 1); }
     }
     start.push_back(n);
@@ -88,8 +187,7 @@ void supernode_partition(int32_t n, const std::vector<int64_t>& frp, const std::
 // Padded pattern (Sec. 2.2 storage, read as): each row keeps its own L
 // columns, widened to whole source supernodes; every node stores its rows'
 // diagonal block densely together with the shared U tail.
-void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int32_t>& fci,
-                 const std::vector<int64_t>& fdiag) {
+void build_nodes(Plan& P, const SymbolicRows& F) {
     const int32_t n = P.n;
     const int32_t nn = (int32_t)P.sn_start.size() - 1;
     P.nnodes = nn;
@@ -101,44 +199,61 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
     P.node_tail_off.assign(nn + 1, 0);
     P.node_panel_off.assign(nn + 1, 0);
     P.tcols.clear();
-    std::vector<char> in(n, 0);
-    std::vector<int32_t> lst;
+    // L columns of row i, ascending: every source node below the row's own
+    // node contributes its whole segment once (the L runs are ascending, so a
+    // node already taken is the last one taken).  Called once to count, once
+    // to fill.
+    auto row_segments = [&](int32_t i, int32_t r, auto&& take) {
+        int32_t last = -1;
+        for (int64_t q = F.lrp[i]; q < F.lrp[i + 1]; ++q) {
+            const int32_t a = F.lrun_first[q], b = std::min(a + F.lrun_len[q], r);
+            for (int32_t k = a; k < b;) {
+                const int32_t S = P.node_of[k];
+                if (S != last) { take(P.sn_start[S], P.sn_start[S + 1]); last = S; }
+                k = P.sn_start[S + 1];
+            }
+            if (b < a + F.lrun_len[q]) break;
+        }
+    };
     int64_t poff = 0;
     P.max_row = 0;
     for (int32_t s = 0; s < nn; ++s) {
-        int32_t r = P.sn_start[s], e = P.sn_start[s + 1] - 1, sz = e - r + 1;
-        for (int64_t q = fdiag[e] + 1; q < frp[e + 1]; ++q) P.tcols.push_back(fci[q]);
+        const int32_t r = P.sn_start[s], e = P.sn_start[s + 1] - 1, sz = e - r + 1;
+        for (int64_t q = F.urp[e] + 1; q < F.urp[e + 1]; ++q) P.tcols.push_back(F.uci[q]);
         P.node_tail_off[s + 1] = (int64_t)P.tcols.size();
-        int64_t w = sz + (P.node_tail_off[s + 1] - P.node_tail_off[s]);
+        const int64_t w = sz + (P.node_tail_off[s + 1] - P.node_tail_off[s]);
         P.node_panel_off[s] = poff;
         poff += w * sz;
         P.node_panel_off[s + 1] = poff;
         for (int32_t i = r; i <= e; ++i) {
-            lst.clear();
-            for (int64_t q = frp[i]; q < fdiag[i]; ++q) {
-                int32_t k = fci[q];
-                if (k >= r) break;
-                if (in[k]) continue;
-                int32_t S = P.node_of[k];
-                for (int32_t t = P.sn_start[S]; t < P.sn_start[S + 1]; ++t)
-                    if (!in[t]) { in[t] = 1; lst.push_back(t); }
-            }
-            std::sort(lst.begin(), lst.end());
-            for (int32_t t : lst) in[t] = 0;
-            P.lcols.insert(P.lcols.end(), lst.begin(), lst.end());
-            P.row_lptr[i + 1] = (int64_t)P.lcols.size();
-            P.max_row = std::max<int32_t>(P.max_row, (int32_t)(lst.size() + w));
+            int64_t cnt = 0;
+            row_segments(i, r, [&](int32_t s0, int32_t s1) { cnt += s1 - s0; });
+            P.row_lptr[i + 1] = P.row_lptr[i] + cnt;
+            P.max_row = std::max<int32_t>(P.max_row, (int32_t)(cnt + w));
         }
     }
+    P.lcols.resize(P.row_lptr[n]);
+    for (int32_t s = 0; s < nn; ++s)
+        for (int32_t i = P.sn_start[s]; i < P.sn_start[s + 1]; ++i) {
+            int32_t* o = P.lcols.data() + P.row_lptr[i];
+            row_segments(i, P.sn_start[s], [&](int32_t s0, int32_t s1) {
+                for (int32_t t = s0; t < s1; ++t) *o++ = t;
+            });
+        }
     P.nnz_l = (int64_t)P.lcols.size();
     P.nnz_panel = poff;
     P.nnz_store = P.nnz_l + P.nnz_panel;
     // flop counts (Sec. 2.1): one division per L(i,k) plus two per U(k, >k) entry
-    double fu = 0.0, fp = 0.0;
-    std::vector<int64_t> ulen(n);
-    for (int32_t i = 0; i < n; ++i) ulen[i] = frp[i + 1] - fdiag[i];
-    for (int32_t i = 0; i < n; ++i)
-        for (int64_t q = frp[i]; q < fdiag[i]; ++q) fu += 1.0 + 2.0 * (double)(ulen[fci[q]] - 1);
+    // (integer terms: the unpadded total is exact, summed over L runs by prefix sums)
+    double fp = 0.0;
+    std::vector<int64_t> ulen(n), upre(n + 1, 0);
+    for (int32_t i = 0; i < n; ++i) {
+        ulen[i] = F.urp[i + 1] - F.urp[i];
+        upre[i + 1] = upre[i] + 2 * ulen[i] - 1;
+    }
+    int64_t fu = 0;
+    for (size_t q = 0; q < F.lrun_first.size(); ++q)
+        fu += upre[F.lrun_first[q] + F.lrun_len[q]] - upre[F.lrun_first[q]];
     P.row_flops.assign(n, 0.0);
     for (int32_t i = 0; i < n; ++i) {
         double f = 0.0;
@@ -147,9 +262,9 @@ void build_nodes(Plan& P, const std::vector<int64_t>& frp, const std::vector<int
         P.row_flops[i] = f;
         fp += f;
     }
-    P.flops_unpadded = fu;
+    P.flops_unpadded = (double)fu;
     P.flops_padded = fp;
-    P.nnz_f = frp[n];
+    P.nnz_f = F.nnz_l + F.urp[n];
     // tail tasks: a 32-column group costs s^2 / 2 multiply-adds per lane; a
     // task takes about 512 of them (one group from s = 32 up), at most one
     // task per group.  A node whose whole tail is about one task's work (or

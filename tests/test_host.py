@@ -161,6 +161,51 @@ def test_pattern_parity_random_unsymmetric(seed):
     s.close()
 
 
+@pytest.mark.parametrize("seed", range(16))
+def test_pattern_parity_chains_and_dense_rows(seed):
+    """Dense diagonal blocks with one-sided couplings (long runs of rows whose
+    U structures nest, cut by pruning and unsymmetry at odd places) followed by
+    an arrowhead of dense rows and columns (rows dense over their whole range):
+    the symbolic shortcuts for chains and dense rows give the oracle's sets."""
+    rng = np.random.default_rng(1700 + seed)
+    nb = int(rng.integers(2, 7))
+    sizes = rng.integers(1, 24, nb)
+    n0 = int(sizes.sum())
+    h = int(rng.integers(1, 6))
+    n = n0 + h
+    a = np.zeros((n, n))
+    off = 0
+    for b in sizes:
+        blk = np.where(rng.random((b, b)) < 0.8, rng.uniform(-1, 1, (b, b)), 0.0)
+        a[off:off + b, off:off + b] = blk
+        if off > 0:                      # one-sided coupling to an earlier block
+            c = int(rng.integers(0, off))
+            if rng.random() < 0.5:
+                a[off + int(rng.integers(0, b)), c] = 0.5
+            else:
+                a[c, off + int(rng.integers(0, b))] = 0.5
+        off += b
+    for t in range(h):                  # arrowhead rows / columns, partly dense
+        r = n0 + t
+        a[r, :] = np.where(rng.random(n) < rng.uniform(0.3, 1.0), rng.uniform(-1, 1, n), 0.0)
+        a[:, r] = np.where(rng.random(n) < rng.uniform(0.3, 1.0), rng.uniform(-1, 1, n), a[:, r])
+    a[np.arange(n), np.arange(n)] += rng.uniform(2, 3, n)
+    A = _dense_csr(a)
+    perm = np.arange(n, dtype=np.int32)
+    if seed % 2:                        # scramble the blocks' interiors, keep the arrow last
+        perm[:n0] = rng.permutation(n0).astype(np.int32)
+    s = Solver(A.n, A.rowptr, A.col, A.val, perm, ordering=3, static_pivot=0,
+               sn_max=int(rng.choice([1, 3, 8, 256])))
+    o = oracle.Oracle(A.n, A.rowptr, A.col, A.val, perm, perm, None, None, sn_max=s.opt.sn_max, numeric=False)
+    prp, pci = s.export_pattern()
+    rp, cp, dr, dc, sn = s.export_perm()
+    assert np.array_equal(o.sn_start, sn)
+    assert np.array_equal(o.padded.col, pci) and np.array_equal(o.padded.rowptr, prp)
+    assert s.info.nnz_lu == len(o.unpadded.col)
+    assert s.info.flops == o.flops[0] and s.info.flops_padded == o.flops[1]
+    s.close()
+
+
 # ------------------------------------------------------------- errors
 def test_error_codes():
     rp = np.array([0, 2, 3], np.int64)
