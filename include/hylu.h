@@ -140,7 +140,11 @@ int hylu_refactor(hylu_handle* h, const double* d_vals, void* stream);
  * was perturbed (or opt.refine == 1) the solution is refined in FP64 on the
  * original A (Sec. 2.3) until the backward error reaches opt.refine_tol, stops
  * halving, or opt.refine_maxit corrections were made; this synchronizes the
- * stream.  Returns HYLU_WARN_REFINE_STALLED if the target was not reached. */
+ * stream.  Returns HYLU_WARN_REFINE_STALLED if the target was not reached.
+ * Workspace: the first call with more right-hand sides (or a larger ld) than
+ * any before allocates device buffers for it (about 2 n nrhs + 2 ld nrhs
+ * doubles); earlier buffers stay allocated until hylu_destroy, so a captured
+ * graph that points at them stays valid. */
 int hylu_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream);
 
 /* Transpose solve A^T x = b with the same factors (U^T then L^T), same
@@ -263,7 +267,8 @@ int hylu_solve_static(hylu_handle* h, const double* d_b, double* d_x, void* stre
  * the own supernode.  HYLU_ERR_STATE when tracing is off. */
 int hylu_debug_trace(hylu_handle* h, unsigned long long* out);
 
-/* Number of kernel launches this library has issued since it was loaded. */
+/* Number of kernel launches this library has issued since it was loaded (a
+ * graph replay counts the kernels recorded in it; recording counts none). */
 int64_t hylu_launch_count(void);
 
 /* Measure the FP64 fused multiply-add throughput of the current device (the

@@ -43,6 +43,7 @@ struct hylu_handle {
     hylu::BatchLayout layout;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
+    int64_t graph_launches = 0;          // kernel launches recorded into the graph
     int grid_max = 0;
     bool timed_factor = false, timed_solve = false;
 };
@@ -68,6 +69,19 @@ int upload(hylu_handle* h, T** p, const std::vector<T>& v, cudaStream_t st) {
 }
 
 #define TRY(x) do { int rc_ = (x); if (rc_ < 0) return rc_; } while (0)
+
+// No C++ exception crosses the C ABI: host allocation failures become
+// HYLU_ERR_NOMEM, anything else HYLU_ERR_INTERNAL.
+template <class F>
+int guarded(F&& f) {
+    try {
+        return f();
+    } catch (const std::bad_alloc&) {
+        return HYLU_ERR_NOMEM;
+    } catch (...) {
+        return HYLU_ERR_INTERNAL;
+    }
+}
 
 int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     if (h->uploaded) return HYLU_OK;
@@ -318,7 +332,7 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
         if (be <= h->opt.refine_tol) return HYLU_OK;
         if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
         be_prev = be;
-            TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
+        TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
                                h->d_dc, nrhs, ld, h->opt.spin_limit, h->grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
         ++h->refine_iters;
@@ -350,7 +364,7 @@ int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs,
         if (be <= h->opt.refine_tol) return HYLU_OK;
         if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
         be_prev = be;
-            TRY(hylu::launch_solve_transpose(P, h->d_r, h->d_d, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
+        TRY(hylu::launch_solve_transpose(P, h->d_r, h->d_d, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
                                          nrhs, ld, h->opt.spin_limit, h->grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
         ++h->refine_iters;
@@ -419,12 +433,7 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
     ao.nd_leaf = o.nd_leaf > 0 ? o.nd_leaf : 256;
     ao.amd_dense = o.amd_dense > 0 ? o.amd_dense : 2.0;
     ao.heavy_ratio = o.heavy_ratio;
-    int rc;
-    try {
-        rc = hylu::analyze(n, rowptr, col, vals, user_perm, ao, h->P);
-    } catch (const std::bad_alloc&) {
-        rc = HYLU_ERR_NOMEM;
-    }
+    const int rc = guarded([&] { return hylu::analyze(n, rowptr, col, vals, user_perm, ao, h->P); });
     if (rc) { delete h; return rc; }
     *out = h;
     return HYLU_OK;
@@ -432,23 +441,23 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
 
 int hylu_factor(hylu_handle* h, const double* d_vals, void* stream) {
     if (!h) return HYLU_ERR_ARG;
-    return do_factor(h, d_vals, static_cast<cudaStream_t>(stream));
+    return guarded([&] { return do_factor(h, d_vals, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_refactor(hylu_handle* h, const double* d_vals, void* stream) {
     if (!h) return HYLU_ERR_ARG;
     if (!h->factored) return HYLU_ERR_STATE;
-    return do_factor(h, d_vals, static_cast<cudaStream_t>(stream));
+    return guarded([&] { return do_factor(h, d_vals, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream) {
     if (!h) return HYLU_ERR_ARG;
-    return do_solve(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream));
+    return guarded([&] { return do_solve(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream) {
     if (!h) return HYLU_ERR_ARG;
-    return do_solve_transpose(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream));
+    return guarded([&] { return do_solve_transpose(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_grad_values(hylu_handle* h, const double* d_lam, const double* d_x, double* d_dvals, int nrhs, int ld,
@@ -543,7 +552,7 @@ int hylu_export_pattern(hylu_handle* h, int64_t* rowptr, int32_t* col) {
     return HYLU_OK;
 }
 
-int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv) {
+static int export_factors_impl(hylu_handle* h, double* vals, int32_t* piv) {
     if (!h) return HYLU_ERR_ARG;
     if (!h->factored) return HYLU_ERR_STATE;
     const hylu::Plan& P = h->P;
@@ -575,6 +584,10 @@ int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv) {
         for (int64_t t = 0; t < nT; ++t) vals[pos++] = row[s + t];
     }
     return HYLU_OK;
+}
+
+int hylu_export_factors(hylu_handle* h, double* vals, int32_t* piv) {
+    return guarded([&] { return export_factors_impl(h, vals, piv); });
 }
 
 int hylu_destroy(hylu_handle* h) {
@@ -617,11 +630,9 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
     for (unsigned t = 0; t < nt; ++t)
         th.emplace_back([&, t]() {
             for (int32_t s = (int32_t)t; s < k; s += (int32_t)nt) {
-                try {
-                    rcs[s] = hylu::analyze(n[s], rowptr[s], col[s], vals ? vals[s] : nullptr, nullptr, ao, plans[s]);
-                } catch (const std::bad_alloc&) {
-                    rcs[s] = HYLU_ERR_NOMEM;
-                }
+                rcs[s] = guarded([&] {
+                    return hylu::analyze(n[s], rowptr[s], col[s], vals ? vals[s] : nullptr, nullptr, ao, plans[s]);
+                });
             }
         });
     for (auto& t : th) t.join();
@@ -632,13 +643,11 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
     h->batch = true;
     std::vector<const hylu::Plan*> ps;
     for (auto& p : plans) ps.push_back(&p);
-    int rc;
-    try {
-        rc = hylu::combine(ps, nsets, h->P, h->layout);
-        if (rc == 0) hylu::split_heavy_rows(h->P, ao.heavy_ratio);
-    } catch (const std::bad_alloc&) {
-        rc = HYLU_ERR_NOMEM;
-    }
+    const int rc = guarded([&] {
+        const int r = hylu::combine(ps, nsets, h->P, h->layout);
+        if (r == 0) hylu::split_heavy_rows(h->P, ao.heavy_ratio);
+        return r;
+    });
     if (rc) { delete h; return rc < 0 ? rc : HYLU_ERR_INTERNAL; }
     *out = h;
     return HYLU_OK;
@@ -653,8 +662,8 @@ int hylu_batch_layout(hylu_handle* h, int32_t* row_base, int64_t* val_base, int3
     return HYLU_OK;
 }
 
-int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
-                       void* stream) {
+static int graph_capture_impl(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs,
+                              int ld, void* stream) {
     if (!h || !d_vals || !d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
     if (!h->factored || nrhs > h->cap_rhs || (size_t)ld * nrhs > h->cap_elems) return HYLU_ERR_STATE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -670,8 +679,11 @@ int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, 
         h->opt.refine = saved_refine; h->opt.timing = saved_timing;
         return HYLU_ERR_CUDA;
     }
+    const int64_t l0 = hylu::launches();
     int rc = do_factor(h, d_vals, st);
     if (rc >= 0) rc = do_solve(h, d_b, d_x, nrhs, ld, st);
+    h->graph_launches = hylu::launches() - l0;
+    hylu::add_launches(-h->graph_launches);  // recorded, not issued: replays count them
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(st, &g);
     h->opt.refine = saved_refine;
@@ -683,17 +695,22 @@ int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, 
     return HYLU_OK;
 }
 
+int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
+                       void* stream) {
+    return guarded([&] { return graph_capture_impl(h, d_vals, d_b, d_x, nrhs, ld, stream); });
+}
+
 int hylu_graph_launch(hylu_handle* h, void* stream) {
     if (!h) return HYLU_ERR_ARG;
     if (!h->graph_exec) return HYLU_ERR_STATE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     h->last = st;
     // the captured launches count as the library's own launches
-    hylu::add_launches(7);
+    hylu::add_launches(h->graph_launches);
     return cudaGraphLaunch(h->graph_exec, st) == cudaSuccess ? HYLU_OK : HYLU_ERR_CUDA;
 }
 
-int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {
+static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {
     if (!h || !d_vals) return HYLU_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     TRY(do_factor(h, d_vals, st));   // uploads and allocates on first use
@@ -724,6 +741,10 @@ int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* st
     h->grid = sms * best;
     if (blocks_per_sm) *blocks_per_sm = best;
     return read_status(h, st);
+}
+
+int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {
+    return guarded([&] { return tune_impl(h, d_vals, blocks_per_sm, stream); });
 }
 
 int hylu_debug_trace(hylu_handle* h, unsigned long long* out) {
