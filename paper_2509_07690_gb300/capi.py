@@ -118,11 +118,29 @@ def default_options(**kw) -> Options:
     return o
 
 
-def hylu_analyze(n, rowptr, col, vals=None, user_perm=None, opt: Options | None = None) -> int:
+def _host_csr(n, rowptr, col, vals=None, what="hylu_analyze"):
+    """Host CSR arrays as the C ABI reads them (lengths n + 1, nnz, nnz)."""
+    n = int(n)
     rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
     col = np.ascontiguousarray(col, dtype=np.int32)
-    vals = None if vals is None else np.ascontiguousarray(vals, dtype=np.float64)
-    user_perm = None if user_perm is None else np.ascontiguousarray(user_perm, dtype=np.int32)
+    if n < 0 or rowptr.ndim != 1 or len(rowptr) != n + 1:
+        raise ValueError(f"{what}: rowptr must hold n + 1 = {n + 1} entries")
+    nnz = int(rowptr[-1])
+    if len(col) != nnz:
+        raise ValueError(f"{what}: col must hold rowptr[n] = {nnz} entries, got {len(col)}")
+    if vals is not None:
+        vals = np.ascontiguousarray(vals, dtype=np.float64)
+        if len(vals) != nnz:
+            raise ValueError(f"{what}: vals must hold rowptr[n] = {nnz} entries, got {len(vals)}")
+    return n, rowptr, col, vals
+
+
+def hylu_analyze(n, rowptr, col, vals=None, user_perm=None, opt: Options | None = None) -> int:
+    n, rowptr, col, vals = _host_csr(n, rowptr, col, vals)
+    if user_perm is not None:
+        user_perm = np.ascontiguousarray(user_perm, dtype=np.int32)
+        if len(user_perm) != n:
+            raise ValueError(f"hylu_analyze: user_perm must hold n = {n} entries")
     h = C.c_void_p()
     rc = load().hylu_analyze(int(n), int(rowptr[-1]), rowptr, col, _ptr(vals), _ptr(user_perm),
                              C.byref(opt) if opt is not None else None, C.byref(h))
@@ -223,13 +241,11 @@ def hylu_analyze_batch(systems, nsets: int, opt: Options | None = None) -> int:
     cis = (C.c_void_p * k)()
     vls = (C.c_void_p * k)()
     for q, (n, rp, ci, v) in enumerate(systems):
-        rp = np.ascontiguousarray(rp, np.int64)
-        ci = np.ascontiguousarray(ci, np.int32)
-        v = np.ascontiguousarray(v, np.float64)
+        _, rp, ci, v = _host_csr(n, rp, ci, v, f"hylu_analyze_batch system {q}")
         keep += [rp, ci, v]
         rps[q] = rp.ctypes.data
         cis[q] = ci.ctypes.data
-        vls[q] = v.ctypes.data
+        vls[q] = None if v is None else v.ctypes.data
     h = C.c_void_p()
     rc = load().hylu_analyze_batch(k, ns.ctypes.data_as(C.c_void_p), C.cast(rps, C.c_void_p),
                                    C.cast(cis, C.c_void_p), C.cast(vls, C.c_void_p), int(nsets),

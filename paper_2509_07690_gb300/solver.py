@@ -13,6 +13,18 @@ def _stream(stream) -> int:
     return int(s.cuda_stream)
 
 
+def _device_f64(t, what: str, numel: int | None = None, multiple_of: int | None = None):
+    """The kernels read and write exactly the sizes the handle implies, so
+    a tensor of another type, layout or size is refused here."""
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{what}: expected a contiguous float64 CUDA tensor")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{what}: expected {numel} values, got {t.numel()}")
+    if multiple_of is not None and (t.numel() == 0 or t.numel() % multiple_of):
+        raise ValueError(f"{what}: expected a positive multiple of {multiple_of} values, got {t.numel()}")
+
+
 class Solver:
     """One analysed sparsity pattern (hylu_analyze) and its device factors."""
 
@@ -28,7 +40,7 @@ class Solver:
     # ------------------------------------------------------------ numeric
     def factor(self, d_vals, stream=None):
         """d_vals: torch float64 CUDA tensor of the nnz values (CSR order)."""
-        assert d_vals.is_cuda and d_vals.dtype.itemsize == 8 and d_vals.is_contiguous()
+        _device_f64(d_vals, "d_vals", numel=int(self.rowptr[-1]))
         fn = capi.hylu_refactor if self._factored else capi.hylu_factor
         rc = fn(self.h, d_vals.data_ptr(), _stream(stream))
         self._factored = True
@@ -38,10 +50,11 @@ class Solver:
         """d_b: float64 CUDA tensor [n] or [nrhs, n] (each right-hand side
         contiguous).  Returns d_x of the same shape."""
         import torch
+        _device_f64(d_b, "d_b", multiple_of=self.n)
         b2 = d_b.reshape(-1, self.n)
-        assert b2.is_contiguous()
         if d_x is None:
             d_x = torch.empty_like(d_b)
+        _device_f64(d_x, "d_x", numel=d_b.numel())
         x2 = d_x.reshape(-1, self.n)
         fn = capi.hylu_solve_transpose if transpose else capi.hylu_solve
         self.last_rc = fn(self.h, b2.data_ptr(), x2.data_ptr(), b2.shape[0], self.n, _stream(stream))
@@ -107,10 +120,14 @@ class BatchSolver(Solver):
                                for v in range(self.nsets) for s in range(self.k)])
 
     def tune(self, d_vals, stream=None) -> int:
+        _device_f64(d_vals, "d_vals", numel=int(self.rowptr[-1]))
         self._factored = True
         return capi.hylu_tune(self.h, d_vals.data_ptr(), _stream(stream))
 
     def graph_capture(self, d_vals, d_b, d_x, stream=None):
+        _device_f64(d_vals, "d_vals", numel=int(self.rowptr[-1]))
+        _device_f64(d_b, "d_b", multiple_of=self.n)
+        _device_f64(d_x, "d_x", numel=d_b.numel())
         b2 = d_b.reshape(-1, self.n)
         capi.hylu_graph_capture(self.h, d_vals.data_ptr(), b2.data_ptr(), d_x.data_ptr(), b2.shape[0], self.n,
                                 _stream(stream))

@@ -233,6 +233,38 @@ def test_error_codes():
     capi.hylu_destroy(h)
 
 
+def test_binding_refuses_arrays_of_the_wrong_size_or_type():
+    """Host arrays whose lengths disagree with n and rowptr[n], and tensors of
+    another dtype, device or size, are refused before the library reads them
+    (the C ABI takes plain pointers and trusts the sizes)."""
+    torch = pytest.importorskip("torch")
+    A = synth.grid5(4)
+    with pytest.raises(ValueError):
+        capi.hylu_analyze(A.n, A.rowptr[:-1], A.col, A.val)
+    with pytest.raises(ValueError):
+        capi.hylu_analyze(A.n, A.rowptr, A.col[:-1], A.val)
+    with pytest.raises(ValueError):
+        capi.hylu_analyze(A.n, A.rowptr, A.col, A.val[:-1])
+    with pytest.raises(ValueError):
+        capi.hylu_analyze(A.n, A.rowptr, A.col, A.val, np.arange(A.n - 1, dtype=np.int32),
+                          capi.default_options(ordering=3))
+    with pytest.raises(ValueError):
+        capi.hylu_analyze_batch([(A.n, A.rowptr, A.col, A.val[:-2])], 1)
+    with pytest.raises(capi.HyluError) as e:          # no values, but static pivoting wants them
+        capi.hylu_analyze_batch([(A.n, A.rowptr, A.col, None)], 1)
+    assert e.value.code == -1
+    s = Solver(A.n, A.rowptr, A.col, A.val)
+    with pytest.raises(TypeError):                    # host tensor
+        s.factor(torch.from_numpy(A.val))
+    with pytest.raises(TypeError):                    # host tensor, wrong dtype
+        s.factor(torch.from_numpy(A.val).float())
+    with pytest.raises(TypeError):
+        s.solve(torch.zeros(A.n, dtype=torch.float64))
+    with pytest.raises(TypeError):
+        s.factor(A.val)
+    s.close()
+
+
 # ------------------------------------------------- heavy-row claim queue
 def test_heavy_rows_selection():
     """Circuit hub rows (dense rows ordered last, most sources finished early)
