@@ -206,7 +206,12 @@ int or_supernodes(or_ctx *c, int sn_max) {
     c->sn_start = (int32_t *)xmalloc(sizeof(int32_t) * (n + 1));
     c->sn_of = (int32_t *)xmalloc(sizeof(int32_t) * n);
     int ns = 0, cur_start = 0;
-    c->sn_start[ns++] = 0;
+    c->sn_start[0] = 0;
+    if (n == 0) {               /* no rows: the partition has no blocks */
+        c->nsn = 0;
+        return 0;
+    }
+    ns = 1;
     for (int r = 0; r + 1 < n; ++r) {
         int64_t dr = diag_index(c->f_rp, c->f_ci, r), dn = diag_index(c->f_rp, c->f_ci, r + 1);
         int64_t lr = c->f_rp[r + 1] - dr, ln = c->f_rp[r + 2] - dn;

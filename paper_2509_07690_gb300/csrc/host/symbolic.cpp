@@ -181,7 +181,7 @@ void supernode_partition(int32_t n, const SymbolicRows& F, int32_t sn_max, std::
                                       sizeof(int32_t) * ln) == 0;
         if (!same || (r + 1 - cur) >= sn_max) { cur = r + 1; start.push_back(r + 1); }
     }
-    start.push_back(n);
+    if (n > 0) start.push_back(n);     // an empty matrix has no supernode
 }
 
 // Padded pattern (Sec. 2.2 storage, read as): each row keeps its own L
