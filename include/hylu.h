@@ -114,7 +114,11 @@ int hylu_default_options(hylu_options* opt);
  * and are copied; `vals` is only read for the matching (may be NULL when
  * opt->static_pivot == 0).  On success *out is a new handle (free it with
  * hylu_destroy).  Errors: HYLU_ERR_ARG, HYLU_ERR_PATTERN,
- * HYLU_ERR_STRUCT_SINGULAR, HYLU_ERR_NOMEM.  Runs on the host only. */
+ * HYLU_ERR_STRUCT_SINGULAR, HYLU_ERR_NOMEM.  Runs on the host only.
+ * n = 0 (an empty system) is accepted: hylu_factor, hylu_refactor,
+ * hylu_solve, hylu_solve_transpose, hylu_grad_values, hylu_tune and the
+ * exports then return HYLU_OK without touching the device, and their device
+ * pointers may be NULL. */
 int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col,
                  const double* vals, const int32_t* user_perm, const hylu_options* opt,
                  hylu_handle** out);
@@ -171,7 +175,9 @@ int hylu_grad_values(hylu_handle* h, const double* d_lam, const double* d_x, dou
  * concatenated in instance order, and hylu_solve right-hand sides of length
  * N = sum over instances of n[s] (instance q at rows hylu_batch_layout's
  * row_base[q]): every instance is factored in ONE persistent launch and
- * solved in one launch sequence.  The k systems are analysed on host threads. */
+ * solved in one launch sequence.  The k systems are analysed on host threads.
+ * Every system needs n >= 1: an empty system in a batch is refused with
+ * HYLU_ERR_ARG (a single empty system is accepted by hylu_analyze). */
 int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr, const int32_t* const* col,
                        const double* const* vals, int32_t nsets, const hylu_options* opt, hylu_handle** out);
 

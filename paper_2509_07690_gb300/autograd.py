@@ -9,7 +9,7 @@ from __future__ import annotations
 import torch
 
 from . import capi
-from .solver import Solver, _stream
+from .solver import Solver, _nrhs, _stream
 
 
 class HyluSolve(torch.autograd.Function):
@@ -31,7 +31,7 @@ class HyluSolve(torch.autograd.Function):
         lam = s.solve(g, transpose=True)
         dvals = None
         if ctx.needs_input_grad[0]:
-            nrhs = lam.reshape(-1, s.n).shape[0]
+            nrhs = _nrhs(lam, s.n)
             dvals = torch.empty(int(s.rowptr[-1]), dtype=torch.float64, device=lam.device)
             capi.hylu_grad_values(s.h, lam.data_ptr(), x.data_ptr(), dvals.data_ptr(), nrhs, s.n,
                                   _stream(None))

@@ -275,6 +275,10 @@ int read_status(hylu_handle* h, cudaStream_t st) {
 }
 
 int do_factor(hylu_handle* h, const double* d_vals, cudaStream_t st) {
+    if (h->P.n == 0) {                 // empty system: nothing to factor, no device work
+        h->factored = true;
+        return HYLU_OK;
+    }
     if (!d_vals) return HYLU_ERR_ARG;
     TRY(ensure_uploaded(h, st));
     if (cudaMemcpyAsync(h->d_avals, d_vals, sizeof(double) * h->P.nnz_a, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
@@ -304,6 +308,7 @@ double max_be(const hylu_handle* h, int nrhs) {
 
 int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, cudaStream_t st) {
     if (!h->factored) return HYLU_ERR_STATE;
+    if (h->P.n == 0) return nrhs < 1 || ld < 0 ? HYLU_ERR_ARG : HYLU_OK;
     if (!d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
     TRY(ensure_rhs(h, nrhs, ld));
     // the perturbation count decides whether to refine (Sec. 2.3); this also
@@ -342,6 +347,7 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
 // Transpose solve A^T x = b with the same refinement rule as do_solve.
 int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, cudaStream_t st) {
     if (!h->factored) return HYLU_ERR_STATE;
+    if (h->P.n == 0) return nrhs < 1 || ld < 0 ? HYLU_ERR_ARG : HYLU_OK;
     if (!d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
     TRY(ensure_rhs(h, nrhs, ld));
     TRY(read_status(h, st));
@@ -462,7 +468,9 @@ int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrh
 
 int hylu_grad_values(hylu_handle* h, const double* d_lam, const double* d_x, double* d_dvals, int nrhs, int ld,
                      void* stream) {
-    if (!h || !d_lam || !d_x || !d_dvals || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
+    if (!h || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
+    if (h->P.n == 0) return h->factored ? HYLU_OK : HYLU_ERR_STATE;
+    if (!d_lam || !d_x || !d_dvals) return HYLU_ERR_ARG;
     if (!h->uploaded) return HYLU_ERR_STATE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     h->last = st;
@@ -502,7 +510,7 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->flops_padded = P.flops_padded;
     info->analyze_ms = P.analyze_ms;
     int rc = HYLU_OK;
-    if (h->factored) rc = read_status(h, h->last);
+    if (h->factored && h->uploaded) rc = read_status(h, h->last);
     info->nperturb = h->nperturb;
     info->refine_iters = h->refine_iters;
     info->backward_error = h->backward_error;
@@ -556,6 +564,7 @@ static int export_factors_impl(hylu_handle* h, double* vals, int32_t* piv) {
     if (!h) return HYLU_ERR_ARG;
     if (!h->factored) return HYLU_ERR_STATE;
     const hylu::Plan& P = h->P;
+    if (P.n == 0) return HYLU_OK;
     if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
     std::vector<double> lv(P.nnz_l), pv(P.nnz_panel);
     std::vector<int32_t> pv_piv(P.n);
@@ -609,6 +618,8 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
                        const double* const* vals, int32_t nsets, const hylu_options* opt, hylu_handle** out) {
     if (!out || k < 1 || nsets < 1 || !n || !rowptr || !col) return HYLU_ERR_ARG;
     *out = nullptr;
+    for (int32_t s = 0; s < k; ++s)
+        if (n[s] < 1) return HYLU_ERR_ARG;   // every instance holds at least one row
     hylu_options o;
     if (opt) o = *opt; else hylu_default_options(&o);
     if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
@@ -714,6 +725,10 @@ static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, v
     if (!h || !d_vals) return HYLU_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     TRY(do_factor(h, d_vals, st));   // uploads and allocates on first use
+    if (h->P.n == 0) {               // empty system: no launch to tune
+        if (blocks_per_sm) *blocks_per_sm = 1;
+        return HYLU_OK;
+    }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
     const int maxper = std::max(1, h->grid_max / std::max(1, sms));

@@ -21,8 +21,17 @@ def _device_f64(t, what: str, numel: int | None = None, multiple_of: int | None 
         raise TypeError(f"{what}: expected a contiguous float64 CUDA tensor")
     if numel is not None and t.numel() != numel:
         raise ValueError(f"{what}: expected {numel} values, got {t.numel()}")
-    if multiple_of is not None and (t.numel() == 0 or t.numel() % multiple_of):
+    if multiple_of == 0 and t.numel() != 0:
+        raise ValueError(f"{what}: an empty system takes empty tensors, got {t.numel()} values")
+    if multiple_of and (t.numel() == 0 or t.numel() % multiple_of):
         raise ValueError(f"{what}: expected a positive multiple of {multiple_of} values, got {t.numel()}")
+
+
+def _nrhs(t, n: int) -> int:
+    """Right-hand sides in a [n] or [nrhs, n] tensor (n = 0: from its shape)."""
+    if n:
+        return t.numel() // n
+    return t.shape[0] if t.dim() == 2 else 1
 
 
 class Solver:
@@ -51,13 +60,11 @@ class Solver:
         contiguous).  Returns d_x of the same shape."""
         import torch
         _device_f64(d_b, "d_b", multiple_of=self.n)
-        b2 = d_b.reshape(-1, self.n)
         if d_x is None:
             d_x = torch.empty_like(d_b)
         _device_f64(d_x, "d_x", numel=d_b.numel())
-        x2 = d_x.reshape(-1, self.n)
         fn = capi.hylu_solve_transpose if transpose else capi.hylu_solve
-        self.last_rc = fn(self.h, b2.data_ptr(), x2.data_ptr(), b2.shape[0], self.n, _stream(stream))
+        self.last_rc = fn(self.h, d_b.data_ptr(), d_x.data_ptr(), _nrhs(d_b, self.n), self.n, _stream(stream))
         return d_x
 
     def get_info(self) -> capi.Info:
@@ -128,9 +135,8 @@ class BatchSolver(Solver):
         _device_f64(d_vals, "d_vals", numel=int(self.rowptr[-1]))
         _device_f64(d_b, "d_b", multiple_of=self.n)
         _device_f64(d_x, "d_x", numel=d_b.numel())
-        b2 = d_b.reshape(-1, self.n)
-        capi.hylu_graph_capture(self.h, d_vals.data_ptr(), b2.data_ptr(), d_x.data_ptr(), b2.shape[0], self.n,
-                                _stream(stream))
+        capi.hylu_graph_capture(self.h, d_vals.data_ptr(), d_b.data_ptr(), d_x.data_ptr(), _nrhs(d_b, self.n),
+                                self.n, _stream(stream))
 
     def graph_launch(self, stream=None):
         capi.hylu_graph_launch(self.h, _stream(stream))

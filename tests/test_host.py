@@ -142,6 +142,26 @@ def test_pattern_partition_flops_bit_exact(name, make, opts):
     s.close()
 
 
+@pytest.mark.parametrize("n", [0, 1, 2, 3])
+def test_pattern_parity_degenerate_sizes(n):
+    """The smallest systems: the empty matrix has no supernode (partition
+    [0]) and no flops; n = 1 is one standalone row.  Pattern, partition and
+    flop count equal the oracle's bit for bit."""
+    a = 3.0 * np.eye(n) + np.triu(np.ones((n, n)), 1) - 0.5 * np.tril(np.ones((n, n)), -2)
+    A = _dense_csr(a)
+    s = Solver(A.n, A.rowptr, A.col, A.val)
+    rp, cp, dr, dc, sn = s.export_perm()
+    o = oracle.Oracle(A.n, A.rowptr, A.col, A.val, rp, cp, dr, dc, numeric=False)
+    prp, pci = s.export_pattern()
+    assert np.array_equal(o.sn_start, sn) and sn[0] == 0 and sn[-1] == n
+    if n == 0:
+        assert list(sn) == [0]
+    assert np.array_equal(o.padded.rowptr, prp) and np.array_equal(o.padded.col, pci)
+    assert s.info.flops == o.flops[0] and s.info.flops_padded == o.flops[1]
+    assert s.info.nnodes == len(sn) - 1
+    s.close()
+
+
 @pytest.mark.parametrize("seed", range(30))
 def test_pattern_parity_random_unsymmetric(seed):
     rng = np.random.default_rng(900 + seed)
@@ -262,6 +282,80 @@ def test_binding_refuses_arrays_of_the_wrong_size_or_type():
         s.solve(torch.zeros(A.n, dtype=torch.float64))
     with pytest.raises(TypeError):
         s.factor(A.val)
+    s.close()
+
+
+# ------------------------------------------------------ empty system
+def test_empty_system_returns_ok_without_device_work():
+    """n = 0 is a valid, degenerate system: analysis gives an empty plan, and
+    factorization, refactorization, both solves, the gradient scatter, the
+    grid tuner and the exports return HYLU_OK with NULL device pointers and
+    launch no kernel (none of these calls reaches the CUDA runtime, so this
+    runs without a GPU).  A solve before the factorization is still refused."""
+    rp = np.zeros(1, np.int64)
+    ci = np.zeros(0, np.int32)
+    h = capi.hylu_analyze(0, rp, ci, np.zeros(0))
+    info = capi.hylu_get_info(h)
+    assert (info.n, info.nnz_a, info.nnz_lu, info.nnz_store, info.nnodes) == (0, 0, 0, 0, 0)
+    assert info.flops == 0.0 and info.flops_padded == 0.0
+    with pytest.raises(capi.HyluError) as e:
+        capi.hylu_solve(h, 0, 0, 1, 0, 0)
+    assert e.value.code == -7
+    l0 = capi.hylu_launch_count()
+    assert capi.hylu_factor(h, 0, 0) == 0
+    assert capi.hylu_refactor(h, 0, 0) == 0
+    assert capi.hylu_solve(h, 0, 0, 1, 0, 0) == 0
+    assert capi.hylu_solve(h, 0, 0, 3, 0, 0) == 0
+    assert capi.hylu_solve_transpose(h, 0, 0, 2, 0, 0) == 0
+    assert capi.hylu_grad_values(h, 0, 0, 0, 1, 0, 0) == 0
+    assert capi.hylu_tune(h, 1, 0) == 1
+    with pytest.raises(capi.HyluError) as e:          # nrhs must still be positive
+        capi.hylu_solve(h, 0, 0, 0, 0, 0)
+    assert e.value.code == -1
+    assert capi.hylu_launch_count() == l0
+    info = capi.hylu_get_info(h)
+    assert info.device_status == 0 and info.nperturb == 0
+    rowperm, colperm, dr, dc, sn = capi.hylu_export_perm(h, 0, info.nnodes)
+    assert len(rowperm) == 0 and list(sn) == [0]
+    prp, pci = capi.hylu_export_pattern(h, 0, 0)
+    assert list(prp) == [0] and len(pci) == 0
+    v, piv = capi.hylu_export_factors(h, 0, 0)
+    assert len(v) == 0 and len(piv) == 0
+    capi.hylu_destroy(h)
+    A = synth.grid5(3)                                # a batch refuses an empty system
+    with pytest.raises(capi.HyluError) as e:
+        capi.hylu_analyze_batch([(A.n, A.rowptr, A.col, A.val), (0, rp, ci, np.zeros(0))], 1)
+    assert e.value.code == -1
+
+
+def test_empty_system_through_the_binding():
+    """The handle wrapper passes empty tensors of an empty system through
+    (shapes [0] and [nrhs, 0]) instead of reshaping by a zero width.  The
+    tensors here are host tensors that report is_cuda, so the marshalling is
+    checked without a GPU; no call reaches the device for n = 0."""
+    torch = pytest.importorskip("torch")
+    from types import SimpleNamespace
+
+    class Tagged(torch.Tensor):
+        @property
+        def is_cuda(self):
+            return True
+
+    def dev(*shape):
+        return torch.Tensor._make_subclass(Tagged, torch.zeros(*shape, dtype=torch.float64))
+
+    st = SimpleNamespace(cuda_stream=0)
+    s = Solver(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    l0 = capi.hylu_launch_count()
+    assert s.factor(dev(0), stream=st) == 0
+    x = s.solve(dev(0), stream=st)
+    assert tuple(x.shape) == (0,)
+    x = s.solve(dev(4, 0), dev(4, 0), stream=st, transpose=True)
+    assert tuple(x.shape) == (4, 0)
+    with pytest.raises(ValueError):                   # an empty system takes empty tensors
+        s.solve(dev(3), stream=st)
+    assert capi.hylu_launch_count() == l0
+    assert s.get_info().device_status == 0
     s.close()
 
 
