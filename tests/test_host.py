@@ -162,6 +162,57 @@ def test_pattern_parity_degenerate_sizes(n):
     s.close()
 
 
+def _degenerate(kind):
+    rng = np.random.default_rng(77)
+    if kind == "diagonal":                 # every row standalone, no L, no U tail
+        n = 500
+        return synth.from_coo(n, np.arange(n), np.arange(n), rng.uniform(1, 2, n))
+    if kind == "permutation":              # the matching must undo a row permutation
+        n = 300
+        p = rng.permutation(n)
+        return synth.from_coo(n, p, np.arange(n), rng.uniform(1, 2, n) * rng.choice([-1, 1], n))
+    if kind == "upper_dense":              # dense upper triangle
+        n = 40
+        r, c = np.triu_indices(n)
+        return synth.from_coo(n, r, c, np.where(r == c, 5.0, rng.uniform(-1, 1, len(r))))
+    if kind == "lower_bidiagonal":         # one chain of standalone rows
+        n = 200
+        r = np.concatenate([np.arange(n), np.arange(1, n)])
+        c = np.concatenate([np.arange(n), np.arange(n - 1)])
+        return synth.from_coo(n, r, c, np.concatenate([np.full(n, 3.0), np.full(n - 1, -1.0)]))
+    if kind == "arrow_first":              # dense first row and column
+        n = 120
+        r = np.concatenate([np.arange(n), np.zeros(n - 1, int), np.arange(1, n)])
+        c = np.concatenate([np.arange(n), np.arange(1, n), np.zeros(n - 1, int)])
+        v = np.concatenate([np.full(n, 4.0), rng.uniform(-1, 1, 2 * (n - 1))])
+        return synth.from_coo(n, r, c, v)
+    raise KeyError(kind)
+
+
+@pytest.mark.parametrize("ordering", [0, 1, 2])
+@pytest.mark.parametrize("kind", ["diagonal", "permutation", "upper_dense", "lower_bidiagonal", "arrow_first"])
+def test_pattern_parity_degenerate_structures(kind, ordering):
+    """Structures at the edges of the method: a diagonal matrix, a row
+    permutation of one, a dense triangle, a single chain and a dense first
+    row and column, under AMD, nested dissection and the natural order.  The
+    matching gives a zero-free diagonal, and the pattern, partition and flop
+    count equal the oracle's bit for bit."""
+    A = _degenerate(kind)
+    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering)
+    rp, cp, dr, dc, sn = s.export_perm()
+    assert sorted(rp) == list(range(A.n)) and sorted(cp) == list(range(A.n))
+    a = A.todense()
+    assert np.all(a[rp, cp] != 0)                     # zero-free diagonal after static pivoting
+    o = oracle.Oracle(A.n, A.rowptr, A.col, A.val, rp, cp, dr, dc, numeric=False)
+    prp, pci = s.export_pattern()
+    assert np.array_equal(o.sn_start, sn)
+    assert np.array_equal(o.padded.rowptr, prp) and np.array_equal(o.padded.col, pci)
+    assert s.info.flops == o.flops[0] and s.info.flops_padded == o.flops[1]
+    if kind in ("diagonal", "permutation"):
+        assert s.info.flops == 0.0 and s.info.nnz_lu == A.n
+    s.close()
+
+
 @pytest.mark.parametrize("seed", range(30))
 def test_pattern_parity_random_unsymmetric(seed):
     rng = np.random.default_rng(900 + seed)
