@@ -263,6 +263,35 @@ int hylu_destroy(hylu_handle* h);
 #define HYLU_STATIC_SOLVE_MAX_N 262144
 int hylu_solve_static(hylu_handle* h, const double* d_b, double* d_x, void* stream);
 
+/* Checkpoint of an analysis (no counterpart in the paper, whose repeated-solve
+ * mode, Sec. 3.2, reuses the preprocessing only within one run).  The host
+ * analysis of hylu_analyze / hylu_analyze_batch (matching, scalings,
+ * ordering, symbolic pattern, supernodes, schedules) costs seconds on large
+ * patterns and depends on nothing but the pattern, the values given to it and
+ * the options; these two calls let a later process skip it.
+ *
+ * hylu_plan_save writes the handle's plan, batch layout and options into the
+ * caller-owned HOST buffer `buf` as one flat byte image (little-endian, with
+ * a version and an FNV-1a checksum).  With buf == NULL, *bytes receives the
+ * size needed; otherwise *bytes is the capacity on entry and the size written
+ * on return (HYLU_ERR_ARG, with *bytes set to the size needed, when the
+ * buffer is too small).  Host only; the handle need not be factored.
+ *
+ * hylu_plan_load makes a new handle from such an image (the caller keeps
+ * `buf`; the library copies what it needs).  opt == NULL keeps the saved
+ * options; otherwise the numeric options (pivot_tau, refinement, precision,
+ * spin_limit, timing, debug) come from *opt and the analysis options
+ * (ordering, static_pivot, scale, sn_max, nd_leaf, amd_dense, heavy_ratio)
+ * stay the saved ones.  The new handle behaves as the saved one did after
+ * its analysis: hylu_factor first, then the solves.  Errors: HYLU_ERR_ARG
+ * (NULL pointers, bytes <= 0, opt->precision not 0 or 1), HYLU_ERR_PATTERN
+ * (not an image of this version: wrong magic, version or byte order, bad
+ * checksum, truncated, or sizes and index ranges that do not fit together),
+ * HYLU_ERR_NOMEM.  The checks catch damaged images, not crafted ones: load
+ * only images this library wrote. */
+int hylu_plan_save(hylu_handle* h, void* buf, int64_t* bytes);
+int hylu_plan_load(const void* buf, int64_t bytes, const hylu_options* opt, hylu_handle** out);
+
 /* Diagnostics: when the handle was analysed with (opt.debug & 2), copy the
  * per-row trace of the last factorization to the HOST array out[4 * n]:
  * for row i, out[4i] = claim time, out[4i+1] = updates from earlier nodes

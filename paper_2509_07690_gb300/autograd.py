@@ -32,7 +32,7 @@ class HyluSolve(torch.autograd.Function):
         dvals = None
         if ctx.needs_input_grad[0]:
             nrhs = _nrhs(lam, s.n)
-            dvals = torch.empty(int(s.rowptr[-1]), dtype=torch.float64, device=lam.device)
+            dvals = torch.empty(s.nnz, dtype=torch.float64, device=lam.device)
             capi.hylu_grad_values(s.h, lam.data_ptr(), x.data_ptr(), dvals.data_ptr(), nrhs, s.n,
                                   _stream(None))
         db = lam if ctx.needs_input_grad[1] else None

@@ -94,6 +94,8 @@ def load():
     lib.hylu_graph_capture.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     lib.hylu_graph_launch.argtypes = [H, C.c_void_p]
     lib.hylu_tune.argtypes = [H, C.c_void_p, C.POINTER(C.c_int), C.c_void_p]
+    lib.hylu_plan_save.argtypes = [H, C.c_void_p, C.POINTER(C.c_int64)]
+    lib.hylu_plan_load.argtypes = [C.c_void_p, C.c_int64, C.POINTER(Options), C.POINTER(H)]
     _lib = lib
     return lib
 
@@ -268,6 +270,27 @@ def hylu_graph_capture(h: int, d_vals: int, d_b: int, d_x: int, nrhs: int, ld: i
 
 def hylu_graph_launch(h: int, stream: int = 0) -> int:
     return _check(load().hylu_graph_launch(h, stream), "hylu_graph_launch")
+
+
+def hylu_plan_save(h: int) -> bytes:
+    """The handle's analysis as a byte image (see include/hylu.h)."""
+    lib = load()
+    need = C.c_int64(0)
+    _check(lib.hylu_plan_save(h, None, C.byref(need)), "hylu_plan_save")
+    buf = C.create_string_buffer(max(need.value, 1))
+    size = C.c_int64(need.value)
+    _check(lib.hylu_plan_save(h, buf, C.byref(size)), "hylu_plan_save")
+    return buf.raw[:size.value]
+
+
+def hylu_plan_load(image: bytes, opt: Options | None = None) -> int:
+    """A new handle from a byte image written by hylu_plan_save."""
+    data = bytes(image)
+    buf = C.create_string_buffer(data, len(data))
+    h = C.c_void_p()
+    _check(load().hylu_plan_load(buf, len(data), C.byref(opt) if opt is not None else None, C.byref(h)),
+           "hylu_plan_load")
+    return h.value
 
 
 def hylu_tune(h: int, d_vals: int, stream: int = 0) -> int:

@@ -771,6 +771,52 @@ int hylu_debug_trace(hylu_handle* h, unsigned long long* out) {
     return HYLU_OK;
 }
 
+int hylu_plan_save(hylu_handle* h, void* buf, int64_t* bytes) {
+    if (!h || !bytes) return HYLU_ERR_ARG;
+    return guarded([&] {
+        std::vector<uint8_t> img;
+        TRY(hylu::save_plan(h->P, h->layout, h->batch, h->opt, img));
+        const int64_t need = (int64_t)img.size();
+        if (!buf) { *bytes = need; return HYLU_OK; }
+        if (*bytes < need) { *bytes = need; return HYLU_ERR_ARG; }
+        std::memcpy(buf, img.data(), img.size());
+        *bytes = need;
+        return HYLU_OK;
+    });
+}
+
+int hylu_plan_load(const void* buf, int64_t bytes, const hylu_options* opt, hylu_handle** out) {
+    if (!out || !buf || bytes <= 0) return HYLU_ERR_ARG;
+    *out = nullptr;
+    if (opt && opt->precision != 0 && opt->precision != 1) return HYLU_ERR_ARG;
+    hylu_handle* h = new (std::nothrow) hylu_handle();
+    if (!h) return HYLU_ERR_NOMEM;
+    hylu_options saved;
+    hylu_default_options(&saved);
+    bool batch = false;
+    const int rc = guarded([&] {
+        return hylu::load_plan(static_cast<const uint8_t*>(buf), (size_t)bytes, h->P, h->layout, batch, saved);
+    });
+    if (rc) { delete h; return rc; }
+    hylu_options o = saved;
+    if (opt) {
+        // numeric options from the caller; the analysis is the saved one
+        o = *opt;
+        if (o.precision == 1 && o.refine == 0) o.refine = 1;   // FP32 factors: always refine in FP64
+        o.ordering = saved.ordering;
+        o.static_pivot = saved.static_pivot;
+        o.scale = saved.scale;
+        o.sn_max = saved.sn_max;
+        o.nd_leaf = saved.nd_leaf;
+        o.amd_dense = saved.amd_dense;
+        o.heavy_ratio = saved.heavy_ratio;
+    }
+    h->opt = o;
+    h->batch = batch;
+    *out = h;
+    return HYLU_OK;
+}
+
 int hylu_measure_fp64_peak(double* gflops, void* stream) {
     if (!gflops) return HYLU_ERR_ARG;
     return hylu::measure_fp64_peak(gflops, static_cast<cudaStream_t>(stream));

@@ -6,6 +6,7 @@
 #include <vector>
 
 #include "preprocess.hpp"
+#include "../../../include/hylu.h"
 
 namespace hylu {
 
@@ -117,6 +118,15 @@ struct SymbolicRows {
     std::vector<int32_t> lrun_first, lrun_len;
     int64_t nnz_l = 0;                   // unpadded entries of L (strictly lower)
 };
+
+// Checkpoint of an analysis (serialize.cpp): the plan, the batch layout and
+// the options as one flat byte image with a checksum, and back.  load_plan
+// returns HYLU_ERR_PATTERN for an image that is not one (wrong magic,
+// version or byte order, bad checksum, truncated, or sizes and index ranges
+// that do not fit together).
+int save_plan(const Plan& P, const BatchLayout& B, bool batch, const hylu_options& opt,
+              std::vector<uint8_t>& out);
+int load_plan(const uint8_t* buf, size_t bytes, Plan& P, BatchLayout& B, bool& batch, hylu_options& opt);
 
 void symbolic_rows(const CsrPattern& ahat, SymbolicRows& F);
 void supernode_partition(int32_t n, const SymbolicRows& F, int32_t sn_max, std::vector<int32_t>& start);

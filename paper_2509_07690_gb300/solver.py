@@ -41,15 +41,48 @@ class Solver:
         self.n = int(n)
         self.rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
         self.col = np.ascontiguousarray(col, dtype=np.int32)
+        self.nnz = int(self.rowptr[-1])
         self.opt = capi.default_options(**opts)
         self.h = capi.hylu_analyze(self.n, self.rowptr, self.col, vals, user_perm, self.opt)
         self.info = capi.hylu_get_info(self.h)
         self._factored = False
 
+    # ------------------------------------------------------------ checkpoint
+    def save(self, path=None) -> bytes:
+        """The analysis as a byte image (hylu_plan_save), also written to
+        `path` when one is given."""
+        image = capi.hylu_plan_save(self.h)
+        if path is not None:
+            with open(path, "wb") as f:
+                f.write(image)
+        return image
+
+    @classmethod
+    def load(cls, source, **opts) -> "Solver":
+        """A solver from a saved analysis (hylu_plan_load): `source` is the
+        byte image or a path to it.  Keyword options set the numeric options
+        (as for the constructor); without any, the saved options are kept.
+        An image of a batch gives a solver over the combined system."""
+        if isinstance(source, (bytes, bytearray, memoryview)):
+            image = bytes(source)
+        else:
+            with open(source, "rb") as f:
+                image = f.read()
+        self = cls.__new__(cls)
+        self.opt = capi.default_options(**opts) if opts else None
+        self.h = capi.hylu_plan_load(image, self.opt)
+        self.info = capi.hylu_get_info(self.h)
+        self.n = int(self.info.n)
+        self.nnz = int(self.info.nnz_a)
+        self.rowptr = None
+        self.col = None
+        self._factored = False
+        return self
+
     # ------------------------------------------------------------ numeric
     def factor(self, d_vals, stream=None):
         """d_vals: torch float64 CUDA tensor of the nnz values (CSR order)."""
-        _device_f64(d_vals, "d_vals", numel=int(self.rowptr[-1]))
+        _device_f64(d_vals, "d_vals", numel=self.nnz)
         fn = capi.hylu_refactor if self._factored else capi.hylu_factor
         rc = fn(self.h, d_vals.data_ptr(), _stream(stream))
         self._factored = True
@@ -118,8 +151,13 @@ class BatchSolver(Solver):
                 rps.append(np.asarray(rp, np.int64)[1:] + off)
                 off += int(rp[-1])
         self.rowptr = np.concatenate([[0]] + rps).astype(np.int64)
+        self.nnz = int(self.rowptr[-1])
         self.col = None
         self._factored = False
+
+    @classmethod
+    def load(cls, source, **opts):
+        raise TypeError("BatchSolver.load: load a batch image with Solver.load (a solver over the combined system)")
 
     def concat_values(self, value_sets):
         """value_sets[v][s]: values of system s in value set v -> one array."""
@@ -127,12 +165,12 @@ class BatchSolver(Solver):
                                for v in range(self.nsets) for s in range(self.k)])
 
     def tune(self, d_vals, stream=None) -> int:
-        _device_f64(d_vals, "d_vals", numel=int(self.rowptr[-1]))
+        _device_f64(d_vals, "d_vals", numel=self.nnz)
         self._factored = True
         return capi.hylu_tune(self.h, d_vals.data_ptr(), _stream(stream))
 
     def graph_capture(self, d_vals, d_b, d_x, stream=None):
-        _device_f64(d_vals, "d_vals", numel=int(self.rowptr[-1]))
+        _device_f64(d_vals, "d_vals", numel=self.nnz)
         _device_f64(d_b, "d_b", multiple_of=self.n)
         _device_f64(d_x, "d_x", numel=d_b.numel())
         capi.hylu_graph_capture(self.h, d_vals.data_ptr(), d_b.data_ptr(), d_x.data_ptr(), _nrhs(d_b, self.n),

@@ -410,6 +410,128 @@ def test_empty_system_through_the_binding():
     s.close()
 
 
+# ------------------------------------------------ checkpoint of an analysis
+INFO_FIELDS = ["n", "nnz_a", "nnz_lu", "nnz_store", "nnodes", "nsupernodes", "rows_in_supernodes",
+               "max_supernode", "ntasks", "flops", "flops_padded", "nheavy", "factor_levels",
+               "fwd_levels", "bwd_levels", "analyze_ms"]
+
+
+def _plan_views(h):
+    """Everything the C ABI shows of a plan: sizes, preprocessing, pattern, schedule."""
+    info = capi.hylu_get_info(h)
+    views = [getattr(info, f) for f in INFO_FIELDS]
+    views += list(capi.hylu_export_perm(h, info.n, info.nnodes))
+    views += list(capi.hylu_export_pattern(h, info.n, info.nnz_store))
+    views += list(capi.hylu_export_schedule(h, info.n, info.ntasks, info.nheavy))
+    return views
+
+
+def _same_views(a, b):
+    assert len(a) == len(b)
+    for x, y in zip(a, b):
+        assert np.array_equal(np.asarray(x), np.asarray(y))
+
+
+def _fnv1a(data: bytes) -> int:
+    h = 1469598103934665603
+    for byte in data:
+        h = ((h ^ byte) * 1099511628211) & 0xFFFFFFFFFFFFFFFF
+    return h
+
+
+CHECKPOINT_CASES = [
+    ("grid5_16", lambda: synth.grid5(16), {}),
+    ("circuit_3000_heavy", lambda: synth.circuit(3000, seed=12), {"heavy_ratio": 1.0}),
+    ("convdiff_8_nd_sn7", lambda: synth.convdiff3d(8), {"ordering": 1, "sn_max": 7}),
+    ("aniso_24_nd", lambda: synth.aniso9(24), {"ordering": 1}),
+    ("grid5_12_fp32", lambda: synth.grid5(12), {"precision": 1}),
+    ("empty", lambda: synth.from_coo(0, [], [], []), {}),
+]
+
+
+@pytest.mark.parametrize("name,make,opts", CHECKPOINT_CASES, ids=[c[0] for c in CHECKPOINT_CASES])
+def test_plan_checkpoint_round_trip(name, make, opts, tmp_path):
+    """A saved analysis loads into a handle whose sizes, permutations,
+    scalings, supernodes, padded pattern and schedules equal the original's,
+    and saving the loaded handle gives the same bytes.  Numeric options given
+    at load time change the options, not the plan."""
+    A = make()
+    s = Solver(A.n, A.rowptr, A.col, A.val, **opts)
+    path = tmp_path / "plan.bin"
+    image = s.save(path)
+    assert path.read_bytes() == image
+    t = Solver.load(path)
+    assert (t.n, t.nnz) == (A.n, A.nnz)
+    _same_views(_plan_views(s.h), _plan_views(t.h))
+    assert t.save() == image
+    u = Solver.load(image, precision=1, pivot_tau=1e-10, spin_limit=1 << 20)
+    _same_views(_plan_views(s.h), _plan_views(u.h))
+    for x in (s, t, u):
+        x.close()
+
+
+def test_plan_checkpoint_batch():
+    """A batch handle's image keeps the block-diagonal plan and its layout."""
+    from paper_2509_07690_gb300.solver import BatchSolver
+    mats = [synth.circuit(300, seed=5), synth.grid5(6), synth.circuit(800, seed=6)]
+    bs = BatchSolver([(m.n, m.rowptr, m.col, m.val) for m in mats], 2)
+    image = bs.save()
+    t = Solver.load(image)
+    assert t.n == bs.n and t.nnz == bs.nnz
+    _same_views(_plan_views(bs.h), _plan_views(t.h))
+    lay_a = capi.hylu_batch_layout(bs.h, 6)
+    lay_b = capi.hylu_batch_layout(t.h, 6)
+    _same_views(lay_a, lay_b)
+    assert t.save() == image
+    with pytest.raises(TypeError):
+        BatchSolver.load(image)
+    bs.close()
+    t.close()
+
+
+def test_plan_checkpoint_rejects_damaged_images():
+    """Truncated, altered and foreign images are refused with
+    HYLU_ERR_PATTERN: the checksum catches altered bytes, and an image whose
+    checksum was recomputed over inconsistent sizes fails the size checks.
+    The options block is 84 bytes after the 16-byte header, so n sits at
+    byte 100."""
+    A = synth.grid5(8)
+    s = Solver(A.n, A.rowptr, A.col, A.val)
+    image = s.save()
+
+    def code(img):
+        with pytest.raises(capi.HyluError) as e:
+            capi.hylu_plan_load(img)
+        return e.value.code
+
+    def resealed(body: bytes) -> bytes:
+        return body + _fnv1a(body).to_bytes(8, "little")
+
+    flipped = bytearray(image)
+    flipped[len(image) // 2] ^= 0x40
+    assert code(bytes(flipped)) == -2                  # altered byte
+    assert code(image[:-1]) == -2                      # truncated
+    assert code(image[:40]) == -2
+    assert code(b"XYLUPLAN" + image[8:]) == -2          # foreign magic
+    body = bytearray(image[:-8])
+    body[8] = 2                                        # version 2
+    assert code(resealed(bytes(body))) == -2
+    body = bytearray(image[:-8])
+    assert int.from_bytes(body[100:104], "little") == A.n
+    body[100:104] = (A.n + 1).to_bytes(4, "little")    # n no longer fits the arrays
+    assert code(resealed(bytes(body))) == -2
+    h = capi.hylu_plan_load(resealed(image[:-8]))     # resealing alone changes nothing
+    assert h
+    capi.hylu_destroy(h)
+    with pytest.raises(capi.HyluError) as e:
+        capi.hylu_plan_load(image, capi.default_options(precision=2))
+    assert e.value.code == -1
+    with pytest.raises(capi.HyluError) as e:
+        capi.hylu_plan_load(b"")
+    assert e.value.code == -1
+    s.close()
+
+
 # ------------------------------------------------- heavy-row claim queue
 def test_heavy_rows_selection():
     """Circuit hub rows (dense rows ordered last, most sources finished early)
