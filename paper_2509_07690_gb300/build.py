@@ -62,7 +62,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if verbose and (r.stdout or r.stderr):
                 sys.stderr.write(r.stdout + r.stderr)
     tmp = SO + f".tmp{os.getpid()}"
-    _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+    # -ldl: the NVTX ranges look up a profiler's injection library with dlopen
+    # (part of libc from glibc 2.34 on, of libdl before)
+    _run([NVCC, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-ldl"])
     os.replace(tmp, SO)
     return SO
 

@@ -8,6 +8,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hylu.h"
 #include "host/plan.hpp"
 #include "kernels.cuh"
@@ -69,6 +71,15 @@ int upload(hylu_handle* h, T** p, const std::vector<T>& v, cudaStream_t st) {
 }
 
 #define TRY(x) do { int rc_ = (x); if (rc_ < 0) return rc_; } while (0)
+
+// NVTX range around an entry point or a refinement step, for timeline tools
+// (nsys, ncu --nvtx); without an attached tool the calls do nothing.
+struct Range {
+    explicit Range(const char* name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range&) = delete;
+    Range& operator=(const Range&) = delete;
+};
 
 // No C++ exception crosses the C ABI: host allocation failures become
 // HYLU_ERR_NOMEM, anything else HYLU_ERR_INTERNAL.
@@ -337,6 +348,7 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
         if (be <= h->opt.refine_tol) return HYLU_OK;
         if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
         be_prev = be;
+        Range step("hylu_refine_step");
         TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
                                h->d_dc, nrhs, ld, h->opt.spin_limit, h->grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
@@ -370,6 +382,7 @@ int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs,
         if (be <= h->opt.refine_tol) return HYLU_OK;
         if (h->refine_iters >= h->opt.refine_maxit || !(be <= 0.5 * be_prev)) return HYLU_WARN_REFINE_STALLED;
         be_prev = be;
+        Range step("hylu_refine_step");
         TRY(hylu::launch_solve_transpose(P, h->d_r, h->d_d, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
                                          nrhs, ld, h->opt.spin_limit, h->grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
@@ -419,6 +432,7 @@ int hylu_default_options(hylu_options* o) {
 
 int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* col, const double* vals,
                  const int32_t* user_perm, const hylu_options* opt, hylu_handle** out) {
+    Range range_("hylu_analyze");
     if (!out || n < 0 || !rowptr || (nnz > 0 && !col)) return HYLU_ERR_ARG;
     *out = nullptr;
     if (rowptr[n] != nnz) return HYLU_ERR_PATTERN;
@@ -446,28 +460,33 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
 }
 
 int hylu_factor(hylu_handle* h, const double* d_vals, void* stream) {
+    Range range_("hylu_factor");
     if (!h) return HYLU_ERR_ARG;
     return guarded([&] { return do_factor(h, d_vals, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_refactor(hylu_handle* h, const double* d_vals, void* stream) {
+    Range range_("hylu_refactor");
     if (!h) return HYLU_ERR_ARG;
     if (!h->factored) return HYLU_ERR_STATE;
     return guarded([&] { return do_factor(h, d_vals, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream) {
+    Range range_("hylu_solve");
     if (!h) return HYLU_ERR_ARG;
     return guarded([&] { return do_solve(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, void* stream) {
+    Range range_("hylu_solve_transpose");
     if (!h) return HYLU_ERR_ARG;
     return guarded([&] { return do_solve_transpose(h, d_b, d_x, nrhs, ld, static_cast<cudaStream_t>(stream)); });
 }
 
 int hylu_grad_values(hylu_handle* h, const double* d_lam, const double* d_x, double* d_dvals, int nrhs, int ld,
                      void* stream) {
+    Range range_("hylu_grad_values");
     if (!h || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
     if (h->P.n == 0) return h->factored ? HYLU_OK : HYLU_ERR_STATE;
     if (!d_lam || !d_x || !d_dvals) return HYLU_ERR_ARG;
@@ -616,6 +635,7 @@ int64_t hylu_launch_count(void) { return hylu::launches(); }
 
 int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr, const int32_t* const* col,
                        const double* const* vals, int32_t nsets, const hylu_options* opt, hylu_handle** out) {
+    Range range_("hylu_analyze_batch");
     if (!out || k < 1 || nsets < 1 || !n || !rowptr || !col) return HYLU_ERR_ARG;
     *out = nullptr;
     for (int32_t s = 0; s < k; ++s)
@@ -708,10 +728,12 @@ static int graph_capture_impl(hylu_handle* h, const double* d_vals, const double
 
 int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
                        void* stream) {
+    Range range_("hylu_graph_capture");
     return guarded([&] { return graph_capture_impl(h, d_vals, d_b, d_x, nrhs, ld, stream); });
 }
 
 int hylu_graph_launch(hylu_handle* h, void* stream) {
+    Range range_("hylu_graph_launch");
     if (!h) return HYLU_ERR_ARG;
     if (!h->graph_exec) return HYLU_ERR_STATE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -759,6 +781,7 @@ static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, v
 }
 
 int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {
+    Range range_("hylu_tune");
     return guarded([&] { return tune_impl(h, d_vals, blocks_per_sm, stream); });
 }
 
@@ -772,6 +795,7 @@ int hylu_debug_trace(hylu_handle* h, unsigned long long* out) {
 }
 
 int hylu_plan_save(hylu_handle* h, void* buf, int64_t* bytes) {
+    Range range_("hylu_plan_save");
     if (!h || !bytes) return HYLU_ERR_ARG;
     return guarded([&] {
         std::vector<uint8_t> img;
@@ -786,6 +810,7 @@ int hylu_plan_save(hylu_handle* h, void* buf, int64_t* bytes) {
 }
 
 int hylu_plan_load(const void* buf, int64_t bytes, const hylu_options* opt, hylu_handle** out) {
+    Range range_("hylu_plan_load");
     if (!out || !buf || bytes <= 0) return HYLU_ERR_ARG;
     *out = nullptr;
     if (opt && opt->precision != 0 && opt->precision != 1) return HYLU_ERR_ARG;
