@@ -140,6 +140,15 @@ def backward_error(A, vals, x, b) -> float:
     return float(np.abs(b - ax).max() / (anorm * np.abs(x).max() + np.abs(b).max()))
 
 
+def kernel_mix(info) -> dict:
+    """Shares of the padded flops by kernel of the paper's Fig. 1 (row-row,
+    sup-row, sup-sup) and the in-supernode factorization, from hylu_info."""
+    total = info.flops_padded if info.flops_padded > 0 else 1.0
+    parts = (("row_row", info.flops_row_row), ("sup_row", info.flops_sup_row),
+             ("sup_sup", info.flops_sup_sup), ("in_supernode", info.flops_in_supernode))
+    return {k: round(v / total, 4) for k, v in parts}
+
+
 def sample_instance(n_s: int):
     """A smaller instance of the same circuit-like generator (same seed rule)."""
     from paper_2509_07690_gb300 import synth
@@ -372,6 +381,7 @@ def run_batch(args, ws, rank, local):
             "config": {"workload": "circuit_batch_512" if k == 512 else f"circuit_batch_{k}", "systems": k, "value_sets": BATCH_SETS,
                        "instances": inst, "nrhs": BATCH_RHS, "rows": bs.n, "flops": bs_flops,
                        "nnz_store": info.nnz_store, "tuned_blocks_per_sm": best, "analyze_s": analyze_s,
+                       "flops_by_kernel": kernel_mix(info),
                        "l2": "factor storage far above the 126 MB L2, no flush",
                        "parallelism": f"replicas x{ws}"},
             "gflops": bs_flops / (t_batch * 1e-3) / 1e9,
@@ -527,6 +537,7 @@ def run_hylu(args, ws, rank, local):
                        "value_sets": VALUE_SETS, "flops": flops, "nnz_lu": info.nnz_lu,
                        "nnz_store": info.nnz_store, "supernodes": info.nsupernodes,
                        "rows_in_supernodes": info.rows_in_supernodes,
+                       "flops_by_kernel": kernel_mix(info),
                        "critical_path_levels": {"factor": info.factor_levels, "forward": info.fwd_levels,
                                                 "backward": info.bwd_levels},
                        "l2": f"factor storage {info.nnz_store * 8 / 1e9:.2f} GB > 126 MB L2, no flush",

@@ -100,6 +100,14 @@ typedef struct {
     int32_t factor_levels;   /* dependency levels of the factor kernel's tasks (critical-path length) */
     int32_t fwd_levels;      /* node levels of the forward / backward substitution (for a batch, */
     int32_t bwd_levels;      /*   the largest over its instances)                                 */
+    /* the padded flops by kernel (Sec. 2.1 counts them during the symbolic
+     * factorization; Sec. 2.2, Fig. 1 names the kernels); they add up to
+     * flops_padded */
+    double flops_row_row;      /* updates from standalone source rows                  */
+    double flops_sup_row;      /* updates from source supernodes into standalone rows  */
+    double flops_sup_sup;      /* updates from source supernodes into supernode rows   */
+    double flops_in_supernode; /* supernode rows against the earlier rows of their own
+                                  diagonal block (the in-supernode factorization)     */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */

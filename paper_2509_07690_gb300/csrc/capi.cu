@@ -527,6 +527,10 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->bwd_levels = levels(P.bwd_off, P.bwd_count);
     info->flops = P.flops_unpadded;
     info->flops_padded = P.flops_padded;
+    info->flops_row_row = P.flops_row_row;
+    info->flops_sup_row = P.flops_sup_row;
+    info->flops_sup_sup = P.flops_sup_sup;
+    info->flops_in_supernode = P.flops_in_sn;
     info->analyze_ms = P.analyze_ms;
     int rc = HYLU_OK;
     if (h->factored && h->uploaded) rc = read_status(h, h->last);

@@ -124,6 +124,10 @@ int combine(const std::vector<const Plan*>& sys, int32_t nsets, Plan& C, BatchLa
         C.nnz_f += P.nnz_f;
         C.flops_unpadded += P.flops_unpadded;
         C.flops_padded += P.flops_padded;
+        C.flops_row_row += P.flops_row_row;
+        C.flops_sup_row += P.flops_sup_row;
+        C.flops_sup_sup += P.flops_sup_sup;
+        C.flops_in_sn += P.flops_in_sn;
         C.max_sn = std::max(C.max_sn, P.max_sn);
         C.max_row = std::max(C.max_row, P.max_row);
         C.analyze_ms += P.analyze_ms;

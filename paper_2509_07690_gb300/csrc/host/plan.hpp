@@ -38,6 +38,11 @@ struct Plan {
     std::vector<int64_t> node_panel_off;// nnodes + 1 into the panel values
     int64_t nnz_l = 0, nnz_panel = 0, nnz_store = 0, nnz_f = 0;
     double flops_unpadded = 0.0, flops_padded = 0.0;
+    // the padded flops by kernel (Sec. 2.2, Fig. 1): updates from standalone
+    // source rows (row-row), from source supernodes into standalone rows
+    // (sup-row) and into supernode rows (sup-sup), and each supernode row's
+    // elimination against the earlier rows of its own diagonal block
+    double flops_row_row = 0.0, flops_sup_row = 0.0, flops_sup_sup = 0.0, flops_in_sn = 0.0;
     std::vector<double> row_flops;      // padded flops of each row
     // tail tasks of the in-supernode step (Sec. 2.2, the triangular solve of
     // a supernode's U tail by its unit lower diagonal block): a supernode with

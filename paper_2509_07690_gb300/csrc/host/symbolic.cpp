@@ -255,10 +255,24 @@ void build_nodes(Plan& P, const SymbolicRows& F) {
     for (size_t q = 0; q < F.lrun_first.size(); ++q)
         fu += upre[F.lrun_first[q] + F.lrun_len[q]] - upre[F.lrun_first[q]];
     P.row_flops.assign(n, 0.0);
+    P.flops_row_row = P.flops_sup_row = P.flops_sup_sup = P.flops_in_sn = 0.0;
     for (int32_t i = 0; i < n; ++i) {
+        const int32_t D = P.node_of[i];
+        const bool dest_sn = P.sn_start[D + 1] - P.sn_start[D] > 1;
         double f = 0.0;
-        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) f += 1.0 + 2.0 * (double)(ulen[P.lcols[t]] - 1);
-        for (int32_t k = P.sn_start[P.node_of[i]]; k < i; ++k) f += 1.0 + 2.0 * (double)(ulen[k] - 1);
+        for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t) {
+            const double g = 1.0 + 2.0 * (double)(ulen[P.lcols[t]] - 1);
+            const int32_t S = P.node_of[P.lcols[t]];
+            if (P.sn_start[S + 1] - P.sn_start[S] == 1) P.flops_row_row += g;
+            else if (dest_sn) P.flops_sup_sup += g;
+            else P.flops_sup_row += g;
+            f += g;
+        }
+        for (int32_t k = P.sn_start[D]; k < i; ++k) {
+            const double g = 1.0 + 2.0 * (double)(ulen[k] - 1);
+            P.flops_in_sn += g;
+            f += g;
+        }
         P.row_flops[i] = f;
         fp += f;
     }

@@ -1,6 +1,6 @@
 """bench.py's host-side helpers: the factor-code hash ignores comments and
-blank lines but not code, and the committed traffic profile is used only
-while that hash matches."""
+blank lines but not code, the committed traffic profile is used only while
+that hash matches, and the kernel mix reads hylu_info's flop split."""
 import os
 import sys
 
@@ -54,3 +54,16 @@ def test_measured_hbm_peak_read_or_fallback(tmp_path, monkeypatch):
     assert bench.measured_hbm_gbs() == 6800.0
     (tmp_path / "MEASURED_PEAKS.json").write_text('{"hbm_gbs": 6787.6}')
     assert bench.measured_hbm_gbs() == 6787.6
+
+
+def test_kernel_mix_shares_sum_to_one():
+    from paper_2509_07690_gb300 import Solver, synth
+    A = synth.convdiff3d(10)
+    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=1)
+    mix = bench.kernel_mix(s.info)
+    assert set(mix) == {"row_row", "sup_row", "sup_sup", "in_supernode"}
+    assert abs(sum(mix.values()) - 1.0) < 1e-3 and mix["sup_sup"] > 0.5
+    s.close()
+    e = Solver(0, [0], [], [])
+    assert sum(bench.kernel_mix(e.info).values()) == 0.0
+    e.close()

@@ -128,6 +128,35 @@ CASES = [
 ]
 
 
+def _kernel_split(o):
+    """The padded flops of the oracle's pattern by kernel: every L entry of
+    row i in column k costs 1 + 2 (|U(k,:)| - 1) (unpadded U row length);
+    a standalone source is row-row, a supernode source sup-row into a
+    standalone row and sup-sup into a supernode row; the columns of a row's
+    own supernode before it are the in-supernode factorization."""
+    sn = np.asarray(o.sn_start)
+    size = np.diff(sn)
+    node = np.repeat(np.arange(len(size)), size)
+    urp, uci = o.unpadded.rowptr, o.unpadded.col
+    n = len(node)
+    ulen = np.array([np.count_nonzero(uci[urp[k]:urp[k + 1]] >= k) for k in range(n)], dtype=np.int64)
+    g = 1 + 2 * (ulen - 1)
+    prp, pci = o.padded.rowptr, o.padded.col
+    rr = sr = ss = ins = 0
+    for i in range(n):
+        r = sn[node[i]]
+        cols = pci[prp[i]:prp[i + 1]]
+        lc = cols[cols < r]
+        from_sn = size[node[lc]] > 1
+        rr += int(g[lc[~from_sn]].sum())
+        if size[node[i]] > 1:
+            ss += int(g[lc[from_sn]].sum())
+        else:
+            sr += int(g[lc[from_sn]].sum())
+        ins += int(g[r:i].sum())
+    return rr, sr, ss, ins
+
+
 @pytest.mark.parametrize("name,make,opts", CASES, ids=[c[0] for c in CASES])
 def test_pattern_partition_flops_bit_exact(name, make, opts):
     A = make()
@@ -139,6 +168,9 @@ def test_pattern_partition_flops_bit_exact(name, make, opts):
     assert np.array_equal(o.padded.rowptr, prp) and np.array_equal(o.padded.col, pci)
     assert s.info.nnz_lu == len(o.unpadded.col)
     assert s.info.flops == o.flops[0] and s.info.flops_padded == o.flops[1]
+    split = _kernel_split(o)
+    assert sum(split) == o.flops[1]
+    assert (s.info.flops_row_row, s.info.flops_sup_row, s.info.flops_sup_sup, s.info.flops_in_supernode) == split
     s.close()
 
 
@@ -413,7 +445,8 @@ def test_empty_system_through_the_binding():
 # ------------------------------------------------ checkpoint of an analysis
 INFO_FIELDS = ["n", "nnz_a", "nnz_lu", "nnz_store", "nnodes", "nsupernodes", "rows_in_supernodes",
                "max_supernode", "ntasks", "flops", "flops_padded", "nheavy", "factor_levels",
-               "fwd_levels", "bwd_levels", "analyze_ms"]
+               "fwd_levels", "bwd_levels", "analyze_ms", "flops_row_row", "flops_sup_row", "flops_sup_sup",
+               "flops_in_supernode"]
 
 
 def _plan_views(h):
