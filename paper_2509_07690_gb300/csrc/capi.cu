@@ -8,7 +8,12 @@
 #include <thread>
 #include <vector>
 
+#if defined(__has_include)
+#if __has_include(<nvtx3/nvToolsExt.h>)
 #include <nvtx3/nvToolsExt.h>
+#define HYLU_HAVE_NVTX 1
+#endif
+#endif
 
 #include "../../include/hylu.h"
 #include "host/plan.hpp"
@@ -73,10 +78,15 @@ int upload(hylu_handle* h, T** p, const std::vector<T>& v, cudaStream_t st) {
 #define TRY(x) do { int rc_ = (x); if (rc_ < 0) return rc_; } while (0)
 
 // NVTX range around an entry point or a refinement step, for timeline tools
-// (nsys, ncu --nvtx); without an attached tool the calls do nothing.
+// (nsys, ncu --nvtx); without an attached tool the calls do nothing, and a
+// toolkit without the NVTX headers builds the ranges as no-ops.
 struct Range {
+#ifdef HYLU_HAVE_NVTX
     explicit Range(const char* name) { nvtxRangePushA(name); }
     ~Range() { nvtxRangePop(); }
+#else
+    explicit Range(const char*) {}
+#endif
     Range(const Range&) = delete;
     Range& operator=(const Range&) = delete;
 };
