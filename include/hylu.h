@@ -11,6 +11,14 @@
  * CUDA kernels, and a call made without a usable CUDA device returns
  * HYLU_ERR_CUDA.
  *
+ * Threads and streams: handles are independent (except for the one scratch
+ * array that every hylu_solve_static call shares), so different host threads
+ * may drive different handles at the same time.  Calls on ONE handle must
+ * not overlap on the host, and because a handle's factor storage, solve
+ * workspace and device counters are shared by its calls, the caller orders
+ * its device work too: calls on one handle made on different streams race
+ * unless those streams are synchronized with each other.
+ *
  * Data conventions (used by every call below):
  *   - A is n x n CSR: rowptr int64[n+1] (rowptr[0] = 0), col int32[nnz]
  *     strictly increasing within each row, values float64[nnz].

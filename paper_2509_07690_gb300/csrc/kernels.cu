@@ -28,6 +28,7 @@
 // diagonal block is stored by column LABEL (pre-pivot column), so that later
 // exchanges never move data; consumers read position p through piv[p].
 #include <algorithm>
+#include <atomic>
 #include <climits>
 #include <cstdio>
 
@@ -40,7 +41,7 @@ namespace {
 constexpr int WARPS = 8;          // warps per block of the persistent kernels
 constexpr int SN_SMEM = 256;      // largest supernode held in shared memory
 constexpr unsigned FULL = 0xffffffffu;
-int64_t g_launches = 0;
+std::atomic<int64_t> g_launches{0};   // kernels issued (host threads may drive separate handles)
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
     int v;
@@ -1420,7 +1421,7 @@ __global__ void axpy_kernel(int32_t n, double* __restrict__ x, const double* __r
 
 }  // namespace
 
-int64_t launches() { return g_launches; }
+int64_t launches() { return g_launches.load(); }
 void count_launch() { ++g_launches; }
 void add_launches(int64_t k) { g_launches += k; }
 
