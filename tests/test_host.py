@@ -503,6 +503,37 @@ def test_plan_checkpoint_round_trip(name, make, opts, tmp_path):
         x.close()
 
 
+def test_analysis_on_concurrent_host_threads():
+    """Separate handles on separate host threads (ctypes releases the GIL
+    during the C calls, so the analyses overlap): every plan equals the one
+    the same input gives when analysed alone."""
+    import threading
+    mats = [(synth.circuit(2500, seed=40 + q), {}) for q in range(3)] + \
+           [(synth.convdiff3d(9), {"ordering": 1}), (synth.aniso9(20), {"ordering": 1})]
+
+    def views(A, opts):
+        s = Solver(A.n, A.rowptr, A.col, A.val, **opts)
+        v = _plan_views(s.h)
+        s.close()
+        del v[INFO_FIELDS.index("analyze_ms")]          # wall time, not part of the plan
+        return v
+
+    alone = [views(A, o) for A, o in mats]
+    got = [None] * len(mats)
+
+    def work(q):
+        for _ in range(3):
+            got[q] = views(*mats[q])
+
+    th = [threading.Thread(target=work, args=(q,)) for q in range(len(mats))]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for q in range(len(mats)):
+        _same_views(alone[q], got[q])
+
+
 def test_plan_checkpoint_batch():
     """A batch handle's image keeps the block-diagonal plan and its layout."""
     from paper_2509_07690_gb300.solver import BatchSolver
