@@ -140,6 +140,15 @@ def backward_error(A, vals, x, b) -> float:
     return float(np.abs(b - ax).max() / (anorm * np.abs(x).max() + np.abs(b).max()))
 
 
+def residual_1(A, vals, x, b) -> float:
+    """The paper's accuracy metric (Sec. 3.3): ||A x - b||_1 / ||b||_1 (host check)."""
+    rid = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    ax = np.bincount(rid, weights=vals * x[A.col], minlength=A.n)
+    r1 = float(np.abs(ax - b).sum())
+    nb = float(np.abs(b).sum())
+    return r1 / nb if nb > 0 else r1
+
+
 def kernel_mix(info) -> dict:
     """Shares of the padded flops by kernel of the paper's Fig. 1 (row-row,
     sup-row, sup-sup) and the in-supernode factorization, from hylu_info."""
@@ -342,13 +351,14 @@ def run_batch(args, ws, rank, local):
     t_batch = allmax(ws, e0.elapsed_time(e1)) / args.steps
     x = dx.cpu().numpy()
     nperturb = bs.get_info().nperturb
-    be = 0.0
+    be = res1 = 0.0
     for q in range(0, inst, 64):              # every 64th instance, every RHS
         v, sidx = divmod(q, k)
         m = mats[sidx]
         rb = bs.row_base[q]
         for r in range(BATCH_RHS):
             be = max(be, backward_error(m, sets[v][sidx], x[r, rb:rb + m.n], b[r, rb:rb + m.n]))
+            res1 = max(res1, residual_1(m, sets[v][sidx], x[r, rb:rb + m.n], b[r, rb:rb + m.n]))
     # per-system plain launches on a sample, extrapolated to every instance
     plain_ms = []
     for sidx in range(0, k, BATCH_SAMPLE_EVERY):
@@ -385,7 +395,7 @@ def run_batch(args, ws, rank, local):
                        "l2": "factor storage far above the 126 MB L2, no flush",
                        "parallelism": f"replicas x{ws}"},
             "gflops": bs_flops / (t_batch * 1e-3) / 1e9,
-            "backward_error": be, "nperturb": nperturb,
+            "backward_error": be, "residual_1": res1, "nperturb": nperturb,
             "plain_launches": {"factorizations_per_s": inst / (t_plain * 1e-3), "ms_per_instance":
                                statistics.mean(plain_ms), "sample": f"every {BATCH_SAMPLE_EVERY}th system "
                                f"({len(plain_ms)} systems, value set 1), refactor + 8-RHS solve, extrapolated "
@@ -517,6 +527,8 @@ def run_hylu(args, ws, rank, local):
     barrier(ws)
     e2e_ms = allmax(ws, e0.elapsed_time(e1)) / (ws * args.steps)
     be_e2e = backward_error(A, sets[(args.steps - 1) % VALUE_SETS].val, h_x.numpy(), b)
+    res1 = max(residual_1(A, sets[(args.steps - 1) % VALUE_SETS].val, x, b),
+               residual_1(A, sets[(args.steps - 1) % VALUE_SETS].val, h_x.numpy(), b))
     # ---------------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline and WORKLOAD == "circuit_100k":
@@ -544,6 +556,7 @@ def run_hylu(args, ws, rank, local):
                        "parallelism": f"replicas x{ws}"},
             "gflops": flops / (value * 1e-3) / 1e9,
             "backward_error": max(be, be_e2e),
+            "residual_1": res1,
             "solve_ms": statistics.mean(solve_ms),
             "nperturb": inf.nperturb,
             "refine_iters": inf.refine_iters,

@@ -1,6 +1,7 @@
 """bench.py's host-side helpers: the factor-code hash ignores comments and
 blank lines but not code, the committed traffic profile is used only while
-that hash matches, and the kernel mix reads hylu_info's flop split."""
+that hash matches, the kernel mix reads hylu_info's flop split, and the
+host accuracy metrics agree with dense arithmetic."""
 import os
 import sys
 
@@ -67,3 +68,21 @@ def test_kernel_mix_shares_sum_to_one():
     e = Solver(0, [0], [], [])
     assert sum(bench.kernel_mix(e.info).values()) == 0.0
     e.close()
+
+
+def test_accuracy_metrics_match_dense_arithmetic():
+    """backward_error and the paper's residual ||Ax - b||_1 / ||b||_1 (Sec. 3.3)
+    against the same quantities from a dense matrix."""
+    import numpy as np
+    from paper_2509_07690_gb300 import synth
+    A = synth.circuit(300, seed=9)
+    a = A.todense()
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(A.n)
+    b = a @ x + 1e-9 * rng.standard_normal(A.n)
+    r = b - a @ x
+    want_be = np.abs(r).max() / (np.abs(a).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max())
+    want_r1 = np.abs(r).sum() / np.abs(b).sum()
+    assert abs(bench.backward_error(A, A.val, x, b) - want_be) <= 1e-6 * want_be
+    assert abs(bench.residual_1(A, A.val, x, b) - want_r1) <= 1e-6 * want_r1
+    assert bench.residual_1(A, A.val, x, a @ x) <= 1e-14
