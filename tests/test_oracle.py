@@ -68,6 +68,37 @@ def test_laplacian1d_pivots_closed_form(n):
     assert o.flops[0] == 3 * (n - 1)
 
 
+@pytest.mark.parametrize("seed", range(3))
+def test_bidiagonal_solves_closed_form(seed):
+    """B unit lower bidiagonal with B(i, i-1) = -a has the inverse
+    B^-1(i, j) = a^(i-j) for j <= i.  A = P B Q^T (rows and columns permuted,
+    values scaled by dr, dc inside the solver) is handed to the oracle with
+    rowperm = p, colperm = q, so its Ahat is B itself up to the scalings:
+    A x = b gives x[q[k]] = sum_{j<=k} a^(k-j) b[p[j]], and A^T z = g gives
+    z[p[j]] = sum_{i>=j} a^(i-j) g[q[i]]."""
+    rng = np.random.default_rng(600 + seed)
+    n, a = 40, 0.5
+    p = rng.permutation(n)
+    q = rng.permutation(n)
+    rows = np.concatenate([p, p[1:]])
+    cols = np.concatenate([q, q[:-1]])
+    vals = np.concatenate([np.ones(n), np.full(n - 1, -a)])
+    A = synth.from_coo(n, rows, cols, vals)
+    dr = rng.uniform(0.5, 2.0, n)
+    dc = rng.uniform(0.5, 2.0, n)
+    o = oracle.Oracle(n, A.rowptr, A.col, A.val, p, q, dr, dc)
+    assert o.nperturb == 0
+    b = rng.standard_normal(n)
+    g = rng.standard_normal(n)
+    x_cf = np.zeros(n)
+    z_cf = np.zeros(n)
+    for k in range(n):
+        x_cf[q[k]] = sum(a ** (k - j) * b[p[j]] for j in range(k + 1))
+        z_cf[p[k]] = sum(a ** (i - k) * g[q[i]] for i in range(k, n))
+    np.testing.assert_allclose(o.solve(b), x_cf, rtol=0, atol=64 * EPS * np.abs(x_cf).max())
+    np.testing.assert_allclose(o.solve_transpose(g), z_cf, rtol=0, atol=64 * EPS * np.abs(z_cf).max())
+
+
 def test_laplacian1d_scaled_pivots():
     """With diagonal scalings the pivots become dr_k * dc_k * (k+1)/k."""
     n = 20
