@@ -63,7 +63,7 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
         std::iota(q.begin(), q.end(), 0);
     } else {
         CsrPattern g = symmetrize(n, brp.data(), bci.data());
-        if (opt.ordering == 1) nd_order(g, q, opt.nd_leaf); else amd_order(g, q, opt.amd_dense);
+        if (opt.ordering == 1) nd_order(g, q, opt.nd_leaf, opt.amd_dense); else amd_order(g, q, opt.amd_dense);
     }
     P.rowperm.resize(n); P.colperm.resize(n);
     for (int32_t k = 0; k < n; ++k) { P.colperm[k] = q[k]; P.rowperm[k] = mrow[q[k]]; }

@@ -5,8 +5,13 @@
 // separator vertices with no neighbour on the far side back to the near side.
 // Both sides are ordered recursively, then the separator last.  Subgraphs of
 // at most leaf_size vertices are ordered by AMD.  Disconnected subgraphs are
-// ordered component by component.
+// ordered component by component.  Vertices denser than
+// max(16, dense_factor sqrt(n)) (the hub rows of circuit matrices) take part
+// in no dissection and are ordered last, as AMD orders them: a hub adjacent
+// to most of the graph leaves level structures only a few levels deep, so
+// every separator would be huge.
 #include <algorithm>
+#include <cmath>
 #include <cstdint>
 #include <vector>
 
@@ -83,18 +88,27 @@ static void order_leaf(const CsrPattern& g, const std::vector<int32_t>& verts, s
 
 }  // namespace
 
-void nd_order(const CsrPattern& g, std::vector<int32_t>& perm, int32_t leaf_size) {
+void nd_order(const CsrPattern& g, std::vector<int32_t>& perm, int32_t leaf_size, double dense_factor) {
     const int32_t n = g.n;
     perm.clear();
     perm.reserve(n);
     std::vector<int32_t> tag(n, 0), lv(n, -1), order;
     int32_t next_tag = 1;
+    // dense vertices carry a tag no subgraph uses, so every search skips them
+    const double mean_deg = n > 0 ? (double)g.rp[n] / (double)n : 0.0;
+    const int32_t dense_thr =
+        std::max<int32_t>(16, (int32_t)std::min(dense_factor * std::sqrt((double)n), 10.0 * mean_deg));
+    std::vector<int32_t> dense;
+    if (n > 32)
+        for (int32_t i = 0; i < n; ++i)
+            if (g.rp[i + 1] - g.rp[i] > dense_thr) { dense.push_back(i); tag[i] = -1; }
     // explicit work stack: (vertex list, tag, phase); phase 0 = split, 1 = emit separator
     struct Task { std::vector<int32_t> verts; int32_t tag; bool emit; };
     std::vector<Task> stack;
-    std::vector<int32_t> all(n);
-    for (int32_t i = 0; i < n; ++i) all[i] = i;
-    stack.push_back({all, 0, false});
+    std::vector<int32_t> all;
+    all.reserve(n - dense.size());
+    for (int32_t i = 0; i < n; ++i) if (tag[i] == 0) all.push_back(i);
+    if (!all.empty()) stack.push_back({all, 0, false});
     while (!stack.empty()) {
         Task t = std::move(stack.back());
         stack.pop_back();
@@ -181,6 +195,7 @@ void nd_order(const CsrPattern& g, std::vector<int32_t>& perm, int32_t leaf_size
         stack.push_back({B, tb, false});
         stack.push_back({A, ta, false});
     }
+    for (int32_t d : dense) perm.push_back(d);
 }
 
 }  // namespace hylu

@@ -27,8 +27,10 @@ bool max_product_matching(int32_t n, const int64_t* rp, const int32_t* ci, const
 void amd_order(const CsrPattern& g, std::vector<int32_t>& perm, double dense_factor = 10.0);
 
 // Nested dissection ordering (Sec. 2.1 [11]) of a symmetric pattern given
-// without its diagonal; leaves of at most leaf_size vertices use AMD.
-void nd_order(const CsrPattern& g, std::vector<int32_t>& perm, int32_t leaf_size = 256);
+// without its diagonal; leaves of at most leaf_size vertices use AMD; vertices
+// denser than max(16, dense_factor sqrt(n)) are ordered last, as in amd_order.
+void nd_order(const CsrPattern& g, std::vector<int32_t>& perm, int32_t leaf_size = 256,
+              double dense_factor = 2.0);
 
 // Symmetric pattern of A + A^T without the diagonal, for an n x n CSR.
 CsrPattern symmetrize(int32_t n, const int64_t* rp, const int32_t* ci);

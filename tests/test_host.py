@@ -106,6 +106,35 @@ def test_orderings_are_permutations_and_reduce_fill(ordering):
         nat.close()
 
 
+ORDERING_QUALITY = [
+    ("grid5_64", lambda: synth.grid5(64)),
+    ("aniso_32", lambda: synth.aniso9(32)),
+    ("convdiff_12", lambda: synth.convdiff3d(12)),
+    ("circuit_3000", lambda: synth.circuit(3000, seed=12)),
+    ("circuit_20000", lambda: synth.circuit(20000, seed=3)),
+]
+
+
+@pytest.mark.parametrize("name,make", ORDERING_QUALITY, ids=[c[0] for c in ORDERING_QUALITY])
+def test_ordering_fill_close_to_superlu_mmd(name, make):
+    """Fill of the AMD and nested dissection orderings against an independent
+    library ordering: SuperLU's multiple minimum degree on A^T + A (scipy
+    splu, diagonal pivots, symmetric mode), |L| + |U| counted with the
+    diagonal once.  AMD stays within 1.1x of it; nested dissection within
+    1.35x, circuit matrices included (their hub rows are ordered last, as
+    AMD orders them)."""
+    sla = pytest.importorskip("scipy.sparse.linalg")
+    import scipy.sparse as sp
+    A = make()
+    M = sp.csc_matrix(sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n)))
+    lu = sla.splu(M, permc_spec="MMD_AT_PLUS_A", diag_pivot_thresh=0.0, options={"SymmetricMode": True})
+    mmd = lu.L.nnz + lu.U.nnz - A.n
+    for ordering, bound in ((0, 1.1), (1, 1.35)):
+        s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering)
+        assert s.info.nnz_lu <= bound * mmd, (ordering, s.info.nnz_lu, mmd)
+        s.close()
+
+
 def test_nested_dissection_fill_grows_slowly_on_grids():
     """2D grids: nested dissection fill grows like n log n, not n^1.5."""
     fills = []
