@@ -22,6 +22,7 @@ CASES = [
     ("convdiff_10_nd", lambda: synth.convdiff3d(10), {"ordering": 1}),
     ("aniso_24_nd_sn9", lambda: synth.aniso9(24), {"ordering": 1, "sn_max": 9}),
     ("circuit_800_natural", lambda: synth.circuit(800, seed=2), {"ordering": 2}),
+    ("circuit_3000_nd", lambda: synth.circuit(3000, seed=12), {"ordering": 1}),
 ]
 
 

@@ -137,6 +137,7 @@ CASES = [
     ("aniso_24_nd", lambda: synth.aniso9(24), {"ordering": 1}),
     ("circuit_2500", lambda: synth.circuit(2500, seed=31), {}),
     ("circuit_4000", lambda: synth.circuit(4000, seed=77), {}),
+    ("circuit_4000_nd", lambda: synth.circuit(4000, seed=77), {"ordering": 1}),
 ]
 
 

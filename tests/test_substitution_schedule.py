@@ -41,6 +41,7 @@ CASES = [
     ("aniso_24_nd", lambda: synth.aniso9(24), {"ordering": 1}),
     ("convdiff_8_sn7", lambda: synth.convdiff3d(8), {"ordering": 1, "sn_max": 7}),
     ("dense_100", lambda: _dense(100, 3), {}),
+    ("circuit_3000_nd", lambda: synth.circuit(3000, seed=12), {"ordering": 1}),
 ]
 
 
