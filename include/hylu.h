@@ -59,6 +59,8 @@ extern "C" {
 #define HYLU_ORDER_ND 1
 #define HYLU_ORDER_NATURAL 2
 #define HYLU_ORDER_USER 3
+#define HYLU_ORDER_AUTO 4   /* AMD and nested dissection both; the plan with the lower estimated
+                               factorization time is kept (see hylu_analyze) */
 
 typedef struct hylu_handle hylu_handle; /* opaque, owned by the library */
 
@@ -116,6 +118,9 @@ typedef struct {
     double flops_sup_sup;      /* updates from source supernodes into supernode rows   */
     double flops_in_supernode; /* supernode rows against the earlier rows of their own
                                   diagonal block (the in-supernode factorization)     */
+    int32_t ordering;          /* HYLU_ORDER_* the plan was built with (HYLU_ORDER_AUTO
+                                  resolves to AMD or ND; a batch whose systems chose
+                                  differently reports HYLU_ORDER_AUTO)                */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */
@@ -131,6 +136,12 @@ int hylu_default_options(hylu_options* opt);
  * opt->static_pivot == 0).  On success *out is a new handle (free it with
  * hylu_destroy).  Errors: HYLU_ERR_ARG, HYLU_ERR_PATTERN,
  * HYLU_ERR_STRUCT_SINGULAR, HYLU_ERR_NOMEM.  Runs on the host only.
+ * HYLU_ORDER_AUTO analyses under both AMD and nested dissection and keeps
+ * the plan whose estimated factorization time is lower: the larger of its
+ * flops at 1.06e12 flop/s (the measured FP64 rate of a GB300) and its
+ * dependency levels at 21 us each (the measured cost of one level along the
+ * factor kernel's chain); info.ordering reports the choice.  Any other
+ * ordering value outside 0..4 returns HYLU_ERR_ARG.
  * n = 0 (an empty system) is accepted: hylu_factor, hylu_refactor,
  * hylu_solve, hylu_solve_transpose, hylu_grad_values, hylu_tune and the
  * exports then return HYLU_OK without touching the device, and their device

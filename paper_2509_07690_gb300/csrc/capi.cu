@@ -449,6 +449,7 @@ int hylu_analyze(int32_t n, int64_t nnz, const int64_t* rowptr, const int32_t* c
     hylu_options o;
     if (opt) o = *opt; else hylu_default_options(&o);
     if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
+    if (o.ordering < HYLU_ORDER_AMD || o.ordering > HYLU_ORDER_AUTO) return HYLU_ERR_ARG;
     if (o.precision != 0 && o.precision != 1) return HYLU_ERR_ARG;
     if (!(o.heavy_ratio >= 0.0)) return HYLU_ERR_ARG;
     if (o.precision == 1 && o.refine == 0) o.refine = 1;   // FP32 factors: always refine in FP64
@@ -541,6 +542,7 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->flops_sup_row = P.flops_sup_row;
     info->flops_sup_sup = P.flops_sup_sup;
     info->flops_in_supernode = P.flops_in_sn;
+    info->ordering = P.ordering;
     info->analyze_ms = P.analyze_ms;
     int rc = HYLU_OK;
     if (h->factored && h->uploaded) rc = read_status(h, h->last);
@@ -657,6 +659,7 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
     hylu_options o;
     if (opt) o = *opt; else hylu_default_options(&o);
     if (o.sn_max < 1 || o.sn_max > 256) return HYLU_ERR_ARG;
+    if (o.ordering < HYLU_ORDER_AMD || o.ordering > HYLU_ORDER_AUTO) return HYLU_ERR_ARG;
     if (o.precision != 0 && o.precision != 1) return HYLU_ERR_ARG;
     if (!(o.heavy_ratio >= 0.0)) return HYLU_ERR_ARG;
     if (o.precision == 1 && o.refine == 0) o.refine = 1;

@@ -21,8 +21,34 @@ static int validate(int32_t n, const int64_t* rp, const int32_t* ci) {
     return 0;
 }
 
+// Estimated factorization time of a plan on one GB300, for choosing between
+// orderings (Sec. 2.1: the kernels and, here, the ordering are chosen from the
+// flop count and the structure the symbolic factorization yields): the larger
+// of the flops at the measured FP64 rate (1.06e12 flop/s) and the dependency
+// chain at the measured cost of one level along it (about 21 us: 182 ms for
+// the 8,676-level chain of the circuit workload under AMD).
+static double estimated_seconds(const Plan& P) {
+    return std::max(P.flops_unpadded / 1.06e12, (double)P.row_levels * 21e-6);
+}
+
 int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
             const int32_t* user_perm, const AnalyzeOptions& opt, Plan& P) {
+    if (opt.ordering == HYLU_ORDER_AUTO) {
+        // both fill-reducing orderings, then the plan with the lower estimate
+        // (AMD on a tie)
+        AnalyzeOptions oa = opt, ob = opt;
+        oa.ordering = HYLU_ORDER_AMD;
+        ob.ordering = HYLU_ORDER_ND;
+        Plan pa, pb;
+        int rc = analyze(n, rp, ci, v, user_perm, oa, pa);
+        if (rc) return rc;
+        rc = analyze(n, rp, ci, v, user_perm, ob, pb);
+        if (rc) return rc;
+        const double ms = pa.analyze_ms + pb.analyze_ms;
+        P = estimated_seconds(pb) < estimated_seconds(pa) ? std::move(pb) : std::move(pa);
+        P.analyze_ms = ms;
+        return 0;
+    }
     auto t0 = std::chrono::steady_clock::now();
     int st = validate(n, rp, ci);
     if (st) return st;
@@ -65,6 +91,7 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
         CsrPattern g = symmetrize(n, brp.data(), bci.data());
         if (opt.ordering == 1) nd_order(g, q, opt.nd_leaf, opt.amd_dense); else amd_order(g, q, opt.amd_dense);
     }
+    P.ordering = (opt.ordering >= 0 && opt.ordering <= 3) ? opt.ordering : HYLU_ORDER_AMD;
     P.rowperm.resize(n); P.colperm.resize(n);
     for (int32_t k = 0; k < n; ++k) { P.colperm[k] = q[k]; P.rowperm[k] = mrow[q[k]]; }
     P.dr = dr; P.dc = dc;

@@ -128,6 +128,7 @@ int combine(const std::vector<const Plan*>& sys, int32_t nsets, Plan& C, BatchLa
         C.flops_sup_row += P.flops_sup_row;
         C.flops_sup_sup += P.flops_sup_sup;
         C.flops_in_sn += P.flops_in_sn;
+        C.ordering = (q == 0 || C.ordering == P.ordering) ? P.ordering : HYLU_ORDER_AUTO;   // AUTO: mixed
         C.max_sn = std::max(C.max_sn, P.max_sn);
         C.max_row = std::max(C.max_row, P.max_row);
         C.analyze_ms += P.analyze_ms;

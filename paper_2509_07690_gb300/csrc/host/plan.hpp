@@ -75,6 +75,7 @@ struct Plan {
     // and the *_off arrays give each instance's slice of the per-level
     // count arrays above (empty: one slice, the whole array)
     std::vector<int32_t> node_inst, fwd_off, bwd_off, ut_off, lt_off;
+    int32_t ordering = 0;               // HYLU_ORDER_* the plan was built with (AUTO: mixed batch)
     int32_t max_row = 0;                // longest row pattern (L + block + tail)
     int32_t max_sn = 1;
     double analyze_ms = 0.0;
@@ -82,7 +83,7 @@ struct Plan {
 };
 
 struct AnalyzeOptions {
-    int ordering = 0;        // 0 AMD, 1 ND, 2 natural, 3 user
+    int ordering = 0;        // 0 AMD, 1 ND, 2 natural, 3 user, 4 the better of AMD and ND
     int static_pivot = 1;    // maximum-product matching
     int scale = 1;           // apply the matching's scalings
     int sn_max = 256;

@@ -15,7 +15,7 @@ _OPTS = [("ordering", "i"), ("static_pivot", "i"), ("scale", "i"), ("sn_max", "i
 _SCALARS = [("n", "i"), ("nnz_a", "q"), ("nnodes", "i"), ("nnz_l", "q"), ("nnz_panel", "q"),
             ("nnz_store", "q"), ("nnz_f", "q"), ("flops_unpadded", "d"), ("flops_padded", "d"),
             ("n_tasks", "i"), ("row_levels", "i"), ("flops_row_row", "d"), ("flops_sup_row", "d"),
-            ("flops_sup_sup", "d"), ("flops_in_sn", "d"), ("max_row", "i"), ("max_sn", "i"),
+            ("flops_sup_sup", "d"), ("flops_in_sn", "d"), ("ordering", "i"), ("max_row", "i"), ("max_sn", "i"),
             ("analyze_ms", "d")]
 I32, I64, F64 = np.int32, np.int64, np.float64
 _ARRAYS = [("a_rp", I64), ("a_ci", I32), ("rowperm", I32), ("colperm", I32), ("dr", F64), ("dc", F64),

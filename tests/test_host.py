@@ -135,6 +135,60 @@ def test_ordering_fill_close_to_superlu_mmd(name, make):
         s.close()
 
 
+def _estimate(info):
+    return max(info.flops / 1.06e12, info.factor_levels * 21e-6)
+
+
+@pytest.mark.parametrize("name,make", [("grid5_32", lambda: synth.grid5(32)),
+                                       ("circuit_20000", lambda: synth.circuit(20000, seed=3)),
+                                       ("convdiff_12", lambda: synth.convdiff3d(12)),
+                                       ("circuit_100k", lambda: synth.workload("circuit_100k"))])
+def test_auto_ordering_keeps_the_lower_estimate(name, make):
+    """HYLU_ORDER_AUTO analyses under AMD and nested dissection and keeps the
+    plan with the lower estimated factorization time (flops at the FP64 rate
+    against the dependency chain); the kept plan is the one that ordering
+    gives on its own."""
+    A = make()
+    views, est = {}, {}
+    for o in (0, 1):
+        s = Solver(A.n, A.rowptr, A.col, A.val, ordering=o)
+        assert s.info.ordering == o
+        est[o] = _estimate(s.info)
+        v = _plan_views(s.h)
+        del v[INFO_FIELDS.index("analyze_ms")]
+        views[o] = v
+        s.close()
+    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=4)
+    want = 1 if est[1] < est[0] else 0
+    assert s.info.ordering == want
+    v = _plan_views(s.h)
+    del v[INFO_FIELDS.index("analyze_ms")]
+    _same_views(views[want], v)
+    s.close()
+    if name == "circuit_100k":
+        assert want == 1                                 # the shallower chain wins
+
+
+def test_ordering_reported_and_checked():
+    A = synth.grid5(10)
+    for o in (0, 1, 2):
+        s = Solver(A.n, A.rowptr, A.col, A.val, ordering=o)
+        assert s.info.ordering == o
+        s.close()
+    s = Solver(A.n, A.rowptr, A.col, A.val, np.arange(A.n, dtype=np.int32)[::-1].copy(), ordering=3)
+    assert s.info.ordering == 3
+    s.close()
+    for bad in (-1, 5):
+        with pytest.raises(capi.HyluError) as e:
+            capi.hylu_analyze(A.n, A.rowptr, A.col, A.val, None, capi.default_options(ordering=bad))
+        assert e.value.code == -1
+    from paper_2509_07690_gb300.solver import BatchSolver
+    mats = [synth.grid5(6), synth.circuit(300, seed=4)]
+    bs = BatchSolver([(m.n, m.rowptr, m.col, m.val) for m in mats], 1, ordering=1)
+    assert bs.info.ordering == 1
+    bs.close()
+
+
 def test_nested_dissection_fill_grows_slowly_on_grids():
     """2D grids: nested dissection fill grows like n log n, not n^1.5."""
     fills = []
@@ -475,7 +529,7 @@ def test_empty_system_through_the_binding():
 INFO_FIELDS = ["n", "nnz_a", "nnz_lu", "nnz_store", "nnodes", "nsupernodes", "rows_in_supernodes",
                "max_supernode", "ntasks", "flops", "flops_padded", "nheavy", "factor_levels",
                "fwd_levels", "bwd_levels", "analyze_ms", "flops_row_row", "flops_sup_row", "flops_sup_sup",
-               "flops_in_supernode"]
+               "flops_in_supernode", "ordering"]
 
 
 def _plan_views(h):
