@@ -12,14 +12,26 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SO = os.path.join(_HERE, "libhylu.so")
 _lib = None
 
+# the #define constants of include/hylu.h (a host test keeps the two in step)
 HYLU_OK = 0
 HYLU_WARN_PERTURBED = 1
 HYLU_WARN_REFINE_STALLED = 2
-ERRORS = {-1: "HYLU_ERR_ARG", -2: "HYLU_ERR_PATTERN", -3: "HYLU_ERR_STRUCT_SINGULAR",
-          -4: "HYLU_ERR_NOMEM", -5: "HYLU_ERR_CUDA", -6: "HYLU_ERR_DEVICE_TIMEOUT",
-          -7: "HYLU_ERR_STATE", -8: "HYLU_ERR_INTERNAL", -9: "HYLU_ERR_TOO_LARGE"}
+HYLU_ERR_ARG = -1
+HYLU_ERR_PATTERN = -2
+HYLU_ERR_STRUCT_SINGULAR = -3
+HYLU_ERR_NOMEM = -4
+HYLU_ERR_CUDA = -5
+HYLU_ERR_DEVICE_TIMEOUT = -6
+HYLU_ERR_STATE = -7
+HYLU_ERR_INTERNAL = -8
 HYLU_ERR_TOO_LARGE = -9
+HYLU_ORDER_AMD = 0
+HYLU_ORDER_ND = 1
+HYLU_ORDER_NATURAL = 2
+HYLU_ORDER_USER = 3
+HYLU_ORDER_AUTO = 4
 HYLU_STATIC_SOLVE_MAX_N = 262144
+ERRORS = {v: k for k, v in list(globals().items()) if k.startswith("HYLU_ERR_")}
 
 
 class HyluError(RuntimeError):

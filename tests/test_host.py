@@ -27,6 +27,16 @@ def test_library_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def test_binding_constants_match_the_header():
+    """Every #define HYLU_* of include/hylu.h has the same value in the binding."""
+    header = open(os.path.join(ROOT, "include", "hylu.h")).read()
+    defines = re.findall(r"^#define\s+(HYLU_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", header, re.M)
+    assert {name for name, _ in defines} == {k for k in dir(capi) if k.startswith("HYLU_")}
+    for name, value in defines:
+        assert getattr(capi, name) == int(value), name
+    assert capi.ERRORS[-9] == "HYLU_ERR_TOO_LARGE" and len(capi.ERRORS) == 9
+
+
 def _dense_csr(a):
     r, c = np.nonzero(a)
     return synth.from_coo(a.shape[0], r, c, a[r, c])
