@@ -2,7 +2,9 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <exception>
 #include <numeric>
+#include <thread>
 
 #include "plan.hpp"
 #include "../../../include/hylu.h"
@@ -36,17 +38,25 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
     if (opt.ordering == HYLU_ORDER_AUTO) {
         // both fill-reducing orderings, then the plan with the lower estimate
         // (AMD on a tie)
+        const auto w0 = std::chrono::steady_clock::now();
         AnalyzeOptions oa = opt, ob = opt;
         oa.ordering = HYLU_ORDER_AMD;
         ob.ordering = HYLU_ORDER_ND;
         Plan pa, pb;
-        int rc = analyze(n, rp, ci, v, user_perm, oa, pa);
+        // the two analyses share no state: nested dissection on a second thread
+        int rb = 0;
+        std::exception_ptr eb;
+        std::thread t([&] {
+            try { rb = analyze(n, rp, ci, v, user_perm, ob, pb); } catch (...) { eb = std::current_exception(); }
+        });
+        int rc = 0;
+        try { rc = analyze(n, rp, ci, v, user_perm, oa, pa); } catch (...) { t.join(); throw; }
+        t.join();
+        if (eb) std::rethrow_exception(eb);
         if (rc) return rc;
-        rc = analyze(n, rp, ci, v, user_perm, ob, pb);
-        if (rc) return rc;
-        const double ms = pa.analyze_ms + pb.analyze_ms;
+        if (rb) return rb;
         P = estimated_seconds(pb) < estimated_seconds(pa) ? std::move(pb) : std::move(pa);
-        P.analyze_ms = ms;
+        P.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - w0).count();
         return 0;
     }
     auto t0 = std::chrono::steady_clock::now();

@@ -47,6 +47,30 @@ class Solver:
         self.info = capi.hylu_get_info(self.h)
         self._factored = False
 
+    @classmethod
+    def from_csr(cls, A, **opts) -> "Solver":
+        """A solver for a square CSR matrix given as any object with
+        indptr / indices / data (scipy.sparse.csr_matrix, for one).  Column
+        indices are sorted per row on a copy (the analysis requires them
+        sorted); duplicate entries are refused by the analysis.  The values
+        in that sorted order are kept as `values`: factor() takes them (or
+        later value sets in the same order) as a CUDA tensor."""
+        n = int(A.shape[0])
+        if A.shape[0] != A.shape[1]:
+            raise ValueError(f"from_csr: the matrix must be square, got {A.shape}")
+        rowptr = np.asarray(A.indptr, dtype=np.int64)
+        col = np.asarray(A.indices, dtype=np.int32).copy()
+        val = np.asarray(A.data, dtype=np.float64).copy()
+        for i in range(n):
+            a, b = rowptr[i], rowptr[i + 1]
+            if b - a > 1 and np.any(np.diff(col[a:b]) < 0):
+                o = np.argsort(col[a:b], kind="stable")
+                col[a:b] = col[a:b][o]
+                val[a:b] = val[a:b][o]
+        s = cls(n, rowptr, col, val, **opts)
+        s.values = val
+        return s
+
     # ------------------------------------------------------------ checkpoint
     def save(self, path=None) -> bytes:
         """The analysis as a byte image (hylu_plan_save), also written to

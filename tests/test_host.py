@@ -461,6 +461,36 @@ def test_binding_refuses_arrays_of_the_wrong_size_or_type():
     s.close()
 
 
+def test_solver_from_scipy_csr():
+    """A scipy CSR matrix with unsorted column indices: the solver sorts a
+    copy per row (values moved with their columns) and analyses the same
+    pattern as the sorted CSR; a duplicate entry is refused."""
+    sp = pytest.importorskip("scipy.sparse")
+    A = synth.circuit(1500, seed=5)
+    M = sp.csr_matrix((A.val, A.col, A.rowptr), shape=(A.n, A.n))
+    rng = np.random.default_rng(2)
+    ind, dat = M.indices.copy(), M.data.copy()
+    for i in range(A.n):                               # shuffle every row
+        a, b = M.indptr[i], M.indptr[i + 1]
+        o = rng.permutation(b - a)
+        ind[a:b], dat[a:b] = ind[a:b][o], dat[a:b][o]
+    U = sp.csr_matrix((dat, ind, M.indptr.copy()), shape=M.shape)
+    assert not U.has_sorted_indices
+    s = Solver.from_csr(U)
+    ref = Solver(A.n, A.rowptr, A.col, A.val)
+    assert np.array_equal(s.values, A.val)
+    _same_views(_plan_views(s.h)[:INFO_FIELDS.index("analyze_ms")], _plan_views(ref.h)[:INFO_FIELDS.index("analyze_ms")])
+    _same_views(_plan_views(s.h)[len(INFO_FIELDS):], _plan_views(ref.h)[len(INFO_FIELDS):])
+    s.close()
+    ref.close()
+    D = sp.csr_matrix((np.array([1.0, 2.0, 3.0]), np.array([0, 0, 1]), np.array([0, 2, 3])), shape=(2, 2))
+    with pytest.raises(capi.HyluError) as e:
+        Solver.from_csr(D)
+    assert e.value.code == -2
+    with pytest.raises(ValueError):
+        Solver.from_csr(sp.csr_matrix(np.ones((2, 3))))
+
+
 # ------------------------------------------------------ empty system
 def test_empty_system_returns_ok_without_device_work():
     """n = 0 is a valid, degenerate system: analysis gives an empty plan, and
