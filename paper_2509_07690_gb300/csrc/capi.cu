@@ -204,7 +204,7 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
         }
         auto slice = [&](const std::vector<int32_t>& off, const std::vector<int32_t>& cnt, const int32_t** out) {
             std::vector<int32_t> o = off.empty() ? std::vector<int32_t>{0, (int32_t)cnt.size()} : off;
-            int32_t* dp;
+            int32_t* dp = nullptr;
             int rc = upload(h, &dp, o, st);
             *out = dp;
             return rc;
