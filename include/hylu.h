@@ -133,7 +133,9 @@ int hylu_default_options(hylu_options* opt);
  * detection (consecutive rows with identical U structure, Sec. 2.2) and the
  * task schedule (Sec. 2.2.1).  All inputs are host arrays owned by the caller
  * and are copied; `vals` is only read for the matching (may be NULL when
- * opt->static_pivot == 0).  On success *out is a new handle (free it with
+ * opt->static_pivot == 0; with static pivoting, a NaN or infinite value
+ * returns HYLU_ERR_ARG).
+ * On success *out is a new handle (free it with
  * hylu_destroy).  Errors: HYLU_ERR_ARG, HYLU_ERR_PATTERN,
  * HYLU_ERR_STRUCT_SINGULAR, HYLU_ERR_NOMEM.  Runs on the host only.
  * HYLU_ORDER_AUTO analyses under both AMD and nested dissection and keeps

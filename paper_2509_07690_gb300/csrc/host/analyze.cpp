@@ -71,6 +71,8 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
     std::vector<double> dr(n, 1.0), dc(n, 1.0);
     if (opt.static_pivot) {
         if (!v) return HYLU_ERR_ARG;
+        for (int64_t q = 0; q < rp[n]; ++q)          // the matching weighs finite magnitudes only
+            if (!std::isfinite(v[q])) return HYLU_ERR_ARG;
         if (!max_product_matching(n, rp, ci, v, match, dr, dc)) return HYLU_ERR_STRUCT_SINGULAR;
         if (!opt.scale) { std::fill(dr.begin(), dr.end(), 1.0); std::fill(dc.begin(), dc.end(), 1.0); }
     } else {

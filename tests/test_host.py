@@ -419,6 +419,14 @@ def test_error_codes():
                           np.array([0, 0], np.int32), capi.default_options(ordering=3))
     assert e.value.code == -1
     A = synth.grid5(4)
+    for bad in (np.nan, np.inf, -np.inf):             # the matching needs finite values
+        v = A.val.copy()
+        v[3] = bad
+        with pytest.raises(capi.HyluError) as e:
+            capi.hylu_analyze(A.n, A.rowptr, A.col, v)
+        assert e.value.code == -1
+        h = capi.hylu_analyze(A.n, A.rowptr, A.col, v, None, capi.default_options(static_pivot=0))
+        capi.hylu_destroy(h)                          # without static pivoting the values are not read
     h = capi.hylu_analyze(A.n, A.rowptr, A.col, A.val)
     with pytest.raises(capi.HyluError) as e:          # refactor before factor
         capi.hylu_refactor(h, 0, 0)
