@@ -120,6 +120,9 @@ class Solver:
         if d_x is None:
             d_x = torch.empty_like(d_b)
         _device_f64(d_x, "d_x", numel=d_b.numel())
+        nbytes = 8 * d_b.numel()
+        if nbytes and d_x.data_ptr() < d_b.data_ptr() + nbytes and d_b.data_ptr() < d_x.data_ptr() + nbytes:
+            raise ValueError("solve: d_b and d_x overlap (the solution may not be written over the right-hand side)")
         fn = capi.hylu_solve_transpose if transpose else capi.hylu_solve
         self.last_rc = fn(self.h, d_b.data_ptr(), d_x.data_ptr(), _nrhs(d_b, self.n), self.n, _stream(stream))
         return d_x

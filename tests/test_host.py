@@ -568,6 +568,14 @@ def test_empty_system_through_the_binding():
     assert tuple(x.shape) == (4, 0)
     with pytest.raises(ValueError):                   # an empty system takes empty tensors
         s.solve(dev(3), stream=st)
+    A = synth.grid5(4)                                # the solution may not overwrite b
+    t = Solver(A.n, A.rowptr, A.col, A.val)
+    b = dev(2, A.n)
+    with pytest.raises(ValueError):
+        t.solve(b, b, stream=st)
+    with pytest.raises(ValueError):
+        t.solve(b[0], b.view(-1)[5:5 + A.n], stream=st)
+    t.close()
     assert capi.hylu_launch_count() == l0
     assert s.get_info().device_status == 0
     s.close()
