@@ -121,6 +121,10 @@ typedef struct {
     int32_t ordering;          /* HYLU_ORDER_* the plan was built with (HYLU_ORDER_AUTO
                                   resolves to AMD or ND; a batch whose systems chose
                                   differently reports HYLU_ORDER_AUTO)                */
+    double analyze_phase_ms[4]; /* analysis wall time by phase: [0] matching and
+                                   scaling, [1] ordering, [2] symbolic factorization,
+                                   supernodes and schedules, [3] value map (a batch:
+                                   summed over its systems)                           */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */

@@ -543,6 +543,7 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->flops_sup_sup = P.flops_sup_sup;
     info->flops_in_supernode = P.flops_in_sn;
     info->ordering = P.ordering;
+    for (int ph = 0; ph < 4; ++ph) info->analyze_phase_ms[ph] = P.analyze_phase_ms[ph];
     info->analyze_ms = P.analyze_ms;
     int rc = HYLU_OK;
     if (h->factored && h->uploaded) rc = read_status(h, h->last);

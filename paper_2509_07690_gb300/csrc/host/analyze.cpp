@@ -60,6 +60,9 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
         return 0;
     }
     auto t0 = std::chrono::steady_clock::now();
+    auto since = [](std::chrono::steady_clock::time_point a) {
+        return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - a).count();
+    };
     int st = validate(n, rp, ci);
     if (st) return st;
     P.n = n;
@@ -81,6 +84,8 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
     // row of A that lands on row j of M*A: the row matched to column j
     std::vector<int32_t> mrow(n);
     for (int32_t i = 0; i < n; ++i) mrow[match[i]] = i;
+    P.analyze_phase_ms[0] = since(t0);
+    const auto t_order = std::chrono::steady_clock::now();
     // pattern of B = M*A (rows permuted), for the ordering
     std::vector<int64_t> brp(n + 1, 0);
     std::vector<int32_t> bci(rp[n]);
@@ -103,6 +108,8 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
         CsrPattern g = symmetrize(n, brp.data(), bci.data());
         if (opt.ordering == 1) nd_order(g, q, opt.nd_leaf, opt.amd_dense); else amd_order(g, q, opt.amd_dense);
     }
+    P.analyze_phase_ms[1] = since(t_order);
+    const auto t_sym = std::chrono::steady_clock::now();
     P.ordering = (opt.ordering >= 0 && opt.ordering <= 3) ? opt.ordering : HYLU_ORDER_AMD;
     P.rowperm.resize(n); P.colperm.resize(n);
     for (int32_t k = 0; k < n; ++k) { P.colperm[k] = q[k]; P.rowperm[k] = mrow[q[k]]; }
@@ -133,6 +140,8 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
     supernode_partition(n, F, std::max(1, opt.sn_max), P.sn_start);
     build_nodes(P, F);
     split_heavy_rows(P, opt.heavy_ratio);
+    P.analyze_phase_ms[2] = since(t_sym);
+    const auto t_map = std::chrono::steady_clock::now();
     // ---- Ahat entries -> slots of their row: [0, nL) the L list, then the
     //      node's block (s slots) and tail
     P.ah_rp = ah.rp;
@@ -167,7 +176,8 @@ int analyze(int32_t n, const int64_t* rp, const int32_t* ci, const double* v,
     }
     P.max_sn = 1;
     for (int32_t s = 0; s < P.nnodes; ++s) P.max_sn = std::max(P.max_sn, P.sn_start[s + 1] - P.sn_start[s]);
-    P.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    P.analyze_phase_ms[3] = since(t_map);
+    P.analyze_ms = since(t0);
     return 0;
 }
 

@@ -132,6 +132,7 @@ int combine(const std::vector<const Plan*>& sys, int32_t nsets, Plan& C, BatchLa
         C.max_sn = std::max(C.max_sn, P.max_sn);
         C.max_row = std::max(C.max_row, P.max_row);
         C.analyze_ms += P.analyze_ms;
+        for (int ph = 0; ph < 4; ++ph) C.analyze_phase_ms[ph] += P.analyze_phase_ms[ph];
     }
     C.sn_start.push_back(C.n);
     C.node_panel_off.push_back(p_off);

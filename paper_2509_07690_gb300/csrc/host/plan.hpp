@@ -79,6 +79,9 @@ struct Plan {
     int32_t max_row = 0;                // longest row pattern (L + block + tail)
     int32_t max_sn = 1;
     double analyze_ms = 0.0;
+    // analysis wall time by phase: matching and scaling, ordering, symbolic
+    // factorization with the node tables and schedules, value map
+    double analyze_phase_ms[4] = {0.0, 0.0, 0.0, 0.0};
     std::string error;
 };
 

@@ -82,7 +82,7 @@ bool visit(V& f, Plan& P, BatchLayout& B, int32_t& batch, hylu_options& o) {
     ok = ok && f(P.n) && f(P.nnz_a) && f(P.nnodes) && f(P.nnz_l) && f(P.nnz_panel) && f(P.nnz_store);
     ok = ok && f(P.nnz_f) && f(P.flops_unpadded) && f(P.flops_padded) && f(P.n_tasks) && f(P.row_levels);
     ok = ok && f(P.flops_row_row) && f(P.flops_sup_row) && f(P.flops_sup_sup) && f(P.flops_in_sn);
-    ok = ok && f(P.ordering) && f(P.max_row) && f(P.max_sn) && f(P.analyze_ms);
+    ok = ok && f(P.ordering) && f(P.max_row) && f(P.max_sn) && f(P.analyze_ms) && f(P.analyze_phase_ms);
     // pattern of A, preprocessing, Ahat scatter
     ok = ok && f(P.a_rp) && f(P.a_ci) && f(P.rowperm) && f(P.colperm) && f(P.dr) && f(P.dc);
     ok = ok && f(P.ah_rp) && f(P.ah_slot) && f(P.ah_src) && f(P.ah_scale);

@@ -16,7 +16,7 @@ _SCALARS = [("n", "i"), ("nnz_a", "q"), ("nnodes", "i"), ("nnz_l", "q"), ("nnz_p
             ("nnz_store", "q"), ("nnz_f", "q"), ("flops_unpadded", "d"), ("flops_padded", "d"),
             ("n_tasks", "i"), ("row_levels", "i"), ("flops_row_row", "d"), ("flops_sup_row", "d"),
             ("flops_sup_sup", "d"), ("flops_in_sn", "d"), ("ordering", "i"), ("max_row", "i"), ("max_sn", "i"),
-            ("analyze_ms", "d")]
+            ("analyze_ms", "d"), ("analyze_phase_ms", "4d")]
 I32, I64, F64 = np.int32, np.int64, np.float64
 _ARRAYS = [("a_rp", I64), ("a_ci", I32), ("rowperm", I32), ("colperm", I32), ("dr", F64), ("dc", F64),
            ("ah_rp", I64), ("ah_slot", I32), ("ah_src", I64), ("ah_scale", F64),
@@ -54,9 +54,9 @@ class PlanImage:
 
     def _scalar(self, f):
         size = struct.calcsize("<" + f)
-        (v,) = struct.unpack_from("<" + f, self._b, self._p)
+        v = struct.unpack_from("<" + f, self._b, self._p)
         self._p += size
-        return v
+        return v[0] if len(v) == 1 else v
 
     def _array(self, dt):
         (count,) = struct.unpack_from("<Q", self._b, self._p)
