@@ -206,6 +206,17 @@ def test_ordering_reported_and_checked():
     bs = BatchSolver([(m.n, m.rowptr, m.col, m.val) for m in mats], 1, ordering=1)
     assert bs.info.ordering == 1
     bs.close()
+    # AUTO inside a batch: each system keeps its own better plan; the batch
+    # reports the common choice, or AUTO when the systems chose differently
+    mats = [synth.grid5(6), synth.circuit(300, seed=4), synth.circuit(2500, seed=9), synth.convdiff3d(6)]
+    picks = []
+    for m in mats:
+        s = Solver(m.n, m.rowptr, m.col, m.val, ordering=4)
+        picks.append(s.info.ordering)
+        s.close()
+    bs = BatchSolver([(m.n, m.rowptr, m.col, m.val) for m in mats], 2, ordering=4)
+    assert bs.info.ordering == (picks[0] if len(set(picks)) == 1 else 4)
+    bs.close()
 
 
 def test_nested_dissection_fill_grows_slowly_on_grids():
