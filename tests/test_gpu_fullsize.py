@@ -41,14 +41,11 @@ def _be_t(A, vals, x, b):
     return np.abs(b - atx).max() / (an * np.abs(x).max() + np.abs(b).max())
 
 
-@pytest.mark.parametrize("ordering", [1, 0], ids=["nd", "amd"])
-def test_circuit_100k_pattern_and_refactor(ordering):
-    """The headline circuit workload under nested dissection (the ordering
-    bench.py times) and AMD."""
+def test_circuit_100k_pattern_and_refactor():
     torch = _torch()
     from paper_2509_07690_gb300 import Solver
     A = synth.workload("circuit_100k")
-    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering)
+    s = Solver(A.n, A.rowptr, A.col, A.val)
     _pattern_matches_oracle(s, A)
     xt, b = synth.rhs(A, 1002)
     db = torch.from_numpy(b[0]).cuda()

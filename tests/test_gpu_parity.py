@@ -119,14 +119,6 @@ def test_circuit_20k_heavy_rows(heavy_ratio):
     run_case(synth.circuit(20000, seed=77), heavy_ratio=heavy_ratio)
 
 
-@pytest.mark.parametrize("n,seed", [(3000, 12), (20000, 77)])
-def test_circuit_nested_dissection(n, seed):
-    """Circuit matrices under nested dissection, hub rows ordered last (the
-    ordering bench.py times on the circuit workload); at n = 20000 the hub
-    rows take the heavy-row queue."""
-    run_case(synth.circuit(n, seed=seed), ordering=1)
-
-
 def test_dense_600_one_heavy_panel():
     rng = np.random.default_rng(600)
     n = 600
