@@ -86,3 +86,13 @@ def test_accuracy_metrics_match_dense_arithmetic():
     assert abs(bench.backward_error(A, A.val, x, b) - want_be) <= 1e-6 * want_be
     assert abs(bench.residual_1(A, A.val, x, b) - want_r1) <= 1e-6 * want_r1
     assert bench.residual_1(A, A.val, x, a @ x) <= 1e-14
+
+
+def test_clock_samplers_are_tracked_until_stopped(tmp_path):
+    """A sampler registers itself and leaves the registry when stopped, so a
+    measurement abandoned half way can stop the ones it started."""
+    c = bench.Clocks(0, str(tmp_path / "clocks.csv"))
+    assert c in bench._ACTIVE_CLOCKS
+    c.stop()
+    assert c not in bench._ACTIVE_CLOCKS
+    c.stop()                                  # stopping twice is harmless
