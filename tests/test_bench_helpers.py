@@ -96,3 +96,14 @@ def test_clock_samplers_are_tracked_until_stopped(tmp_path):
     c.stop()
     assert c not in bench._ACTIVE_CLOCKS
     c.stop()                                  # stopping twice is harmless
+
+
+def test_ordering_choice_from_the_trial():
+    """Nested dissection unless its trial failed or a passing AMD trial was faster."""
+    good = lambda ms: {"factor_ms": ms, "backward_error": 1e-16}   # noqa: E731
+    assert bench.choose_ordering({"ND": good(50.0), "AMD": good(200.0)}) == 1
+    assert bench.choose_ordering({"ND": good(250.0), "AMD": good(200.0)}) == 0
+    assert bench.choose_ordering({"ND": {"error": "HyluError"}, "AMD": good(200.0)}) == 0
+    assert bench.choose_ordering({"ND": {"factor_ms": 50.0, "backward_error": 1e-9}, "AMD": good(200.0)}) == 0
+    assert bench.choose_ordering({"ND": good(50.0), "AMD": {"error": "HyluError"}}) == 1
+    assert bench.choose_ordering({"ND": good(250.0), "AMD": {"factor_ms": 10.0, "backward_error": 1.0}}) == 1
