@@ -465,8 +465,10 @@ def ordering_trial(args, local) -> dict:
     events) and the worst backward error, or the library error it raised."""
     import gc
     import torch
-    from paper_2509_07690_gb300 import Solver, capi
+    from paper_2509_07690_gb300 import Solver, build as pbuild, capi
+    pbuild.build()
     dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)                # the library works on the current device
     A, sets, b = make_inputs(args.n, args.scale)
     fp32 = args.precision == "fp32"
     d_b = torch.from_numpy(b).to(dev)
