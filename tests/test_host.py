@@ -377,6 +377,42 @@ def test_pattern_parity_random_unsymmetric(seed):
     s.close()
 
 
+@pytest.mark.parametrize("seed", range(20))
+def test_nested_dissection_with_dense_vertices(seed):
+    """Random sparse matrices with a few planted dense rows and columns under
+    nested dissection (dense vertices set aside and ordered last) and AUTO:
+    the ordering is a permutation with the dense vertices at its end, and the
+    pattern, partition and flop count equal the oracle's."""
+    rng = np.random.default_rng(2200 + seed)
+    n = int(rng.integers(40, 400))
+    a = np.where(rng.random((n, n)) < 4.0 / n, rng.uniform(-1, 1, (n, n)), 0.0)
+    hubs = rng.choice(n, int(rng.integers(1, 5)), replace=False)
+    for h in hubs:
+        a[h, :] = np.where(rng.random(n) < 0.6, rng.uniform(-1, 1, n), a[h, :])
+        a[:, h] = np.where(rng.random(n) < 0.6, rng.uniform(-1, 1, n), a[:, h])
+    a[np.arange(n), np.arange(n)] = np.abs(a).sum(axis=1) + 1.0
+    A = _dense_csr(a)
+    for ordering in (1, 4):
+        s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering)
+        rp, cp, dr, dc, sn = s.export_perm()
+        assert sorted(cp) == list(range(n))
+        if ordering == 1:
+            # dense: degree in A + A^T (no diagonal) above max(16, min(2 sqrt(n), 10 x mean degree))
+            pat = (a != 0) | (a.T != 0)
+            np.fill_diagonal(pat, False)
+            deg = pat.sum(axis=1)
+            thr = max(16, int(min(2.0 * np.sqrt(n), 10.0 * deg.sum() / n)))
+            dense = np.nonzero(deg > thr)[0]
+            assert set(hubs.tolist()) <= set(dense.tolist())
+            assert list(cp[n - len(dense):]) == sorted(dense.tolist())
+        o = oracle.Oracle(A.n, A.rowptr, A.col, A.val, rp, cp, dr, dc, numeric=False)
+        prp, pci = s.export_pattern()
+        assert np.array_equal(o.sn_start, sn)
+        assert np.array_equal(o.padded.rowptr, prp) and np.array_equal(o.padded.col, pci)
+        assert s.info.flops == o.flops[0]
+        s.close()
+
+
 @pytest.mark.parametrize("seed", range(16))
 def test_pattern_parity_chains_and_dense_rows(seed):
     """Dense diagonal blocks with one-sided couplings (long runs of rows whose
