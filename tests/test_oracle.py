@@ -99,6 +99,37 @@ def test_bidiagonal_solves_closed_form(seed):
     np.testing.assert_allclose(o.solve_transpose(g), z_cf, rtol=0, atol=64 * EPS * np.abs(z_cf).max())
 
 
+@pytest.mark.parametrize("n", [3, 10, 50])
+def test_arrowhead_closed_form(n):
+    """Diagonal d plus a dense last row r and last column c, natural order, no
+    scaling.  U(k,:) = {k, n-1} for k < n-1, so L(n-1, k) = r_k / d_k costs one
+    division and one multiply-add: 3 (n-1) flops.  Only the last two rows
+    share a U structure: partition {0}, ..., {n-3}, {n-2, n-1}.  The last
+    pivot is the Schur complement d_{n-1} - sum_k r_k c_k / d_k (with the
+    supernode's pivoting: the larger of the last block's candidates)."""
+    rng = np.random.default_rng(n)
+    d = rng.uniform(4.0, 5.0, n)
+    r = rng.uniform(-1, 1, n - 1)
+    c = rng.uniform(-1, 1, n - 1)
+    rows = list(range(n)) + [n - 1] * (n - 1) + list(range(n - 1))
+    cols = list(range(n)) + list(range(n - 1)) + [n - 1] * (n - 1)
+    A = synth.from_coo(n, rows, cols, list(d) + list(r) + list(c))
+    o = oracle.Oracle(n, A.rowptr, A.col, A.val)
+    assert o.flops[0] == 3 * (n - 1)
+    assert list(o.sn_start) == list(range(n - 1)) + [n]
+    L, U, piv = oracle.dense_factors(o)
+    np.testing.assert_allclose(np.diag(U)[:n - 2], d[:n - 2], rtol=0, atol=0)
+    # the last 2 x 2 block after eliminating rows 0..n-3, pivoted inside the supernode
+    s = d[n - 1] - np.sum(r[:n - 2] * c[:n - 2] / d[:n - 2])
+    blk = np.array([[d[n - 2], c[n - 2]], [r[n - 2], s]])
+    a = np.zeros((n, n))
+    a[np.arange(n), np.arange(n)] = d
+    a[n - 1, :n - 1] = r
+    a[:n - 1, n - 1] = c
+    np.testing.assert_allclose(L @ U, a[:, piv], rtol=0, atol=1e-13)
+    assert abs(np.prod(np.diag(U)[n - 2:])) == pytest.approx(abs(np.linalg.det(blk)), rel=1e-12)
+
+
 def test_laplacian1d_scaled_pivots():
     """With diagonal scalings the pivots become dr_k * dc_k * (k+1)/k."""
     n = 20
