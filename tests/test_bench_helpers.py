@@ -107,3 +107,11 @@ def test_ordering_choice_from_the_trial():
     assert bench.choose_ordering({"ND": {"factor_ms": 50.0, "backward_error": 1e-9}, "AMD": good(200.0)}) == 0
     assert bench.choose_ordering({"ND": good(50.0), "AMD": {"error": "HyluError"}}) == 1
     assert bench.choose_ordering({"ND": good(250.0), "AMD": {"factor_ms": 10.0, "backward_error": 1.0}}) == 1
+
+
+def test_workload_orderings():
+    """AMD for the 5-point grid (its configuration names AMD), nested
+    dissection for the PDE workloads and the circuit matrix."""
+    assert bench.ordering_for("grid5_64") == 0
+    for w in ("convdiff3d_64", "aniso9_512", "circuit_100k", "circuit"):
+        assert bench.ordering_for(w) == 1
