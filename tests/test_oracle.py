@@ -294,6 +294,44 @@ def test_padding_invariants(seed):
             for k in p[p < i]:
                 uk = _rows(P, k)
                 assert set(uk[uk > k]) <= set(p)
+            # exact L content: the row's own unpadded L columns before its
+            # block, each widened to its source node's full segment, and
+            # nothing more (no union over the rows of the supernode)
+            want = set()
+            for k in f[f < r]:
+                S = sn_of[k]
+                want |= set(range(sn[S], sn[S + 1]))
+            assert np.array_equal(p[p < r], np.array(sorted(want), dtype=p.dtype))
+
+
+def _golden_rows(name):
+    g = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, *v = line.split()
+        g[k] = np.array([int(t) for t in v], dtype=np.int64)
+    return g
+
+
+def test_golden_padded_pattern():
+    # tests/golden/padded_pattern_6.txt: a source supernode {0,1} feeding a
+    # standalone row (2) and a supernode row (3), and a supernode {3,4} whose
+    # second row keeps its own L column only
+    g = _golden_rows("padded_pattern_6.txt")
+    n = 6
+    a = np.zeros((n, n))
+    rng = np.random.default_rng(5)
+    for i in range(n):
+        a[i, g[f"A{i}"]] = rng.uniform(1.0, 2.0, len(g[f"A{i}"]))
+    a += 10.0 * np.eye(n)
+    A = dense_csr(a)
+    o = oracle.Oracle(n, A.rowptr, A.col, A.val, sn_max=8)
+    F, P = o.unpadded, o.padded
+    assert np.array_equal(o.sn_start, g["sn"])
+    for i in range(n):
+        assert np.array_equal(_rows(F, i), g[f"F{i}"]), i
+        assert np.array_equal(_rows(P, i), g[f"P{i}"]), i
 
 
 # -------------------------------------------- reconstruction and solves
@@ -345,3 +383,49 @@ def test_workload_small_cases_backward_error():
         xt, b = synth.rhs(m, 1)
         x, _, be = o.solve_refine(b[0], force=True)
         assert be <= 1e-12, be
+
+
+# ------------------------------------------------- backward error (Sec. 2.3)
+def _dense_backward_error(a, x, b):
+    # ||b - A x||_inf / (||A||_inf ||x||_inf + ||b||_inf), ||A||_inf the
+    # largest absolute row sum
+    r = b - a @ x
+    return np.abs(r).max() / (np.abs(a).sum(axis=1).max() * np.abs(x).max() + np.abs(b).max())
+
+
+def test_backward_error_hand_case():
+    # row sums 3, 0.5, 0.5 (||A||_inf = 3) but column sums 1, 1.5, 1.5
+    # (||A||_1 = 1.5): x = (1, 2, 3), b = (1, 1, 1) -> A x = (6, 1, 1.5),
+    # r = (-5, 0, -0.5), so the error is 5 / (3 * 3 + 1) = 0.5 exactly.  The
+    # column-sum norm would give 5 / 5.5, the 1-norms 5.5 / 12, and a dropped
+    # ||b|| term 5 / 9.
+    a = np.array([[1.0, 1.0, 1.0], [0.0, 0.5, 0.0], [0.0, 0.0, 0.5]])
+    A = dense_csr(a)
+    x = np.array([1.0, 2.0, 3.0])
+    b = np.ones(3)
+    assert oracle.backward_error(3, A.rowptr, A.col, A.val, x, b) == 0.5
+
+
+def test_backward_error_zero_denominator():
+    # x = 0 and b = 0: the residual is 0 and so is the error
+    A = dense_csr(np.array([[2.0, 1.0], [0.0, 3.0]]))
+    assert oracle.backward_error(2, A.rowptr, A.col, A.val, np.zeros(2), np.zeros(2)) == 0.0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_backward_error_matches_dense(seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(3, 80))
+    a = random_sparse(n, rng.uniform(0.05, 0.3), rng)
+    a[rng.integers(n), :] *= 7.0          # one heavy row: row and column norms differ
+    A = dense_csr(a)
+    x = rng.standard_normal(n) * rng.uniform(0.1, 10.0)
+    b = rng.standard_normal(n)
+    got = oracle.backward_error(n, A.rowptr, A.col, A.val, x, b)
+    want = _dense_backward_error(a, x, b)
+    assert abs(got - want) <= 1e-13 * want
+    # the exact solution of a diagonally dominant system has an error near eps
+    a2 = a + np.diag(np.abs(a).sum(axis=1) + 1.0)
+    A2 = dense_csr(a2)
+    xs = np.linalg.solve(a2, b)
+    assert oracle.backward_error(n, A2.rowptr, A2.col, A2.val, xs, b) <= 1e-15 * n
