@@ -220,17 +220,25 @@ int hylu_analyze_batch(int32_t k, const int32_t* n, const int64_t* const* rowptr
 int hylu_batch_layout(hylu_handle* h, int32_t* row_base, int64_t* val_base, int32_t* total_n);
 
 /* Capture refactorization of d_vals followed by the substitution of d_b into
- * d_x (nrhs columns, leading dimension ld; no refinement inside the graph) as
- * a CUDA graph on `stream`, replayed by hylu_graph_launch.  Requires a
- * previous hylu_factor and hylu_solve with at least nrhs right-hand sides (so
- * that nothing is allocated during capture), and a created stream (the legacy
- * default stream cannot be captured: HYLU_ERR_ARG).  The pointers are baked
- * into the graph; the values behind them are read afresh by every replay (the
- * kernels' readiness generations live in device memory and advance on each
- * replay), so new values written into d_vals / d_b between replays are
- * factored and solved. */
+ * d_x (nrhs columns, leading dimension ld) as a CUDA graph on `stream`,
+ * replayed by hylu_graph_launch.  A graph cannot branch on the host, so the
+ * iterative refinement of Sec. 2.3 is recorded as a FIXED number of
+ * `corrections` (0..16) FP64 steps after the solve (residual r = b - A x on
+ * the original A, solve A d = r, x += d), whatever the backward error; one
+ * more residual pass follows, so that hylu_get_info after a replay reports
+ * the backward error of the replay's final x (over the whole system of the
+ * handle: for a batch, the block-diagonal system of all its instances) and
+ * refine_iters = corrections.  Two corrections take a solution whose pivots
+ * were perturbed (relative size ~1.5e-8) to about 1e-16 on well-conditioned
+ * systems.  Requires a previous hylu_factor and hylu_solve with at least
+ * nrhs right-hand sides (so that nothing is allocated during capture), and
+ * a created stream (the legacy default stream cannot be captured:
+ * HYLU_ERR_ARG).  The pointers are baked into the graph; the values behind
+ * them are read afresh by every replay (the kernels' readiness generations
+ * live in device memory and advance on each replay), so new values written
+ * into d_vals / d_b between replays are factored and solved. */
 int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
-                       void* stream);
+                       int corrections, void* stream);
 int hylu_graph_launch(hylu_handle* h, void* stream);
 
 /* Autotune the persistent grid (thread blocks per SM, 1..4) of the factor
@@ -283,7 +291,15 @@ int hylu_destroy(hylu_handle* h);
  * allocations earlier: this call does not allocate them).  d_b is read, d_x
  * written, both DEVICE arrays of n doubles.  No iterative refinement is
  * applied (use hylu_solve when a pivot was perturbed).  Asynchronous on
- * `stream`; nothing is synchronized.
+ * `stream`; nothing is synchronized, so a failure of the factorization on
+ * the device (HYLU_ERR_DEVICE_TIMEOUT) does not show here: read it with
+ * hylu_get_info before trusting the result.
+ *
+ * Errors: HYLU_ERR_STATE when `h` is not factored, or holds FP32 factors
+ * (opt.precision = 1: their solution is only FP32-accurate without the FP64
+ * refinement that hylu_solve applies); HYLU_ERR_ARG for NULL pointers (n > 0)
+ * or when the current device is not the one `h` was factored on.  A factored
+ * empty system (n = 0) returns HYLU_OK without device work.
  *
  * Limits and sharing: n above HYLU_STATIC_SOLVE_MAX_N returns
  * HYLU_ERR_TOO_LARGE before any device work.  The array is shared by every
@@ -292,7 +308,9 @@ int hylu_destroy(hylu_handle* h);
  * work overlaps on the GPU -- on different streams, or on different handles
  * -- race on it and must be ordered by the caller.  The first call on each
  * device looks up the array's device address (cudaGetSymbolAddress, with that
- * device current); make that first call before any stream capture. */
+ * device current); make that first call before any stream capture.  The
+ * address is cached for the process: after a cudaDeviceReset of a device
+ * (which also ends every handle on it) do not call this function again. */
 #define HYLU_STATIC_SOLVE_MAX_N 262144
 int hylu_solve_static(hylu_handle* h, const double* d_b, double* d_x, void* stream);
 

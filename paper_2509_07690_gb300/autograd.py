@@ -3,7 +3,12 @@
 Forward: numeric factorization of A's values and the solve (library
 kernels).  Backward reuses the stored L and U: one transpose solve
 lam = A^{-T} g gives dL/db = lam, and the library's adjoint scatter gives
-dL/dA_ij = -lam_i x_j on A's pattern (no dense gradient is formed)."""
+dL/dA_ij = -lam_i x_j on A's pattern (no dense gradient is formed).
+
+A Solver holds one set of factors.  When the same Solver factored other
+values between this forward and its backward (two differentiable solves
+before one backward), the backward refactors the values its forward used
+before the transpose solve, so every gradient is taken on its own A."""
 from __future__ import annotations
 
 import torch
@@ -20,13 +25,18 @@ class HyluSolve(torch.autograd.Function):
         solver.factor(vals)
         x = solver.solve(b)
         ctx.solver = solver
-        ctx.save_for_backward(x)
+        ctx.factor_gen = solver.factor_gen
+        ctx.save_for_backward(x, vals)
         return x
 
     @staticmethod
     def backward(ctx, gx: torch.Tensor):
-        (x,) = ctx.saved_tensors
+        x, vals = ctx.saved_tensors
         s = ctx.solver
+        if s.factor_gen != ctx.factor_gen:
+            # the handle's factors belong to later values: restore this A's
+            s.factor(vals)
+            ctx.factor_gen = s.factor_gen
         g = gx.contiguous()
         lam = s.solve(g, transpose=True)
         dvals = None

@@ -105,7 +105,8 @@ def load():
     lib.hylu_analyze_batch.argtypes = [C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32,
                                        C.POINTER(Options), C.POINTER(H)]
     lib.hylu_batch_layout.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
-    lib.hylu_graph_capture.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.hylu_graph_capture.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                       C.c_void_p]
     lib.hylu_graph_launch.argtypes = [H, C.c_void_p]
     lib.hylu_tune.argtypes = [H, C.c_void_p, C.POINTER(C.c_int), C.c_void_p]
     lib.hylu_plan_save.argtypes = [H, C.c_void_p, C.POINTER(C.c_int64)]
@@ -278,8 +279,10 @@ def hylu_batch_layout(h: int, ninst: int):
     return rb, vb, tot.value
 
 
-def hylu_graph_capture(h: int, d_vals: int, d_b: int, d_x: int, nrhs: int, ld: int, stream: int = 0) -> int:
-    return _check(load().hylu_graph_capture(h, d_vals, d_b, d_x, nrhs, ld, stream), "hylu_graph_capture")
+def hylu_graph_capture(h: int, d_vals: int, d_b: int, d_x: int, nrhs: int, ld: int, corrections: int = 0,
+                       stream: int = 0) -> int:
+    return _check(load().hylu_graph_capture(h, d_vals, d_b, d_x, nrhs, ld, corrections, stream),
+                  "hylu_graph_capture")
 
 
 def hylu_graph_launch(h: int, stream: int = 0) -> int:

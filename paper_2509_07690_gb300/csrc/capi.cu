@@ -51,6 +51,9 @@ struct hylu_handle {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;          // kernel launches recorded into the graph
+    int graph_corrections = 0;           // refinement steps recorded after the graph's solve
+    int graph_nrhs = 0;
+    bool graph_norms_pending = false;    // a replay wrote residual norms not yet read
     int grid_max = 0;
     bool timed_factor = false, timed_solve = false;
 };
@@ -344,6 +347,7 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
     h->refine_iters = 0;
     h->backward_error = -1.0;
     h->last = st;
+    h->graph_norms_pending = false;
     if (h->opt.refine < 0 || !(h->nperturb > 0 || h->opt.refine)) return HYLU_OK;
     // iterative refinement in FP64 on the original A (Sec. 2.3)
     double be_prev = INFINITY;
@@ -408,8 +412,22 @@ int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs,
 namespace hylu {
 int32_t handle_n(const hylu_handle* h) { return h->P.n; }
 
+// HYLU_OK when the allocation-free substitution can run on h now, 1 when
+// there is nothing to do (a factored empty system), else an error: not
+// factored, FP32 factors (they need the refinement of hylu_solve to reach
+// the FP64 backward error), or a current device other than the handle's.
+int static_solve_ready(const hylu_handle* h) {
+    if (!h->factored) return HYLU_ERR_STATE;
+    if (h->P.n == 0) return 1;
+    if (!h->uploaded || h->opt.precision != 0) return HYLU_ERR_STATE;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return HYLU_ERR_CUDA;
+    return dev == h->device ? HYLU_OK : HYLU_ERR_ARG;
+}
+
 int solve_into(hylu_handle* h, const double* d_b, double* d_x, double* z, double* xh, cudaStream_t st) {
-    if (!h->factored || !h->uploaded) return HYLU_ERR_STATE;
+    const int ready = static_solve_ready(h);
+    if (ready != HYLU_OK) return ready < 0 ? ready : HYLU_OK;
     h->last = st;
     return launch_solve(h->dp, d_b, d_x, z, xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc, 1, h->P.n,
                         h->opt.spin_limit, h->grid, st);
@@ -547,6 +565,16 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->analyze_ms = P.analyze_ms;
     int rc = HYLU_OK;
     if (h->factored && h->uploaded) rc = read_status(h, h->last);
+    if (rc == HYLU_OK && h->graph_norms_pending) {
+        // the last replay's final residual: its backward error (read_status
+        // above synchronized the stream the graph ran on)
+        const int nr = h->graph_nrhs;
+        if (cudaMemcpy(h->h_norms, h->d_norms, sizeof(double) * (3 * nr + 1), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return HYLU_ERR_CUDA;
+        h->backward_error = max_be(h, nr);
+        h->refine_iters = h->graph_corrections;
+        h->graph_norms_pending = false;
+    }
     info->nperturb = h->nperturb;
     info->refine_iters = h->refine_iters;
     info->backward_error = h->backward_error;
@@ -712,8 +740,9 @@ int hylu_batch_layout(hylu_handle* h, int32_t* row_base, int64_t* val_base, int3
 }
 
 static int graph_capture_impl(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs,
-                              int ld, void* stream) {
+                              int ld, int corrections, void* stream) {
     if (!h || !d_vals || !d_b || !d_x || nrhs < 1 || ld < h->P.n) return HYLU_ERR_ARG;
+    if (corrections < 0 || corrections > 16) return HYLU_ERR_ARG;
     if (!h->factored || nrhs > h->cap_rhs || (size_t)ld * nrhs > h->cap_elems) return HYLU_ERR_STATE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     if (!st) return HYLU_ERR_ARG;   // the legacy default stream cannot be captured
@@ -731,6 +760,16 @@ static int graph_capture_impl(hylu_handle* h, const double* d_vals, const double
     const int64_t l0 = hylu::launches();
     int rc = do_factor(h, d_vals, st);
     if (rc >= 0) rc = do_solve(h, d_b, d_x, nrhs, ld, st);
+    // fixed refinement steps (Sec. 2.3) and the residual of the final x,
+    // whose norms hylu_get_info reads after a replay
+    for (int c = 0; rc >= 0 && c <= corrections; ++c) {
+        rc = hylu::launch_residual(h->P.n, h->d_arp, h->d_aci, h->d_avals, d_x, d_b, h->d_r, h->d_norms, nrhs,
+                                   ld, st);
+        if (rc >= 0 && c < corrections)
+            rc = hylu::launch_solve(h->dp, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
+                                    h->d_dc, nrhs, ld, h->opt.spin_limit, h->grid, st);
+        if (rc >= 0 && c < corrections) rc = hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st);
+    }
     h->graph_launches = hylu::launches() - l0;
     hylu::add_launches(-h->graph_launches);  // recorded, not issued: replays count them
     cudaGraph_t g = nullptr;
@@ -741,13 +780,16 @@ static int graph_capture_impl(hylu_handle* h, const double* d_vals, const double
     if (ce != cudaSuccess || !g) return HYLU_ERR_CUDA;
     h->graph = g;
     if (cudaGraphInstantiate(&h->graph_exec, g, 0) != cudaSuccess) return HYLU_ERR_CUDA;
+    h->graph_corrections = corrections;
+    h->graph_nrhs = nrhs;
+    h->graph_norms_pending = false;
     return HYLU_OK;
 }
 
 int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, double* d_x, int nrhs, int ld,
-                       void* stream) {
+                       int corrections, void* stream) {
     Range range_("hylu_graph_capture");
-    return guarded([&] { return graph_capture_impl(h, d_vals, d_b, d_x, nrhs, ld, stream); });
+    return guarded([&] { return graph_capture_impl(h, d_vals, d_b, d_x, nrhs, ld, corrections, stream); });
 }
 
 int hylu_graph_launch(hylu_handle* h, void* stream) {
@@ -758,7 +800,9 @@ int hylu_graph_launch(hylu_handle* h, void* stream) {
     h->last = st;
     // the captured launches count as the library's own launches
     hylu::add_launches(h->graph_launches);
-    return cudaGraphLaunch(h->graph_exec, st) == cudaSuccess ? HYLU_OK : HYLU_ERR_CUDA;
+    if (cudaGraphLaunch(h->graph_exec, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    h->graph_norms_pending = true;
+    return HYLU_OK;
 }
 
 static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {

@@ -13,6 +13,7 @@ struct hylu_handle;
 
 namespace hylu {
 int32_t handle_n(const hylu_handle* h);
+int static_solve_ready(const hylu_handle* h);
 int solve_into(hylu_handle* h, const double* d_b, double* d_x, double* z, double* xh, cudaStream_t st);
 }  // namespace hylu
 
@@ -26,7 +27,9 @@ constexpr int kMaxDevices = 128;
 static __device__ __align__(256) double g_scratch[2 * kMaxN];
 
 // Device address of g_scratch per device.  In host code the name g_scratch
-// is only a host-side stand-in, so the address is looked up once per device.
+// is only a host-side stand-in, so the address is looked up once per device
+// (with that device current) and cached for the life of the process; a
+// cudaDeviceReset of the device ends every handle on it and this cache too.
 double* g_addr[kMaxDevices] = {};
 std::mutex g_mu;
 
@@ -46,9 +49,15 @@ int scratch_address(double** out) {
 }  // namespace
 
 extern "C" int hylu_solve_static(hylu_handle* h, const double* d_b, double* d_x, void* stream) {
-    if (!h || !d_b || !d_x) return HYLU_ERR_ARG;
+    if (!h) return HYLU_ERR_ARG;
     const int32_t n = hylu::handle_n(h);
     if ((int64_t)n > kMaxN) return HYLU_ERR_TOO_LARGE;
+    // state, precision and current device first: the array is looked up on
+    // the current device, which must be the handle's
+    const int ready = hylu::static_solve_ready(h);
+    if (ready < 0) return ready;
+    if (ready == 1) return HYLU_OK;              // factored empty system
+    if (!d_b || !d_x) return HYLU_ERR_ARG;
     double* base = nullptr;
     const int rc = scratch_address(&base);
     if (rc != HYLU_OK) return rc;

@@ -46,6 +46,7 @@ class Solver:
         self.h = capi.hylu_analyze(self.n, self.rowptr, self.col, vals, user_perm, self.opt)
         self.info = capi.hylu_get_info(self.h)
         self._factored = False
+        self.factor_gen = 0      # factorizations issued on this handle
 
     @classmethod
     def from_csr(cls, A, **opts) -> "Solver":
@@ -101,6 +102,7 @@ class Solver:
         self.rowptr = None
         self.col = None
         self._factored = False
+        self.factor_gen = 0
         return self
 
     # ------------------------------------------------------------ numeric
@@ -110,6 +112,7 @@ class Solver:
         fn = capi.hylu_refactor if self._factored else capi.hylu_factor
         rc = fn(self.h, d_vals.data_ptr(), _stream(stream))
         self._factored = True
+        self.factor_gen += 1
         return rc
 
     def solve(self, d_b, d_x=None, stream=None, transpose=False):
@@ -181,6 +184,7 @@ class BatchSolver(Solver):
         self.nnz = int(self.rowptr[-1])
         self.col = None
         self._factored = False
+        self.factor_gen = 0
 
     @classmethod
     def load(cls, source, **opts):
@@ -194,14 +198,17 @@ class BatchSolver(Solver):
     def tune(self, d_vals, stream=None) -> int:
         _device_f64(d_vals, "d_vals", numel=self.nnz)
         self._factored = True
+        self.factor_gen += 1
         return capi.hylu_tune(self.h, d_vals.data_ptr(), _stream(stream))
 
-    def graph_capture(self, d_vals, d_b, d_x, stream=None):
+    def graph_capture(self, d_vals, d_b, d_x, corrections: int = 0, stream=None):
+        """Record refactor + solve (+ `corrections` fixed FP64 refinement
+        steps, then the residual norms get_info reports) as a CUDA graph."""
         _device_f64(d_vals, "d_vals", numel=self.nnz)
         _device_f64(d_b, "d_b", multiple_of=self.n)
         _device_f64(d_x, "d_x", numel=d_b.numel())
         capi.hylu_graph_capture(self.h, d_vals.data_ptr(), d_b.data_ptr(), d_x.data_ptr(), _nrhs(d_b, self.n),
-                                self.n, _stream(stream))
+                                self.n, int(corrections), _stream(stream))
 
     def graph_launch(self, stream=None):
         capi.hylu_graph_launch(self.h, _stream(stream))

@@ -66,6 +66,35 @@ def _grad_case(A, opts, rng):
     return s, vals.grad.cpu().numpy(), bt.grad.cpu().numpy(), w.cpu().numpy(), b[0], x.detach().cpu().numpy()
 
 
+def test_two_solves_on_one_solver_before_backward():
+    """Two differentiable solves with different values on one Solver, then
+    one backward: each gradient must be the dense-formula gradient of its
+    own A, although the handle holds the second A's factors at backward."""
+    torch = _torch()
+    from paper_2509_07690_gb300 import Solver, solve
+    A = synth.aniso9(10, seed=5)
+    rng = np.random.default_rng(8)
+    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=1)
+    v1 = A.val.copy()
+    v2 = A.val * rng.uniform(0.5, 1.5, A.nnz)
+    b = rng.standard_normal(A.n)
+    w1, w2 = rng.standard_normal(A.n), rng.standard_normal(A.n)
+    t1 = torch.from_numpy(v1).cuda().requires_grad_(True)
+    t2 = torch.from_numpy(v2).cuda().requires_grad_(True)
+    bt = torch.from_numpy(b).cuda()
+    x1 = solve(t1, bt, s)
+    x2 = solve(t2, bt, s)
+    loss = (torch.from_numpy(w1).cuda() * x1).sum() + (torch.from_numpy(w2).cuda() * x2).sum()
+    loss.backward()
+    rid = np.repeat(np.arange(A.n), np.diff(A.rowptr))
+    for vals, w, t in ((v1, w1, t1), (v2, w2, t2)):
+        a = synth.CSR(A.n, A.rowptr, A.col, vals).todense()
+        lam = np.linalg.solve(a.T, w)
+        xd = np.linalg.solve(a, b)
+        np.testing.assert_allclose(t.grad.cpu().numpy(), -lam[rid] * xd[A.col], rtol=1e-9, atol=1e-12)
+    s.close()
+
+
 @pytest.mark.parametrize("n_grid", [6, 12])
 def test_gradient_matches_dense_formula(n_grid):
     rng = np.random.default_rng(n_grid)
