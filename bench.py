@@ -1,17 +1,21 @@
-"""Benchmark of the GB300 HYLU numeric phase (numeric LU ms per factorization,
-GFLOP/s from the symbolic flop count, fraction of the FP64 roofline) on the
-circuit-like workload: n = 100,000, 1% hubs, AMD ordering, refactorization of
-16 fresh value sets on one pattern, each followed by a solve that must reach
-backward error <= 1e-12.
+"""Benchmark of the GB300 HYLU numeric phase: numeric LU ms per factorization,
+GFLOP/s from the symbolic flop count and the fraction of the roofline, with
+every solve held to backward error <= 1e-12.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl hylu|reference]
+                    [--workload convdiff3d_64|circuit_100k|aniso9_512|grid5_64|circuit_batch_512]
 
+Default workload: the 3D 7-point upwind convection-diffusion operator on a 64^3
+grid (n = 262,144, nested dissection), the largest single-GPU configuration.
 One step = refactor (value scatter + numeric factorization) + forward/backward
-substitution (+ refinement if a pivot was perturbed), inputs resident in HBM.
-Under torchrun every rank factors its own replica (the path does not shard);
-rank 0 prints one JSON line.  `--impl reference` times the CPU oracle on a
-bounded sample (a smaller instance of the same generator, extrapolated by the
-symbolic flop count) instead.
+substitution (+ refinement where taken), inputs resident in HBM.  On that
+workload the line also carries the precision form (FP32 factors, FP64
+refinement to the same 1e-12) measured on the same matrix.  Under torchrun
+every rank factors its own replica (the path does not shard; the batching
+workload splits its systems across ranks); rank 0 prints one JSON line.
+`--impl reference` times the CPU oracle on a bounded sample instead: a
+smaller instance of the same generator under the same ordering, extrapolated
+by the symbolic flop count.
 """
 from __future__ import annotations
 
@@ -30,14 +34,21 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "circuit_100k"
+WORKLOAD = "convdiff3d_64"
+CIRCUIT_N = 30000          # size of the 'circuit' profiling workload (--n)
 VALUE_SETS = 16
-METRIC = "numeric LU ms/factor (circuit-like n=100000, refactor of 16 value sets, backward error <= 1e-12)"
+METRICS = {
+    "circuit_100k": "numeric LU ms/factor (circuit-like n=100000, refactor of 16 value sets, "
+                    "backward error <= 1e-12)",
+    "convdiff3d_64": "numeric LU ms/factor (3D 7-point upwind convection-diffusion 64^3, n=262144, "
+                     "nested dissection, backward error <= 1e-12)",
+}
+METRIC = METRICS["convdiff3d_64"]
 
 
 def metric_name() -> str:
-    if WORKLOAD == "circuit_100k":
-        return METRIC
+    if WORKLOAD in METRICS:
+        return METRICS[WORKLOAD]
     return f"numeric LU ms/factor ({WORKLOAD}, backward error <= 1e-12)"
 
 
@@ -49,13 +60,15 @@ def parse():
     ap.add_argument("--impl", default="hylu", choices=["hylu", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-ordering-trial", action="store_true",
-                    help="circuit workload: skip the untimed AMD / nested dissection trial")
-    ap.add_argument("--workload", default="circuit_100k",
+    ap.add_argument("--ordering-trial", action="store_true",
+                    help="circuit workload: untimed AMD / nested dissection trial first, the faster one timed")
+    ap.add_argument("--no-precision-form", action="store_true",
+                    help="convdiff3d_64: skip the second measurement (the precision form)")
+    ap.add_argument("--workload", default="convdiff3d_64",
                     choices=["circuit_100k", "circuit", "grid5_64", "aniso9_512", "convdiff3d_64",
                              "circuit_batch_512"],
-                    help="circuit_100k is the headline configuration; 'circuit' with --n is the same "
-                         "generator at another size (profiling cases)")
+                    help="convdiff3d_64 is the largest single-GPU configuration (default); 'circuit' "
+                         "with --n is the circuit generator at another size (profiling cases)")
     ap.add_argument("--n", type=int, default=30000, help="size for --workload circuit")
     ap.add_argument("--scale", type=float, default=1.0,
                     help="grid workloads: grid side x scale (profiling cases; 1 is the configuration)")
@@ -64,8 +77,9 @@ def parse():
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="fp32: the precision form (FP32 factors, FP64 refinement on every solve)")
     args = ap.parse_args()
-    global WORKLOAD
+    global WORKLOAD, CIRCUIT_N
     WORKLOAD = args.workload
+    CIRCUIT_N = args.n
     return args
 
 
@@ -131,12 +145,12 @@ def make_inputs(n_circuit: int = 30000, scale: float = 1.0):
 
 
 def ordering_for(workload: str) -> int:
-    """Nested dissection (1) for the PDE workloads and the circuit matrix, AMD
-    (0) for the 5-point grid.  On the circuit matrix nested dissection (hub
-    rows last) needs 11% fewer flops than AMD and its dependency graph is
-    6.4x shallower (1,347 against 8,676 factor levels), and the factor kernel
-    is bound by that chain."""
-    return 1 if workload in ("aniso9_512", "convdiff3d_64", "circuit_100k", "circuit") else 0
+    """Nested dissection (1) for the PDE workloads, AMD (0) for the 5-point
+    grid and the circuit matrices.  On the circuit matrix nested dissection
+    (hub rows last) has 11% fewer flops and a 6.4x shallower dependency graph,
+    but measured on the GB300 its factorization is slower (260 against 212
+    ms): the hub rows, not the chain, bound it."""
+    return 1 if workload in ("aniso9_512", "convdiff3d_64") else 0
 
 
 def backward_error(A, vals, x, b) -> float:
@@ -165,20 +179,30 @@ def kernel_mix(info) -> dict:
     return {k: round(v / total, 4) for k, v in parts}
 
 
-def sample_instance(n_s: int):
-    """A smaller instance of the same circuit-like generator (same seed rule)."""
+# oracle sample sizes: a fraction of the workload's size parameter (circuit
+# rows, grid side), its starting value, and the exponent with which the
+# oracle's time grows in it (flops of the ordering: circuits ~ n^3 here,
+# 3D nested dissection n^2 = k^6, 2D nested dissection n^1.5 = k^3)
+SAMPLE_GROWTH = {"circuit_100k": (0.1, 3.0), "circuit": (0.1, 3.0), "convdiff3d_64": (0.25, 6.0),
+                 "aniso9_512": (0.1, 3.0), "grid5_64": (1.0, 3.0)}
+
+
+def sample_instance(frac: float):
+    """A smaller instance of the workload's own generator (same seed rule):
+    frac x the circuit size or the grid side."""
     from paper_2509_07690_gb300 import synth
-    idx = synth.WORKLOADS[WORKLOAD]["index"]
-    return synth.circuit(n_s, seed=1000 + idx)
+    if WORKLOAD == "circuit":
+        return synth.circuit(max(50, int(round(CIRCUIT_N * frac))), seed=1001)
+    return synth.workload(WORKLOAD, frac)
 
 
-def oracle_once(n_s: int, ordering: int | None = None):
+def oracle_once(frac: float, ordering: int | None = None):
     """Preprocess a sample instance with the library's host analysis (the
     oracle takes the same matching, scaling and ordering as every parity
     test), then time the oracle's factorization of it on one host core."""
     import oracle
     from paper_2509_07690_gb300 import Solver
-    A = sample_instance(n_s)
+    A = sample_instance(frac)
     s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering_for(WORKLOAD) if ordering is None else ordering)
     rp, cp, dr, dc, _ = s.export_perm()
     s.close()
@@ -187,18 +211,18 @@ def oracle_once(n_s: int, ordering: int | None = None):
     dt = time.perf_counter() - t0
     fl = o.flops[0]
     del o
-    return dt, fl
+    return dt, fl, A.n
 
 
-def oracle_size(budget_s: float, ordering: int | None = None) -> int:
-    """Largest sample size n_s (grown by 1.5x from 10,000) whose oracle run is
-    predicted to fit the budget (time grows about like n_s^3 here)."""
-    n_s = 10_000
-    dt, _ = oracle_once(n_s, ordering)
-    while n_s < 100_000 and dt * 1.5 ** 3 < budget_s:
-        n_s = min(100_000, int(n_s * 1.5))
-        dt, _ = oracle_once(n_s, ordering)
-    return n_s
+def oracle_size(budget_s: float, ordering: int | None = None) -> float:
+    """Largest sample fraction (grown by 1.2x from the workload's start,
+    at most 1) whose oracle run is predicted to fit the budget."""
+    frac, expo = SAMPLE_GROWTH.get(WORKLOAD, (0.1, 3.0))
+    dt, _, _ = oracle_once(frac, ordering)
+    while frac < 1.0 and dt * 1.2 ** expo < budget_s:
+        frac = min(1.0, frac * 1.2)
+        dt, _, _ = oracle_once(frac, ordering)
+    return frac
 
 
 # ----------------------------------------------------------------- clocks
@@ -305,15 +329,40 @@ BATCH_RHS = 8
 BATCH_SAMPLE_EVERY = 16
 
 
-def batch_inputs(count: int = 512):
+def partition_systems(weights, ws: int) -> list[list[int]]:
+    """Split independent systems over ws ranks with no exchange between them
+    (the batching form shards by system): largest weight first, each to the
+    least-loaded rank (ties to the lower rank), every rank's list ascending.
+    The same on every rank (deterministic), so no rank needs to ask another.
+    A rank's load is at most the mean load plus the largest single weight."""
+    order = sorted(range(len(weights)), key=lambda q: (-weights[q], q))
+    load = [0.0] * ws
+    parts = [[] for _ in range(ws)]
+    for q in order:
+        r = min(range(ws), key=lambda j: (load[j], j))
+        parts[r].append(q)
+        load[r] += weights[q]
+    return [sorted(p) for p in parts]
+
+
+def batch_weight(n: int) -> float:
+    """Work proxy of one circuit-like system of n rows for the split across
+    ranks: its flops grow about like n^2 on this generator (AMD), known
+    before any analysis."""
+    return float(n) ** 2
+
+
+def batch_inputs(count: int = 512, only=None):
     """512 circuit-like systems (n ~ U[2000, 40000]) of the circuit generator,
-    4 value sets each (the matrix's own values, then fresh sets), 8 RHS."""
+    4 value sets each (the matrix's own values, then fresh sets), 8 RHS.
+    only: the indices of the systems to generate (this rank's share)."""
     from paper_2509_07690_gb300 import synth
     idx = synth.WORKLOADS["circuit_batch_512"]["index"]
     sizes = synth.circuit_batch_sizes()[:count]
-    mats = [synth.circuit(int(n), seed=1000 * (idx + 1) + q) for q, n in enumerate(sizes)]
+    keep = range(len(sizes)) if only is None else only
+    mats = [synth.circuit(int(sizes[q]), seed=1000 * (idx + 1) + q) for q in keep]
     sets = [[m.val if v == 0 else synth.circuit_values(m.rowptr, m.col, 7919 * (v + 1) + q)
-             for q, m in enumerate(mats)] for v in range(BATCH_SETS)]
+             for q, m in zip(keep, mats)] for v in range(BATCH_SETS)]
     return mats, sets
 
 
@@ -327,7 +376,10 @@ def run_batch(args, ws, rank, local):
     pbuild.build()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    mats, sets = batch_inputs(args.batch_systems)
+    from paper_2509_07690_gb300 import synth
+    sizes = synth.circuit_batch_sizes()[:args.batch_systems]
+    share = partition_systems([batch_weight(int(n)) for n in sizes], ws)[rank]
+    mats, sets = batch_inputs(args.batch_systems, only=share)
     k = len(mats)
     t0 = time.time()
     bs = BatchSolver([(m.n, m.rowptr, m.col, m.val) for m in mats], BATCH_SETS)
@@ -344,8 +396,13 @@ def run_batch(args, ws, rank, local):
     best = bs.tune(vals)
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream())
+    # the graph cannot test the backward error on the host: where the
+    # untimed factorization perturbed a pivot, two fixed FP64 refinement
+    # steps are recorded after the solve; every replay's final residual is
+    # read back below
+    corrections = 2 if bs.get_info().nperturb > 0 else 0
     with torch.cuda.stream(side):
-        bs.graph_capture(vals, db, dx, stream=side)
+        bs.graph_capture(vals, db, dx, corrections=corrections, stream=side)
         for _ in range(args.warmup):
             bs.graph_launch(stream=side)
         side.synchronize()
@@ -362,8 +419,10 @@ def run_batch(args, ws, rank, local):
         launches = capi.hylu_launch_count() - l0
         clk = clocks.stop() if clocks else None
     t_batch = allmax(ws, e0.elapsed_time(e1)) / args.steps
+    inst_all = int(round(allsum(ws, float(inst))))
     x = dx.cpu().numpy()
-    nperturb = bs.get_info().nperturb
+    ginfo = bs.get_info()
+    nperturb = ginfo.nperturb
     be = res1 = 0.0
     for q in range(0, inst, 64):              # every 64th instance, every RHS
         v, sidx = divmod(q, k)
@@ -393,26 +452,29 @@ def run_batch(args, ws, rank, local):
         plain_ms.append(a0.elapsed_time(a1))
         s.close()
     t_plain = statistics.mean(plain_ms) * inst
-    bs_flops = info.flops
+    bs_flops = allsum(ws, info.flops)
+    be = allmax(ws, max(be, ginfo.backward_error))
+    nsys = args.batch_systems
     if rank == 0:
         out = {
-            "metric": f"factorizations/s (batching form: {k} circuit-like systems n~U[2000,40000] x 4 value sets "
-                      "x 8 RHS, one persistent launch per kernel in a CUDA graph)",
-            "value": inst / (t_batch * 1e-3), "unit": "factorizations/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "circuit_batch_512" if k == 512 else f"circuit_batch_{k}", "systems": k, "value_sets": BATCH_SETS,
-                       "instances": inst, "nrhs": BATCH_RHS, "rows": bs.n, "flops": bs_flops,
-                       "nnz_store": info.nnz_store, "tuned_blocks_per_sm": best, "analyze_s": analyze_s,
-                       "flops_by_kernel": kernel_mix(info),
+            "metric": f"factorizations/s (batching form: {nsys} circuit-like systems n~U[2000,40000] x 4 value "
+                      "sets x 8 RHS, one persistent launch per kernel in a CUDA graph)",
+            "value": inst_all / (t_batch * 1e-3), "unit": "factorizations/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_batch, "higher_is_better": True,
+            "scaling": "weak" if ws == 1 else "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "circuit_batch_512" if nsys == 512 else f"circuit_batch_{nsys}",
+                       "systems": nsys, "systems_rank0": k, "value_sets": BATCH_SETS,
+                       "instances": inst_all, "nrhs": BATCH_RHS, "rows_rank0": bs.n, "flops": bs_flops,
+                       "nnz_store_rank0": info.nnz_store, "tuned_blocks_per_sm": best, "analyze_s": analyze_s,
+                       "flops_by_kernel": kernel_mix(info), "graph_refinement_steps": corrections,
                        "l2": "factor storage far above the 126 MB L2, no flush",
-                       "parallelism": f"replicas x{ws}"},
+                       "parallelism": f"systems split over {ws} ranks (no exchange)" if ws > 1 else "1 GPU"},
             "gflops": bs_flops / (t_batch * 1e-3) / 1e9,
             "backward_error": be, "residual_1": res1, "nperturb": nperturb,
             "plain_launches": {"factorizations_per_s": inst / (t_plain * 1e-3), "ms_per_instance":
                                statistics.mean(plain_ms), "sample": f"every {BATCH_SAMPLE_EVERY}th system "
                                f"({len(plain_ms)} systems, value set 1), refactor + 8-RHS solve, extrapolated "
-                               f"to {inst} instances"},
+                               f"to rank 0's {inst} instances"},
             "speedup_vs_plain_launches": t_plain / t_batch,
             "cpu_baseline": None,
             "gpu_launches": int(launches),
@@ -425,27 +487,38 @@ def run_batch(args, ws, rank, local):
 
 # ----------------------------------------------------------------- arms
 def run_reference(args, ws, rank):
+    """The CPU oracle on the machine's host cores: each step times one oracle
+    factorization of a smaller instance of the same generator under the
+    ordering the GPU arm times, extrapolated by the symbolic flop count."""
     if rank != 0:
         return 0
     from paper_2509_07690_gb300 import Solver
-    A, sets, b = make_inputs()
-    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering_for(WORKLOAD))
+    if WORKLOAD == "circuit_batch_512":
+        print(json.dumps({"impl": "reference", "unavailable": "the batching workload has no oracle arm: "
+                          "its per-instance parity is checked in the tests"}), flush=True)
+        return 0
+    A, sets, b = make_inputs(args.n, args.scale)
+    ordering = ordering_for(WORKLOAD)
+    s = Solver(A.n, A.rowptr, A.col, A.val, ordering=ordering)
     total_flops = s.info.flops
     s.close()
-    n_s = oracle_size(max(2.0, args.cpu_seconds / 4))
-    rates = []
+    frac = oracle_size(max(2.0, args.cpu_seconds / 4), ordering)
+    rates, n_s = [], 0
     for k in range(args.warmup + args.steps):
-        dt, fl = oracle_once(n_s)
+        dt, fl, n_s = oracle_once(frac, ordering)
         if k >= args.warmup:
             rates.append(dt / fl)
     ms_full = statistics.mean(rates) * total_flops * 1e3
-    sample = (f"circuit-like generator at n={n_s} (same seed rule), oracle factorization timed per step, "
-              f"extrapolated to the n={A.n} flop count")
-    out = {"metric": METRIC, "value": ms_full, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+    oname = "ND" if ordering == 1 else "AMD"
+    sample = (f"extrapolation: {WORKLOAD} generator at n={n_s} (same seed rule, {oname} ordering as the GPU arm), "
+              f"oracle factorization timed per step on one core, scaled by the flop count to n={A.n} "
+              f"({total_flops:.3e} flops)")
+    out = {"metric": metric_name(), "value": ms_full, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": ms_full, "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-           "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "flops": total_flops},
-           "cpu_baseline": {"value": ms_full, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample},
+           "config": {"workload": WORKLOAD, "n": A.n, "nnz": A.nnz, "flops": total_flops, "ordering": oname},
+           "cpu_baseline": {"value": ms_full, "unit": "ms", "cores": 1, "kind": "oracle", "sample": sample,
+                            "extrapolated_from_n": n_s},
            "e2e": {"value": ms_full, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -517,26 +590,45 @@ def run_hylu(args, ws, rank, local):
     import gc
     from paper_2509_07690_gb300 import capi
     ordering = ordering_for(WORKLOAD)
-    if ordering == 0 or not WORKLOAD.startswith("circuit"):
-        return measure_hylu(args, ws, rank, local, ordering)
+    if not (WORKLOAD.startswith("circuit") and args.ordering_trial):
+        out = measure_hylu(args, ws, rank, local, ordering)
+        if WORKLOAD == "convdiff3d_64" and args.precision == "fp64" and not args.no_precision_form:
+            gc.collect()
+            out32 = measure_hylu(args, ws, rank, local, ordering, fp32=True, sub=True)
+            if out is not None and out32 is not None:
+                out["precision_form"] = precision_summary(out, out32)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return 0
     trial = None
-    if ws == 1 and not args.no_ordering_trial:
+    if ws == 1:
         trial = ordering_trial(args, local)
         ordering = choose_ordering(trial)
         if ordering == 0:
-            return measure_hylu(args, ws, rank, local, 0, trial=trial)
+            out = measure_hylu(args, ws, rank, local, 0, trial=trial)
+            if out is not None:
+                print(json.dumps(out), flush=True)
+            return 0
     try:
-        return measure_hylu(args, ws, rank, local, 1, strict=True, trial=trial)
+        out = measure_hylu(args, ws, rank, local, 1, strict=True, trial=trial)
     except (capi.HyluError, Rejected) as e:
         reason = f"{type(e).__name__}: {e}"
-    for c in list(_ACTIVE_CLOCKS):
-        c.stop()
-    gc.collect()                              # releases the failed run's solver
-    sys.stderr.write(f"bench: nested dissection run failed ({reason}); timing AMD instead\n")
-    return measure_hylu(args, ws, rank, local, 0, fallback_from={"ordering": "ND", "reason": reason}, trial=trial)
+        for c in list(_ACTIVE_CLOCKS):
+            c.stop()
+        gc.collect()                              # releases the failed run's solver
+        sys.stderr.write(f"bench: nested dissection run failed ({reason}); timing AMD instead\n")
+        out = measure_hylu(args, ws, rank, local, 0, fallback_from={"ordering": "ND", "reason": reason},
+                           trial=trial)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+    return 0
 
 
-def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fallback_from=None, trial=None):
+def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fallback_from=None, trial=None,
+                 fp32: bool | None = None, sub: bool = False):
+    """One measured form on the workload; returns the JSON object (rank 0)
+    or None.  sub: a second form reported inside the main line (no CPU
+    baseline)."""
     import torch
     from paper_2509_07690_gb300 import Solver, build as pbuild, capi
     pbuild.build()
@@ -544,7 +636,8 @@ def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fal
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream()
     A, sets, b = make_inputs(args.n, args.scale)
-    fp32 = args.precision == "fp32"
+    if fp32 is None:
+        fp32 = args.precision == "fp32"
     s = Solver(A.n, A.rowptr, A.col, A.val, timing=1, ordering=ordering, precision=1 if fp32 else 0)
     info = s.info
     flops = info.flops
@@ -632,12 +725,14 @@ def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fal
         raise Rejected(f"backward error {max(be, be_e2e):.2e} above 1e-12")
     # ---------------- CPU oracle baseline (rank 0, N = 1 only)
     cpu = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline and WORKLOAD == "circuit_100k":
-        n_s = oracle_size(args.cpu_seconds / 2, ordering)
-        dt, fl = oracle_once(n_s, ordering)
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline and not sub:
+        frac = oracle_size(args.cpu_seconds / 2, ordering)
+        dt, fl, n_s = oracle_once(frac, ordering)
         cpu = {"value": dt * 1e3 * flops / fl, "unit": "ms", "cores": 1, "kind": "oracle",
-               "sample": f"circuit-like generator at n={n_s} ({fl:.3e} flops, {dt:.1f} s on one core), "
-                         f"extrapolated to the n={A.n} flop count; host has {os.cpu_count()} cores"}
+               "sample": f"extrapolation: {WORKLOAD} generator at n={n_s} ({fl:.3e} flops, {dt:.1f} s on one "
+                         f"core, same ordering), scaled by the flop count to n={A.n}; host has "
+                         f"{os.cpu_count()} cores",
+               "extrapolated_from_n": n_s}
     if rank == 0:
         out = {
             "metric": metric_name(), "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
@@ -692,9 +787,23 @@ def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fal
             out["fallback_from"] = fallback_from
         if trial:
             out["ordering_trial"] = {"refactorizations": TRIAL_REFACTORS, **trial}
-        print(json.dumps(out), flush=True)
+        s.close()
+        return out
     s.close()
-    return 0
+    return None
+
+
+def precision_summary(fp64: dict, fp32: dict) -> dict:
+    """The precision form measured on the same matrix, against the FP64 line:
+    factor and step times (the FP32 step includes its FP64 refinement), the
+    backward error both reach, and the factor kernel's roofline."""
+    return {"precision": fp32["config"]["precision"], "factor_ms": fp32["value"],
+            "ms_per_step": fp32["ms_per_step"], "gflops": fp32["gflops"], "solve_ms": fp32["solve_ms"],
+            "refine_iters": fp32["refine_iters"], "backward_error": fp32["backward_error"],
+            "e2e_ms": fp32["e2e"]["value"], "roofline": fp32["roofline"],
+            "speedup_factor_vs_fp64": fp64["value"] / fp32["value"],
+            "speedup_step_vs_fp64": fp64["ms_per_step"] / fp32["ms_per_step"],
+            "gpu_launches": fp32["gpu_launches"], "clocks": fp32["clocks"]}
 
 
 def main():
