@@ -363,6 +363,19 @@ int64_t hylu_launch_count(void);
  * `stream` and synchronizes it; *gflops receives FLOP/s / 1e9 (2 per FMA). */
 int hylu_measure_fp64_peak(double* gflops, void* stream);
 
+/* The tensor-core tile engine of the precision form's sup-sup update (Sec.
+ * 2.2, Fig. 1c), applied to plain dense matrices so that it can be checked on
+ * its own: C -= A B with A (m x k, row stride lda), B (k x n, ldb) and C
+ * (m x n, ldc) FP32 row-major DEVICE arrays.  Each operand is split into
+ * nsplit (2 or 3) BF16 terms and the products run as tcgen05 MMAs with FP32
+ * accumulation in tensor memory (3 term products for nsplit 2, about 2^-16
+ * relative accuracy; 6 for nsplit 3, about FP32 accuracy).  Allocates its
+ * split copies of A, synchronizes `stream` and frees them; returns
+ * HYLU_ERR_ARG for bad sizes, HYLU_ERR_CUDA when the driver offers no TMA
+ * tensor-map encoder, HYLU_ERR_DEVICE_TIMEOUT when a bounded wait expired. */
+int hylu_split_gemm(const float* d_a, const float* d_b, float* d_c, int m, int n, int k, int lda, int ldb,
+                    int ldc, int nsplit, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -99,6 +99,8 @@ def load():
     lib.hylu_launch_count.restype = C.c_int64
     lib.hylu_launch_count.argtypes = []
     lib.hylu_measure_fp64_peak.argtypes = [C.POINTER(C.c_double), C.c_void_p]
+    lib.hylu_split_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
+                                    C.c_int, C.c_int, C.c_int, C.c_void_p]
     lib.hylu_solve_static.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
     lib.hylu_debug_trace.argtypes = [H, C.c_void_p]
     lib.hylu_grad_values.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
@@ -232,6 +234,14 @@ def hylu_measure_fp64_peak(stream: int = 0) -> float:
     g = C.c_double()
     _check(load().hylu_measure_fp64_peak(C.byref(g), stream), "hylu_measure_fp64_peak")
     return g.value
+
+
+def hylu_split_gemm(d_a: int, d_b: int, d_c: int, m: int, n: int, k: int, lda: int, ldb: int, ldc: int,
+                    nsplit: int = 3, stream: int = 0) -> int:
+    """C -= A B on the tensor-core tile engine (FP32 arrays split into BF16
+    terms; see include/hylu.h)."""
+    return _check(load().hylu_split_gemm(d_a, d_b, d_c, m, n, k, lda, ldb, ldc, nsplit, stream),
+                  "hylu_split_gemm")
 
 
 def hylu_solve_static(h: int, d_b: int, d_x: int, stream: int = 0) -> int:

@@ -121,6 +121,7 @@ int warps_per_block();
 int dense_l_min();
 int64_t launches();
 int measure_fp64_peak(double* gflops, cudaStream_t st);
+bool tensor_maps_available();  // the driver's TMA tensor-map encoder was found
 void count_launch();
 void add_launches(int64_t k);
 
