@@ -84,6 +84,10 @@ typedef struct {
     double heavy_ratio;    /* rows whose update work is at least heavy_ratio x the mean row (and
                               at least 1e6 flops) are claimed first, from a queue of their own,
                               by two warps of every block; 0 disables (32) */
+    int gemm_min_rows;     /* precision form (precision = 1): supernodes of at least this many rows,
+                              and every node downstream of one, take the updates of their diagonal
+                              block and U tail as split-BF16 tensor-core GEMM tiles (Sec. 2.2,
+                              Fig. 1c, sup-sup); 0 disables (64).  Ignored for FP64 factors. */
 } hylu_options;
 
 typedef struct {
@@ -260,6 +264,17 @@ int hylu_export_perm(hylu_handle* h, int32_t* rowperm, int32_t* colperm, double*
  * n + t is tail task t), heavy int32[info.nheavy] (the heavy-row queue),
  * task_node int32[info.ntasks - n] (the supernode each tail task solves). */
 int hylu_export_schedule(hylu_handle* h, int32_t* order, int32_t* heavy, int32_t* task_node);
+
+/* Diagnostics: the tables of the tensor-core sup-sup update that a
+ * precision-form factorization of `h` would use with gemm_min_rows =
+ * min_rows (see GemmPlan in the sources), as one flat int64 HOST array:
+ * a header of 10 counts (destinations, union L columns, (destination, N
+ * tile) pairs, triples, chunks, GEMM tasks, diag tasks, claim-order length,
+ * levels, L slots) followed by the arrays in a fixed order.  buf == NULL:
+ * *len receives the length; otherwise *len is the capacity on entry.  Host
+ * only.  HYLU_ERR_INTERNAL when the pattern is not closed under the
+ * supernode tails (never for a plan of this library). */
+int hylu_export_gemm_plan(hylu_handle* h, int min_rows, int64_t* buf, int64_t* len);
 
 /* Padded storage pattern in CSR form (HOST arrays, any may be NULL):
  * rowptr int64[n+1], col int32[info.nnz_store]; columns sorted per row. */

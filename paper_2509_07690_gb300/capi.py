@@ -46,7 +46,7 @@ class Options(C.Structure):
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine", C.c_int),
                 ("spin_limit", C.c_longlong), ("rows_per_task", C.c_int), ("debug", C.c_int),
                 ("amd_dense", C.c_double), ("timing", C.c_int), ("precision", C.c_int),
-                ("heavy_ratio", C.c_double)]
+                ("heavy_ratio", C.c_double), ("gemm_min_rows", C.c_int)]
 
 
 class Info(C.Structure):
@@ -99,6 +99,7 @@ def load():
     lib.hylu_launch_count.restype = C.c_int64
     lib.hylu_launch_count.argtypes = []
     lib.hylu_measure_fp64_peak.argtypes = [C.POINTER(C.c_double), C.c_void_p]
+    lib.hylu_export_gemm_plan.argtypes = [H, C.c_int, C.c_void_p, C.POINTER(C.c_int64)]
     lib.hylu_split_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                     C.c_int, C.c_int, C.c_int, C.c_void_p]
     lib.hylu_solve_static.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -234,6 +235,37 @@ def hylu_measure_fp64_peak(stream: int = 0) -> float:
     g = C.c_double()
     _check(load().hylu_measure_fp64_peak(C.byref(g), stream), "hylu_measure_fp64_peak")
     return g.value
+
+
+GEMM_PLAN_ARRAYS = (
+    ("gd_node", "ngd"), ("gd_K", "ngd"), ("gd_Kp", "ngd"), ("gd_Mp", "ngd"), ("gd_ntiles", "ngd"),
+    ("gd_a_off", "ngd"), ("gd_lc_off", "ngd+1"), ("lc_cols", "nlc"), ("gd_tile_base", "ngd+1"),
+    ("pr_tri_off", "npairs+1"), ("tri_u0", "ntri"), ("tri_len", "ntri"), ("tri_node", "ntri"),
+    ("tri_jlo", "ntri"), ("tri_jhi", "ntri"), ("pr_ck_off", "npairs+1"), ("ck_kc", "nck"), ("ck_t0", "nck"),
+    ("ck_t1", "nck"), ("task_gd", "ntask"), ("task_mt", "ntask"), ("task_nt", "ntask"),
+    ("task_level", "ntask"), ("lu_pos", "nl"), ("row_order", "norder"), ("diag_row", "ndiag"),
+    ("walk_level", "n"), ("diag_level", "n"))
+
+
+def hylu_export_gemm_plan(h: int, min_rows: int, n: int) -> dict:
+    """The tensor-core sup-sup tables for gemm_min_rows = min_rows, as a dict
+    of int64 arrays (empty arrays when no node qualifies)."""
+    lib = load()
+    ln = C.c_int64(0)
+    _check(lib.hylu_export_gemm_plan(h, int(min_rows), None, C.byref(ln)), "hylu_export_gemm_plan")
+    buf = np.zeros(ln.value, np.int64)
+    _check(lib.hylu_export_gemm_plan(h, int(min_rows), buf.ctypes.data, C.byref(ln)), "hylu_export_gemm_plan")
+    names = ("ngd", "nlc", "npairs", "ntri", "nck", "ntask", "ndiag", "norder", "levels", "nl")
+    cnt = dict(zip(names, (int(v) for v in buf[:10])))
+    cnt["n"] = int(n)
+    out = dict(cnt)
+    pos = 10
+    for name, size in GEMM_PLAN_ARRAYS:
+        key, _, plus = size.partition("+")
+        m = cnt[key] + (int(plus) if plus else 0) if cnt["ngd"] else 0
+        out[name] = buf[pos:pos + m]
+        pos += m
+    return out
 
 
 def hylu_split_gemm(d_a: int, d_b: int, d_c: int, m: int, n: int, k: int, lda: int, ldb: int, ldc: int,
