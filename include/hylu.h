@@ -268,9 +268,10 @@ int hylu_export_schedule(hylu_handle* h, int32_t* order, int32_t* heavy, int32_t
 /* Diagnostics: the tables of the tensor-core sup-sup update that a
  * precision-form factorization of `h` would use with gemm_min_rows =
  * min_rows (see GemmPlan in the sources), as one flat int64 HOST array:
- * a header of 10 counts (destinations, union L columns, (destination, N
- * tile) pairs, triples, chunks, GEMM tasks, diag tasks, claim-order length,
- * levels, L slots) followed by the arrays in a fixed order.  buf == NULL:
+ * a header of 10 numbers (destinations, (destination, source) pairs, tail
+ * map entries, GEMM tasks, diag tasks, claim-order length, levels, L slots,
+ * smallest source supernode of a pair, A elements per split term) followed by
+ * the arrays in a fixed order.  buf == NULL:
  * *len receives the length; otherwise *len is the capacity on entry.  Host
  * only.  HYLU_ERR_INTERNAL when the pattern is not closed under the
  * supernode tails (never for a plan of this library). */

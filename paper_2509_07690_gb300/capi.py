@@ -238,13 +238,12 @@ def hylu_measure_fp64_peak(stream: int = 0) -> float:
 
 
 GEMM_PLAN_ARRAYS = (
-    ("gd_node", "ngd"), ("gd_K", "ngd"), ("gd_Kp", "ngd"), ("gd_Mp", "ngd"), ("gd_ntiles", "ngd"),
-    ("gd_a_off", "ngd"), ("gd_lc_off", "ngd+1"), ("lc_cols", "nlc"), ("gd_tile_base", "ngd+1"),
-    ("pr_tri_off", "npairs+1"), ("tri_u0", "ntri"), ("tri_len", "ntri"), ("tri_node", "ntri"),
-    ("tri_jlo", "ntri"), ("tri_jhi", "ntri"), ("pr_ck_off", "npairs+1"), ("ck_kc", "nck"), ("ck_t0", "nck"),
-    ("ck_t1", "nck"), ("task_gd", "ntask"), ("task_mt", "ntask"), ("task_nt", "ntask"),
-    ("task_level", "ntask"), ("lu_pos", "nl"), ("row_order", "norder"), ("diag_row", "ndiag"),
-    ("walk_level", "n"), ("diag_level", "n"))
+    ("gd_node", "ngd"), ("gd_Kp", "ngd"), ("gd_Mp", "ngd"), ("gd_a_off", "ngd"), ("gd_ntask", "ngd"),
+    ("pair_gd", "npair"), ("pair_src", "npair"), ("pair_u0", "npair"), ("pair_len", "npair"),
+    ("pair_jr", "npair"), ("pair_nj", "npair"), ("pair_need", "npair"), ("pair_x_off", "npair"),
+    ("xmap", "nxmap"), ("gd_slot", "nl"), ("task_pair", "ntask"), ("task_mt", "ntask"), ("task_jt", "ntask"),
+    ("task_level", "ntask"), ("row_order", "norder"), ("diag_row", "ndiag"), ("walk_level", "n"),
+    ("diag_level", "n"))
 
 
 def hylu_export_gemm_plan(h: int, min_rows: int, n: int) -> dict:
@@ -255,14 +254,13 @@ def hylu_export_gemm_plan(h: int, min_rows: int, n: int) -> dict:
     _check(lib.hylu_export_gemm_plan(h, int(min_rows), None, C.byref(ln)), "hylu_export_gemm_plan")
     buf = np.zeros(ln.value, np.int64)
     _check(lib.hylu_export_gemm_plan(h, int(min_rows), buf.ctypes.data, C.byref(ln)), "hylu_export_gemm_plan")
-    names = ("ngd", "nlc", "npairs", "ntri", "nck", "ntask", "ndiag", "norder", "levels", "nl")
+    names = ("ngd", "npair", "nxmap", "ntask", "ndiag", "norder", "levels", "nl", "min_src", "a_elems")
     cnt = dict(zip(names, (int(v) for v in buf[:10])))
     cnt["n"] = int(n)
     out = dict(cnt)
     pos = 10
     for name, size in GEMM_PLAN_ARRAYS:
-        key, _, plus = size.partition("+")
-        m = cnt[key] + (int(plus) if plus else 0) if cnt["ngd"] else 0
+        m = cnt[size] if cnt["ngd"] else 0
         out[name] = buf[pos:pos + m]
         pos += m
     return out

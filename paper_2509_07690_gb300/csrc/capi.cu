@@ -616,18 +616,18 @@ int hylu_export_gemm_plan(hylu_handle* h, int min_rows, int64_t* buf, int64_t* l
         hylu::GemmPlan G;
         if (hylu::build_gemm_plan(h->P, min_rows, G) != 0) return HYLU_ERR_INTERNAL;
         std::vector<int64_t> out;
-        const int64_t npairs = G.ngd ? (int64_t)G.pr_tri_off.size() - 1 : 0;
-        const int64_t head[10] = {G.ngd, (int64_t)G.lc_cols.size(), npairs, (int64_t)G.tri_u0.size(),
-                                  (int64_t)G.ck_kc.size(), (int64_t)G.task_gd.size(), (int64_t)G.diag_row.size(),
-                                  (int64_t)G.row_order.size(), G.levels, (int64_t)h->P.lcols.size()};
+        const int64_t head[10] = {G.ngd, (int64_t)G.pair_gd.size(), (int64_t)G.xmap.size(),
+                                  (int64_t)G.task_pair.size(), (int64_t)G.diag_row.size(),
+                                  (int64_t)G.row_order.size(), G.levels, (int64_t)h->P.lcols.size(), G.min_src,
+                                  G.a_elems};
         out.insert(out.end(), head, head + 10);
         if (G.ngd) {
             auto put = [&](const auto& v) { for (auto x : v) out.push_back((int64_t)x); };
-            put(G.gd_node); put(G.gd_K); put(G.gd_Kp); put(G.gd_Mp); put(G.gd_ntiles); put(G.gd_a_off);
-            put(G.gd_lc_off); put(G.lc_cols); put(G.gd_tile_base); put(G.pr_tri_off); put(G.tri_u0);
-            put(G.tri_len); put(G.tri_node); put(G.tri_jlo); put(G.tri_jhi); put(G.pr_ck_off); put(G.ck_kc);
-            put(G.ck_t0); put(G.ck_t1); put(G.task_gd); put(G.task_mt); put(G.task_nt); put(G.task_level);
-            put(G.lu_pos); put(G.row_order); put(G.diag_row); put(G.walk_level); put(G.diag_level);
+            put(G.gd_node); put(G.gd_Kp); put(G.gd_Mp); put(G.gd_a_off); put(G.gd_ntask);
+            put(G.pair_gd); put(G.pair_src); put(G.pair_u0); put(G.pair_len); put(G.pair_jr); put(G.pair_nj);
+            put(G.pair_need); put(G.pair_x_off); put(G.xmap); put(G.gd_slot);
+            put(G.task_pair); put(G.task_mt); put(G.task_jt); put(G.task_level);
+            put(G.row_order); put(G.diag_row); put(G.walk_level); put(G.diag_level);
         }
         const int64_t need = (int64_t)out.size();
         if (!buf) { *len = need; return HYLU_OK; }

@@ -1,6 +1,7 @@
 // Tables of the precision form's tensor-core sup-sup update (HYLU Sec. 2.2,
-// Fig. 1c: a supernode destination takes the updates of its sources as dense
-// products), built once per plan on the host.  See GemmPlan in plan.hpp.
+// Fig. 1c: a supernode destination takes the updates of its source
+// supernodes as dense products), built once per plan on the host.  See
+// GemmPlan in plan.hpp.
 #include <algorithm>
 #include <vector>
 
@@ -19,6 +20,7 @@ int build_gemm_plan(const Plan& P, int32_t min_rows, GemmPlan& G) {
     const int32_t n = P.n, nn = P.nnodes;
     G.gd_of_node.assign(nn, -1);
     if (min_rows <= 0 || nn == 0) return 0;
+    G.min_src = std::min(16, std::max(2, min_rows));
     auto seg_len = [&](int32_t S) { return P.sn_start[S + 1] - P.sn_start[S]; };
     auto ntask = [&](int32_t S) { return P.node_ntask.empty() ? 0 : P.node_ntask[S]; };
 
@@ -42,93 +44,73 @@ int build_gemm_plan(const Plan& P, int32_t min_rows, GemmPlan& G) {
         }
     if (G.ngd == 0) return 0;
 
-    // ---- per destination: union L columns, A block, union position of
-    //      every L slot, and the (N tile, source segment) triples
-    G.lu_pos.assign(P.lcols.size(), -1);
-    G.gd_lc_off.push_back(0);
-    G.gd_tile_base.push_back(0);
-    G.pr_tri_off.push_back(0);
-    G.pr_ck_off.push_back(0);
-    std::vector<int32_t> colx(n, -1);        // global column -> U-column index of the destination
-    std::vector<int32_t> lc;
+    // ---- pairs (destination, large source supernode with tail entries at
+    //      or past the destination's first row), their A columns and maps
+    G.gd_slot.assign(P.lcols.size(), -1);
+    std::vector<int32_t> colx(n, -1);          // global column -> U-column index of the destination
+    std::vector<int32_t> pair_of(nn, -1);      // source -> pair of the current destination
+    std::vector<int32_t> srcs;
     for (int32_t g = 0; g < G.ngd; ++g) {
         const int32_t D = G.gd_node[g];
         const int32_t r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int64_t t0 = P.node_tail_off[D];
         const int32_t nT = (int32_t)(P.node_tail_off[D + 1] - t0);
-        const int32_t w = s + nT;
-        lc.clear();
-        for (int32_t i = r; i <= e; ++i)
-            lc.insert(lc.end(), P.lcols.begin() + P.row_lptr[i], P.lcols.begin() + P.row_lptr[i + 1]);
-        std::sort(lc.begin(), lc.end());
-        lc.erase(std::unique(lc.begin(), lc.end()), lc.end());
-        const int32_t K = (int32_t)lc.size();
-        G.gd_K.push_back(K);
-        G.gd_Kp.push_back(round_up(K, GemmPlan::TK));
-        G.gd_Mp.push_back(round_up(s, GemmPlan::TM));
-        G.gd_a_off.push_back(G.a_elems);
-        G.a_elems += (int64_t)G.gd_Mp.back() * G.gd_Kp.back();
-        G.lc_cols.insert(G.lc_cols.end(), lc.begin(), lc.end());
-        G.gd_lc_off.push_back((int64_t)G.lc_cols.size());
-        for (int32_t i = r; i <= e; ++i)
-            for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1]; ++t)
-                G.lu_pos[t] = (int32_t)(std::lower_bound(lc.begin(), lc.end(), P.lcols[t]) - lc.begin());
-        const int32_t ntiles = (w + GemmPlan::TN - 1) / GemmPlan::TN;
-        G.gd_ntiles.push_back(ntiles);
-        G.gd_tile_base.push_back(G.gd_tile_base.back() + ntiles);
         for (int32_t x = 0; x < s; ++x) colx[r + x] = x;
         for (int32_t j = 0; j < nT; ++j) colx[P.tcols[t0 + j]] = s + j;
-        struct Tri { int32_t u0, len, S, jlo, jhi; };
-        std::vector<std::vector<Tri>> per(ntiles);
-        for (int32_t u = 0; u < K;) {
-            const int32_t S = P.node_of[lc[u]], len = seg_len(S);
-            if (lc[u] != P.sn_start[S] || u + len > K || lc[u + len - 1] != P.sn_start[S + 1] - 1) return -1;
-            const int64_t a = P.node_tail_off[S], b = P.node_tail_off[S + 1];
-            int64_t j = std::lower_bound(P.tcols.begin() + a, P.tcols.begin() + b, r) - P.tcols.begin();
-            while (j < b) {
-                const int32_t x = colx[P.tcols[j]];
-                if (x < 0) return -1;                 // a tail column outside D's U columns: not closed
-                const int32_t nt = x / GemmPlan::TN;
-                int64_t j2 = j + 1;
-                while (j2 < b && colx[P.tcols[j2]] >= 0 && colx[P.tcols[j2]] / GemmPlan::TN == nt) ++j2;
-                per[nt].push_back({u, len, S, (int32_t)(j - a), (int32_t)(j2 - a)});
-                j = j2;
+        srcs.clear();
+        for (int32_t i = r; i <= e; ++i)
+            for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
+                const int32_t S = P.node_of[P.lcols[t]];
+                srcs.push_back(S);
+                t += seg_len(S);
             }
-            u += len;
+        std::sort(srcs.begin(), srcs.end());
+        srcs.erase(std::unique(srcs.begin(), srcs.end()), srcs.end());
+        int32_t kp = 0;
+        for (int32_t S : srcs) {
+            if (seg_len(S) < G.min_src) continue;
+            const int64_t a = P.node_tail_off[S], b = P.node_tail_off[S + 1];
+            const int64_t jr = std::lower_bound(P.tcols.begin() + a, P.tcols.begin() + b, r) - P.tcols.begin();
+            if (jr == b) continue;
+            const int32_t p = (int32_t)G.pair_gd.size();
+            pair_of[S] = p;
+            G.pair_gd.push_back(g);
+            G.pair_src.push_back(S);
+            G.pair_u0.push_back(kp);
+            G.pair_len.push_back(seg_len(S));
+            G.pair_jr.push_back((int32_t)(jr - a));
+            G.pair_nj.push_back((int32_t)(b - jr));
+            G.pair_need.push_back(0);
+            G.pair_x_off.push_back((int64_t)G.xmap.size());
+            for (int64_t j = jr; j < b; ++j) {
+                const int32_t x = colx[P.tcols[j]];
+                if (x < 0) return -1;            // a tail column outside D's U columns: not closed
+                G.xmap.push_back(x);
+            }
+            kp += round_up(seg_len(S), GemmPlan::TK);
         }
+        for (int32_t i = r; i <= e; ++i)
+            for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
+                const int32_t S = P.node_of[P.lcols[t]];
+                if (pair_of[S] >= 0) {
+                    G.gd_slot[t] = pair_of[S];
+                    G.pair_need[pair_of[S]]++;
+                }
+                t += seg_len(S);
+            }
+        for (int32_t S : srcs) pair_of[S] = -1;
         for (int32_t x = 0; x < s; ++x) colx[r + x] = -1;
         for (int32_t j = 0; j < nT; ++j) colx[P.tcols[t0 + j]] = -1;
-        for (int32_t nt = 0; nt < ntiles; ++nt) {
-            const int32_t base = (int32_t)G.tri_u0.size();
-            for (const Tri& q : per[nt]) {
-                const int32_t idx = (int32_t)G.tri_u0.size();
-                G.tri_u0.push_back(q.u0);
-                G.tri_len.push_back(q.len);
-                G.tri_node.push_back(q.S);
-                G.tri_jlo.push_back(q.jlo);
-                G.tri_jhi.push_back(q.jhi);
-                const int32_t k0 = q.u0 / GemmPlan::TK, k1 = (q.u0 + q.len - 1) / GemmPlan::TK;
-                for (int32_t kc = k0; kc <= k1; ++kc) {
-                    const size_t nc = G.ck_kc.size();
-                    if (nc > (size_t)G.pr_ck_off.back() && G.ck_kc[nc - 1] == kc) {
-                        G.ck_t1[nc - 1] = idx + 1;
-                    } else {
-                        G.ck_kc.push_back(kc);
-                        G.ck_t0.push_back(idx);
-                        G.ck_t1.push_back(idx + 1);
-                    }
-                }
-            }
-            (void)base;
-            G.pr_tri_off.push_back((int32_t)G.tri_u0.size());
-            G.pr_ck_off.push_back((int32_t)G.ck_kc.size());
-        }
+        G.gd_Kp.push_back(kp);
+        G.gd_Mp.push_back(round_up(s, GemmPlan::TM));
+        G.gd_a_off.push_back(G.a_elems);
+        G.a_elems += (int64_t)G.gd_Mp.back() * kp;
     }
 
     // ---- levels: nodes before any destination keep theirs; a destination
-    //      row walks after its sources complete, the node's GEMM tiles after
-    //      every walk, the diagonal-block steps after the tiles, one row per
-    //      level, and its tail tasks after the last step
+    //      row walks after its sources complete, the destination's GEMM tasks
+    //      come after every walk, the diagonal-block steps after the tasks,
+    //      one row per level, and its tail tasks after the last step
     G.walk_level.assign(n, -1);
     G.diag_level.assign(n, -1);
     std::vector<int32_t> gemm_level(G.ngd, 0);
@@ -177,18 +159,23 @@ int build_gemm_plan(const Plan& P, int32_t min_rows, GemmPlan& G) {
     for (int32_t d = 0; d < nd; ++d) G.row_order[cnt[G.diag_level[G.diag_row[d]]]++] = n + P.n_tasks + d;
     for (int32_t i = 0; i < n; ++i) G.row_order[cnt[G.walk_level[i]]++] = i;
     G.levels = maxl + 1;
-    // GEMM tasks by level, then destination, M tile, N tile
-    std::vector<int32_t> order(G.ngd);
-    for (int32_t g = 0; g < G.ngd; ++g) order[g] = g;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return gemm_level[a] < gemm_level[b]; });
-    for (int32_t g : order)
+    // GEMM tasks by level, then pair, M tile, tail tile
+    std::vector<int32_t> order(G.pair_gd.size());
+    for (size_t p = 0; p < order.size(); ++p) order[p] = (int32_t)p;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int32_t a, int32_t b) { return gemm_level[G.pair_gd[a]] < gemm_level[G.pair_gd[b]]; });
+    G.gd_ntask.assign(G.ngd, 0);
+    for (int32_t p : order) {
+        const int32_t g = G.pair_gd[p];
         for (int32_t mt = 0; mt < G.gd_Mp[g] / GemmPlan::TM; ++mt)
-            for (int32_t nt = 0; nt < G.gd_ntiles[g]; ++nt) {
-                G.task_gd.push_back(g);
+            for (int32_t jt = 0; jt * GemmPlan::TN < G.pair_nj[p]; ++jt) {
+                G.task_pair.push_back(p);
                 G.task_mt.push_back(mt);
-                G.task_nt.push_back(nt);
+                G.task_jt.push_back(jt);
                 G.task_level.push_back(gemm_level[g]);
+                G.gd_ntask[g]++;
             }
+    }
     return 0;
 }
 

@@ -138,38 +138,38 @@ int save_plan(const Plan& P, const BatchLayout& B, bool batch, const hylu_option
 int load_plan(const uint8_t* buf, size_t bytes, Plan& P, BatchLayout& B, bool& batch, hylu_options& opt);
 
 // Tensor-core tables of the precision form (gemm_plan.cpp).  A supernode of
-// at least min_rows rows, and every node that has such a node (or a node
-// that does) among its sources, is a GEMM destination D.  Its rows walk
-// their sources as other rows do (multipliers, and the updates that land in
-// their own L part), but the updates of their U part -- D's diagonal block
-// and U tail -- are summed as one dense product
-//     X_D[:, U cols] -= L_D[:, Lc] * U[Lc, U cols]
-// over the union Lc of D's L columns, computed by GEMM tiles of TM x TN
-// destination entries over K chunks of TK union columns.  Each row then
-// takes its diagonal-block step in a task of its own (a "diag task").
+// at least min_rows rows, and every node with such a node (or one
+// downstream of it) among its sources, is a GEMM destination D.  Its rows
+// walk their sources as other rows do, but for a large source supernode S
+// (at least min_src = min(16, max(2, min_rows)) rows) a row only computes
+// its multipliers L(i, S) (the triangular solve with S's diagonal block)
+// and the updates that land in its own L part; the updates of D's diagonal
+// block and U tail from S are the dense product
+//     X_D[:, T_S >= r_D] -= L_{D,S} * U_{S, T_S >= r_D}
+// computed by GEMM tasks on the tensor cores, one per (pair (D, S), 128-row
+// M tile of D, 64-entry tile of S's tail) and added into D's panel.  Each
+// row of D then takes its diagonal-block step in a task of its own (a
+// "diag task") once its walk and D's GEMM tasks are done.
 struct GemmPlan {
     static constexpr int TM = 128, TN = 64, TK = 32;
-    int32_t ngd = 0;
+    int32_t ngd = 0, min_src = 0;
     std::vector<int32_t> gd_of_node;    // node -> destination, or -1
     std::vector<int32_t> gd_node;       // destination -> node
-    std::vector<int32_t> gd_K, gd_Kp, gd_Mp, gd_ntiles;
-    std::vector<int64_t> gd_a_off;      // start of the destination's Mp x Kp block in each term array
+    std::vector<int32_t> gd_Kp, gd_Mp;  // A block of the destination: Mp rows x Kp columns
+    std::vector<int64_t> gd_a_off;      // its start in each term array
+    std::vector<int32_t> gd_ntask;      // GEMM tasks of the destination
     int64_t a_elems = 0;                // elements of one term array
-    std::vector<int64_t> gd_lc_off;     // ngd + 1 into lc_cols
-    std::vector<int32_t> lc_cols;       // union L columns of every destination, sorted
-    std::vector<int32_t> gd_tile_base;  // ngd + 1: first (destination, N tile) pair
-    // per (destination, N tile) pair: the source segments whose U tail meets
-    // the tile -- union offset u0 and length of the segment, source node, and
-    // the range [jlo, jhi) of its tail entries that fall in the tile
-    std::vector<int32_t> pr_tri_off;    // npairs + 1
-    std::vector<int32_t> tri_u0, tri_len, tri_node, tri_jlo, tri_jhi;
-    // and the K chunks with any such segment: chunk index, first and end
-    // triple overlapping it
-    std::vector<int32_t> pr_ck_off;     // npairs + 1
-    std::vector<int32_t> ck_kc, ck_t0, ck_t1;
-    // GEMM tasks in claim order (by level): destination, M tile, N tile
-    std::vector<int32_t> task_gd, task_mt, task_nt, task_level;
-    std::vector<int32_t> lu_pos;        // per L slot of a destination row: union index (else -1)
+    // pairs (destination, large source): A columns [u0, u0 + len) hold
+    // L_{D,S} (u0 a multiple of TK), the source's tail entries jr .. jr + nj
+    // are the ones at or past r_D, need = rows of D that hold S, and xmap
+    // [x_off, x_off + nj) gives each of them its U-column index in D
+    std::vector<int32_t> pair_gd, pair_src, pair_u0, pair_len, pair_jr, pair_nj, pair_need;
+    std::vector<int64_t> pair_x_off;
+    std::vector<int32_t> xmap;
+    std::vector<int32_t> gd_slot;       // per L slot: the pair at the first slot of a large source
+                                        // segment in a destination row, else -1
+    // GEMM tasks in claim order (by level): pair, M tile, tail tile
+    std::vector<int32_t> task_pair, task_mt, task_jt, task_level;
     // claim order of the rows' queue: rows (< n), tail tasks (n + t) and diag
     // tasks (n + n_tasks + d, the diagonal-block step of row diag_row[d])
     std::vector<int32_t> row_order, diag_row;

@@ -1,11 +1,10 @@
 """Host tables of the precision form's tensor-core sup-sup update (HYLU
 Sec. 2.2, Fig. 1c), rebuilt here by brute force from the exported padded
 pattern and compared entry by entry: the destination set (large supernodes
-and everything downstream of one), each destination's union of L columns,
-the union position of every L slot, the (N tile, source segment, tail
-range) triples that say which source tail entries land in which tile, the K
-chunks of every tile, the GEMM task list, and the claim order (every task
-after everything it waits on)."""
+and everything downstream of one),
+the (destination, large source) pairs with their A columns, tail ranges and
+U-column maps, the pair named at each L slot, the GEMM task list, and the
+claim order (every task after everything it waits on)."""
 import numpy as np
 import pytest
 
@@ -56,62 +55,61 @@ def test_gemm_plan_matches_brute_force(name, A, opts, min_rows):
     if len(gd) == 0:
         s.close()
         return
+    min_src = min(16, max(2, min_rows))
+    assert G["min_src"] == min_src
     assert np.array_equal(G["gd_node"], gd)
     lslot0 = np.concatenate([[0], np.cumsum([len(x) for x in B["lcols"]])])
+    want_pairs = []
     a_off = 0
     for g, D in enumerate(gd):
         r, e = sn[D], sn[D + 1] - 1
         sD = e - r + 1
-        lc = np.unique(np.concatenate([B["lcols"][i] for i in range(r, e + 1)] + [np.zeros(0, np.int64)]))
-        got_lc = G["lc_cols"][G["gd_lc_off"][g]:G["gd_lc_off"][g + 1]]
-        assert np.array_equal(got_lc, lc)
-        K = len(lc)
-        assert G["gd_K"][g] == K and G["gd_Kp"][g] == -(-K // TK) * TK
-        assert G["gd_Mp"][g] == -(-sD // TM) * TM
-        assert G["gd_a_off"][g] == a_off
-        a_off += G["gd_Mp"][g] * G["gd_Kp"][g]
-        for i in range(r, e + 1):
-            pos = G["lu_pos"][lslot0[i]:lslot0[i + 1]]
-            assert np.array_equal(lc[pos], B["lcols"][i])
         ucols = np.concatenate([np.arange(r, e + 1), B["tail"][D]])
-        ntiles = -(-len(ucols) // TN)
-        assert G["gd_ntiles"][g] == ntiles
         uidx = {int(c): x for x, c in enumerate(ucols)}
-        # every (tile, union column, tail entry) the product needs, by brute force
-        want = set()
-        for k in lc:
+        kp = 0
+        for S in B["src"][D]:
+            ln = sn[S + 1] - sn[S]
+            T = B["tail"][S]
+            jr = int(np.searchsorted(T, r))
+            if ln < min_src or jr == len(T):
+                continue
+            need = sum(1 for i in range(r, e + 1) if sn[S] in set(B["lcols"][i].tolist()))
+            want_pairs.append((g, S, kp, ln, jr, len(T) - jr, need, [uidx[int(c)] for c in T[jr:]]))
+            kp += -(-ln // TK) * TK
+        assert G["gd_Kp"][g] == kp and G["gd_Mp"][g] == -(-sD // TM) * TM
+        assert G["gd_a_off"][g] == a_off
+        a_off += G["gd_Mp"][g] * kp
+    assert G["a_elems"] == a_off
+    assert G["npair"] == len(want_pairs)
+    for p, (g, S, u0, ln, jr, nj, need, xm) in enumerate(want_pairs):
+        got = (G["pair_gd"][p], G["pair_src"][p], G["pair_u0"][p], G["pair_len"][p], G["pair_jr"][p],
+               G["pair_nj"][p], G["pair_need"][p])
+        assert got == (g, S, u0, ln, jr, nj, need), p
+        x0 = G["pair_x_off"][p]
+        assert list(G["xmap"][x0:x0 + nj]) == xm
+    # the first L slot of every large source segment in a destination row
+    # names its pair; no other slot does
+    pair_of = {(int(G["pair_gd"][p]), int(G["pair_src"][p])): p for p in range(G["npair"])}
+    gd_of = {int(D): g for g, D in enumerate(gd)}
+    want_slot = np.full(G["nl"], -1)
+    for i in range(A.n):
+        D = int(node_of[i])
+        if D not in gd_of:
+            continue
+        for t, k in enumerate(B["lcols"][i]):
             S = int(node_of[k])
-            for j, c in enumerate(B["tail"][S]):
-                if c >= r:
-                    want.add((uidx[int(c)] // TN, int(k), j))
-        got = set()
-        for nt in range(ntiles):
-            pair = G["gd_tile_base"][g] + nt
-            t0, t1 = G["pr_tri_off"][pair], G["pr_tri_off"][pair + 1]
-            for t in range(t0, t1):
-                u0, ln, S = G["tri_u0"][t], G["tri_len"][t], G["tri_node"][t]
-                assert lc[u0] == sn[S] and ln == sn[S + 1] - sn[S]
-                for j in range(G["tri_jlo"][t], G["tri_jhi"][t]):
-                    assert uidx[int(B["tail"][S][j])] // TN == nt
-                    for k in range(sn[S], sn[S + 1]):
-                        got.add((nt, int(k), j))
-            # chunks: exactly those overlapping a triple, each with its triples
-            c0, c1 = G["pr_ck_off"][pair], G["pr_ck_off"][pair + 1]
-            want_ck = sorted({kc for t in range(t0, t1)
-                              for kc in range(G["tri_u0"][t] // TK, (G["tri_u0"][t] + G["tri_len"][t] - 1) // TK + 1)})
-            assert list(G["ck_kc"][c0:c1]) == want_ck
-            for q in range(c0, c1):
-                kc = G["ck_kc"][q]
-                over = [t for t in range(t0, t1)
-                        if G["tri_u0"][t] < (kc + 1) * TK and G["tri_u0"][t] + G["tri_len"][t] > kc * TK]
-                assert list(range(G["ck_t0"][q], G["ck_t1"][q])) == over
-        assert got == want, (name, D)
-    # GEMM tasks: every (destination, M tile, N tile) once, levels ascending
-    tasks = sorted(zip(G["task_gd"], G["task_mt"], G["task_nt"]))
-    want_tasks = sorted((g, mt, nt) for g in range(len(gd)) for mt in range(G["gd_Mp"][g] // TM)
-                        for nt in range(G["gd_ntiles"][g]))
+            if k == sn[S] and (gd_of[D], S) in pair_of:
+                want_slot[lslot0[i] + t] = pair_of[(gd_of[D], S)]
+    assert np.array_equal(G["gd_slot"], want_slot)
+    # GEMM tasks: every (pair, M tile, tail tile) once, levels ascending, and
+    # the per-destination counts
+    tasks = sorted(zip(G["task_pair"], G["task_mt"], G["task_jt"]))
+    want_tasks = sorted((p, mt, jt) for p, w in enumerate(want_pairs)
+                        for mt in range(G["gd_Mp"][w[0]] // TM) for jt in range(-(-w[5] // TN)))
     assert tasks == want_tasks
     assert np.all(np.diff(G["task_level"]) >= 0)
+    cnt = np.bincount(G["pair_gd"][G["task_pair"]], minlength=len(gd))
+    assert np.array_equal(G["gd_ntask"], cnt)
     s.close()
 
 
@@ -142,7 +140,7 @@ def test_gemm_claim_order_respects_dependencies(name, A, opts):
     tasks_of = {}
     for t, D in enumerate(task_node):
         tasks_of.setdefault(int(D), []).append(n + t)
-    gemm_level = {int(g): int(l) for g, l in zip(G["task_gd"], G["task_level"])}
+    gemm_level = {int(G["pair_gd"][p]): int(l) for p, l in zip(G["task_pair"], G["task_level"])}
 
     def complete(S):
         """Queue positions whose end completes node S."""
@@ -159,6 +157,8 @@ def test_gemm_claim_order_respects_dependencies(name, A, opts):
             assert where[i] > where[i - 1]
     for D, g in gd_of.items():
         r, e = sn[D], sn[D + 1] - 1
+        if g not in gemm_level:
+            continue
         lg = gemm_level[g]
         assert all(G["walk_level"][i] < lg for i in range(r, e + 1))
         for i in range(r, e + 1):
