@@ -129,6 +129,11 @@ typedef struct {
                                    scaling, [1] ordering, [2] symbolic factorization,
                                    supernodes and schedules, [3] value map (a batch:
                                    summed over its systems)                           */
+    int32_t gemm_destinations;  /* precision form: GEMM destinations (see gemm_min_rows), 0 when the
+                                   tensor-core sup-sup path is off                     */
+    int32_t gemm_tasks;         /* its tensor-core GEMM tasks per factorization           */
+    double gemm_flops;          /* useful FP32 flops of those tasks (2 per multiply-add of
+                                   L_{D,S} U_{S,T}); 6 BF16 products carry each          */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */

@@ -52,6 +52,7 @@ struct hylu_handle {
     cudaGraphExec_t graph_exec = nullptr;
     int64_t graph_launches = 0;          // kernel launches recorded into the graph
     int graph_corrections = 0;           // refinement steps recorded after the graph's solve
+    double gemm_flops = 0.0;             // useful flops of the tensor-core sup-sup tasks
     int graph_nrhs = 0;
     bool graph_norms_pending = false;    // a replay wrote residual norms not yet read
     int grid_max = 0;
@@ -105,6 +106,71 @@ int guarded(F&& f) {
     } catch (...) {
         return HYLU_ERR_INTERNAL;
     }
+}
+
+// Precision form: the tables of the tensor-core sup-sup update (GemmPlan),
+// the split multiplier blocks and their TMA tensor maps.  Off (n_gd = 0) for
+// FP64 factors, gemm_min_rows = 0, when no pair qualifies, or without the
+// driver's tensor-map encoder.
+int upload_gemm(hylu_handle* h, cudaStream_t st) {
+    hylu::DevPlan& d = h->dp;
+    d.n_gd = d.n_gtask = d.n_diag = d.gemm_blocks = d.n_pair = 0;
+    d.a_elems = 0;
+    d.a_term[0] = d.a_term[1] = d.a_term[2] = nullptr;
+    d.tmaps = nullptr;
+    if (h->opt.precision != 1 || h->opt.gemm_min_rows <= 0) return HYLU_OK;
+    if (!hylu::tensor_maps_available() || !hylu::gemm_smem_fits()) return HYLU_OK;
+    hylu::GemmPlan G;
+    if (hylu::build_gemm_plan(h->P, h->opt.gemm_min_rows, G) != 0) return HYLU_ERR_INTERNAL;
+    if (G.ngd == 0 || G.task_pair.empty()) return HYLU_OK;
+    int32_t *gon, *gn, *gkp, *gnt, *pg, *ps, *pu, *pj, *pn, *pnd, *xm, *gs, *tp, *tm, *tj, *dr, *ro;
+    int64_t *gao, *pxo;
+    TRY(upload(h, &gon, G.gd_of_node, st));
+    TRY(upload(h, &gn, G.gd_node, st));
+    TRY(upload(h, &gkp, G.gd_Kp, st));
+    TRY(upload(h, &gao, G.gd_a_off, st));
+    TRY(upload(h, &gnt, G.gd_ntask, st));
+    TRY(upload(h, &pg, G.pair_gd, st));
+    TRY(upload(h, &ps, G.pair_src, st));
+    TRY(upload(h, &pu, G.pair_u0, st));
+    TRY(upload(h, &pj, G.pair_jr, st));
+    TRY(upload(h, &pn, G.pair_nj, st));
+    TRY(upload(h, &pnd, G.pair_need, st));
+    TRY(upload(h, &pxo, G.pair_x_off, st));
+    TRY(upload(h, &xm, G.xmap, st));
+    TRY(upload(h, &gs, G.gd_slot, st));
+    TRY(upload(h, &tp, G.task_pair, st));
+    TRY(upload(h, &tm, G.task_mt, st));
+    TRY(upload(h, &tj, G.task_jt, st));
+    TRY(upload(h, &dr, G.diag_row, st));
+    TRY(upload(h, &ro, G.row_order, st));
+    d.gd_of_node = gon; d.gd_node = gn; d.gd_Kp = gkp; d.gd_a_off = gao; d.gd_ntask = gnt;
+    d.pair_gd = pg; d.pair_src = ps; d.pair_u0 = pu; d.pair_jr = pj; d.pair_nj = pn; d.pair_need = pnd;
+    d.pair_x_off = pxo; d.xmap = xm; d.gd_slot = gs; d.gt_pair = tp; d.gt_mt = tm; d.gt_jt = tj;
+    d.diag_row = dr;
+    d.row_order = ro;
+    TRY(dalloc(h, &d.pair_cnt, G.pair_gd.size()));
+    TRY(dalloc(h, &d.gd_done, G.ngd));
+    TRY(dalloc(h, &d.walk_done, h->P.n));
+    if (cudaMemsetAsync(d.walk_done, 0, sizeof(int32_t) * h->P.n, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    for (int s = 0; s < 3; ++s) TRY(dalloc(h, &d.a_term[s], (size_t)G.a_elems));
+    std::vector<unsigned char> maps(hylu::tensor_map_bytes() * 3 * (size_t)G.ngd);
+    TRY(hylu::encode_a_maps(G.ngd, G.gd_Mp.data(), G.gd_Kp.data(), G.gd_a_off.data(), d.a_term, maps.data()));
+    unsigned char* dm = nullptr;
+    TRY(upload(h, &dm, maps, st));
+    d.tmaps = dm;
+    d.n_gd = G.ngd;
+    d.n_pair = (int32_t)G.pair_gd.size();
+    d.n_gtask = (int32_t)G.task_pair.size();
+    d.n_diag = (int32_t)G.diag_row.size();
+    d.a_elems = G.a_elems;
+    h->gemm_flops = 0.0;
+    for (size_t p = 0; p < G.pair_gd.size(); ++p) {
+        h->gemm_flops += 2.0 * (double)G.pair_need[p] * G.pair_len[p] * G.pair_nj[p];
+    }
+    // the host copies above must outlive the asynchronous uploads
+    if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;
+    return HYLU_OK;
 }
 
 int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
@@ -226,6 +292,7 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     TRY(dalloc(h, &d.dinv, P.n));
     TRY(dalloc(h, &d.status, hylu::ST_WORDS));
     h->grid = hylu::factor_grid(h->device);
+    TRY(upload_gemm(h, st));
     {
         int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
@@ -308,6 +375,9 @@ int do_factor(hylu_handle* h, const double* d_vals, cudaStream_t st) {
     if (cudaMemcpyAsync(h->d_avals, d_vals, sizeof(double) * h->P.nnz_a, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return HYLU_ERR_CUDA;
     TRY(hylu::launch_reset(h->dp.status, h->dp.piv, h->dp.pinv, h->dp.gens, h->P.n, st));
+    // blocks of the factor launch that run the tensor-core GEMM tasks (one
+    // in eight; the rest take rows)
+    h->dp.gemm_blocks = h->dp.n_gd > 0 ? std::max(1, std::min(h->dp.n_gtask, h->grid / 8)) : 0;
     TRY(hylu::launch_factor(h->dp, h->d_avals, h->P.nnz_a, h->opt.pivot_tau,
                             h->opt.spin_limit, h->grid, st, h->opt.timing ? h->ev[0] : nullptr,
                             h->opt.timing ? h->ev[1] : nullptr));
@@ -563,6 +633,9 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->flops_in_supernode = P.flops_in_sn;
     info->ordering = P.ordering;
     for (int ph = 0; ph < 4; ++ph) info->analyze_phase_ms[ph] = P.analyze_phase_ms[ph];
+    info->gemm_destinations = h->dp.n_gd;
+    info->gemm_tasks = h->dp.n_gtask;
+    info->gemm_flops = h->gemm_flops;
     info->analyze_ms = P.analyze_ms;
     int rc = HYLU_OK;
     if (h->factored && h->uploaded) rc = read_status(h, h->last);

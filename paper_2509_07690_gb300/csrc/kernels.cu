@@ -32,7 +32,10 @@
 #include <climits>
 #include <cstdio>
 
+#include <cuda.h>
+
 #include "kernels.cuh"
+#include "tc_gemm.cuh"
 #include "../../include/hylu.h"
 
 namespace hylu {
@@ -88,6 +91,23 @@ __device__ __forceinline__ bool warp_wait(const int* flag, int gen, int* status,
         unsigned long long t1;
         asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t1));
         *waited += t1 - t0;
+    }
+    return __all_sync(FULL, ok) != 0;
+}
+
+// All lanes wait (bounded) until *cnt >= target (a counter zeroed before the
+// launch); errors as for warp_wait.
+__device__ __forceinline__ bool warp_wait_ge(const int* cnt, int target, int* status, int who, long long limit) {
+    int ok = 1;
+    long long it = 0;
+    while (ld_acquire(cnt) < target) {
+        if (++it > limit) {
+            if (atomicCAS(status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0) status[ST_FAILED] = who;
+            ok = 0;
+            break;
+        }
+        if ((it & 255) == 0 && ld_relaxed(status + ST_ERR) != 0) { ok = 0; break; }
+        if (it > 16) __nanosleep(64);
     }
     return __all_sync(FULL, ok) != 0;
 }
@@ -188,14 +208,15 @@ struct Panel {
 // Update x with entries j in [j0, nTS) of a standalone source's tail, all with
 // multiplier l; entries with columns below r go to the L part (atomic adds to
 // global memory: no one reads them before the window moves past them and a
-// fence is taken), the others to the panel, or, when spau is set (a row with
-// a dense L vector and a panel in global memory), to the dense vector by
-// column as well.  Loads of UNR batches are issued before any update so that
+// fence is taken), the others to the panel (by reductions when atomic_u is
+// set: the row of a GEMM destination, whose panel the tensor-core tasks add
+// to as well), or, when spau is set (a row with a dense L vector and a panel
+// in global memory), to the dense vector by column as well.  Loads of UNR batches are issued before any update so that
 // their latencies overlap.
 template <typename T>
 __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, const T* __restrict__ U1,
                                            int j0, int nTS, T l, int r, const int* pos, T* xl, T* spa,
-                                           T* spau, const Panel<T>& pn, int lane) {
+                                           T* spau, const Panel<T>& pn, int lane, bool atomic_u = false) {
     for (int jb = j0; jb < nTS; jb += 32 * UNR_TAIL) {
         int c[UNR_TAIL];
         T u[UNR_TAIL];
@@ -214,6 +235,7 @@ __device__ __forceinline__ void apply_tail(const int32_t* __restrict__ tcS, cons
             if (c[m] < 0) continue;
             if (c[m] < r) atomicAdd(spa ? spa + c[m] : xl + ix[m], -l * u[m]);
             else if (spau) atomicAdd(spau + c[m], -l * u[m]);
+            else if (atomic_u) atomicAdd(pn.x + ix[m], -l * u[m]);
             else pn.x[ix[m]] -= l * u[m];
         }
     }
@@ -312,12 +334,168 @@ __device__ bool tail_task(const DevPlan& P, int t, int gen, long long limit, War
 }
 
 
+// ------------------------------------------------ tensor-core sup-sup tasks
+// The last P.gemm_blocks blocks of the precision-form factor launch run the
+// GEMM tasks (Sec. 2.2, Fig. 1c, sup-sup): for a pair (destination D, source
+// supernode S), one 128-row tile of D and 64 entries of S's tail at or past
+// D's first row,
+//     X_D[rows, T_S cols] -= L_{D,S}[rows, :] * U_{S, T_S cols}
+// with L_{D,S} (the multipliers D's rows computed and split into three BF16
+// terms) loaded by TMA, U_{S,.} (final: the rows waited for S) gathered from
+// S's panel and split on the way, the products on the tensor cores (6 term
+// products, FP32 accumulation in TMEM), and the result added into D's panel
+// rows at the U-column index of each tail entry (FP32 reductions: the rows
+// add their updates from small sources to the same entries).  A task waits,
+// bounded, until every row of D that holds S has written its multipliers;
+// the last task of D lets D's diag tasks start.
+struct GemmSmem {
+    tc::TileSmem<3> t;
+    int xm[tc::TN];      // U-column index in D of the tile's tail entries
+    int task;
+};
+
+__device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw, long long limit) {
+    const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
+    GemmSmem& G = *reinterpret_cast<GemmSmem*>(base);
+    tc::TileSmem<3>& sm = G.t;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        tc::mbar_init(&sm.bar_tma, 1);
+        tc::mbar_init(&sm.bar_mma, 1);
+        tc::mbar_fence_init();
+        sm.abort = 0;
+    }
+    if (warp == 0) tc::tmem_alloc(&sm.tmem_base, tc::TMEM_COLS);
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = sm.tmem_base;
+    const CUtensorMap* maps = static_cast<const CUtensorMap*>(P.tmaps);
+    // an mbarrier try_wait may suspend for a while by itself: fewer tries
+    const long long mlimit = limit < (1LL << 22) ? limit : (1LL << 22);
+    uint32_t ph_tma = 0, ph_mma = 0;
+    for (;;) {
+        if (tid == 0) {
+            int q = atomicAdd(P.status + ST_CNT_G, 1);
+            if (q >= P.n_gtask || ld_relaxed(P.status + ST_ERR) != 0) q = -1;
+            G.task = q;
+            if (q >= 0) {
+                // every row of D that holds S has written L_{D,S}
+                const int p = P.gt_pair[q];
+                const int need = P.pair_need[p];
+                long long it = 0;
+                while (ld_acquire(P.pair_cnt + p) < need) {
+                    if (++it > limit || ld_relaxed(P.status + ST_ERR) != 0) {
+                        if (atomicCAS(P.status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT) == 0)
+                            P.status[ST_FAILED] = P.gd_node[P.pair_gd[p]];
+                        G.task = -1;
+                        break;
+                    }
+                    __nanosleep(64);
+                }
+                // the multipliers were written through the generic proxy;
+                // the tensor copies below read them through the async proxy
+                asm volatile("fence.proxy.async.global;" ::: "memory");
+            }
+        }
+        __syncthreads();
+        const int q = G.task;
+        if (q < 0) break;
+        const int p = P.gt_pair[q], mt = P.gt_mt[q], jt = P.gt_jt[q];
+        const int g = P.pair_gd[p], D = P.gd_node[g], S = P.pair_src[p];
+        const int rD = P.sn_start[D], sD = P.sn_start[D + 1] - rD;
+        const int wD = sD + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+        const int rS = P.sn_start[S], sS = P.sn_start[S + 1] - rS;
+        const int wS = sS + (int)(P.node_tail_off[S + 1] - P.node_tail_off[S]);
+        const int nj = min(tc::TN, P.pair_nj[p] - jt * tc::TN);
+        const int j0 = sS + P.pair_jr[p] + jt * tc::TN;     // panel column of the tile's first entry
+        const float* US = P.pval32 + P.node_panel_off[S];
+        float* XD = P.pval32 + P.node_panel_off[D];
+        if (tid < tc::TN) G.xm[tid] = tid < nj ? P.xmap[P.pair_x_off[p] + jt * tc::TN + tid] : 0;
+        const int nch = (sS + tc::TK - 1) / tc::TK;
+        const int u0 = P.pair_u0[p];
+        bool ok = true;
+        for (int c = 0; c < nch; ++c) {
+            if (tid == 0) {
+                tc::mbar_expect_tx(&sm.bar_tma, 3 * tc::A_TERM_BYTES);
+                for (int s = 0; s < 3; ++s)
+                    for (int j = 0; j < tc::TK / tc::KB; ++j)
+                        tc::tma_load_2d(&sm.a[s][j * tc::KB * tc::TM], maps + 3 * g + s,
+                                        u0 + c * tc::TK + j * tc::KB, mt * tc::TM, &sm.bar_tma);
+            }
+            // B: positions c*TK .. of S (rows of its panel), the tile's tail entries
+            for (int e2 = tid; e2 < tc::TK * tc::TN; e2 += 128) {
+                const int k = e2 / tc::TN, t = e2 % tc::TN;
+                const int pk = c * tc::TK + k;
+                const float v = (pk < sS && t < nj) ? __ldcg(US + (int64_t)pk * wS + j0 + t) : 0.f;
+                __nv_bfloat16 h3[3];
+                tc::split_bf16<3>(v, h3);
+                for (int s = 0; s < 3; ++s)
+                    *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.b[s]) + tc::b_off(t, k)) = h3[s];
+            }
+            tc::fence_async_smem();
+            __syncthreads();
+            if (tid == 0) {
+                if (!tc::mbar_wait(&sm.bar_tma, ph_tma, mlimit)) {
+                    sm.abort = 1;
+                    atomicCAS(P.status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT);
+                    tc::mbar_wait(&sm.bar_tma, ph_tma, mlimit);     // copies still in flight
+                } else {
+                    tc::tc_fence_after();
+                    tc::issue_chunk<3>(sm, tmem, c == 0);
+                    tc::mma_commit(&sm.bar_mma);
+                }
+            }
+            ph_tma ^= 1u;
+            __syncthreads();
+            if (sm.abort) { ok = false; break; }
+            if (!tc::mbar_wait(&sm.bar_mma, ph_mma, mlimit)) {
+                if (tid == 0) atomicCAS(P.status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT);
+                tc::mbar_wait(&sm.bar_mma, ph_mma, mlimit);
+                sm.abort = 1;
+            }
+            ph_mma ^= 1u;
+            __syncthreads();
+            if (sm.abort) { ok = false; break; }
+        }
+        if (!ok) break;
+        // epilogue: this warp's 32 TMEM lanes are rows mt*128 + warp*32 + lane
+        tc::tc_fence_after();
+        const int m = mt * tc::TM + warp * 32 + lane;
+        for (int jj = 0; jj < tc::TN / 16; ++jj) {
+            float v[16];
+            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(jj * 16), v);
+            if (m < sD) {
+#pragma unroll
+                for (int u = 0; u < 16; ++u) {
+                    const int t = jj * 16 + u;
+                    if (t < nj) atomicAdd(XD + (int64_t)m * wD + G.xm[t], -v[u]);
+                }
+            }
+        }
+        tc::tc_fence_before();
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(P.gd_done + g, 1);
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, tc::TMEM_COLS);
+}
+
 template <typename T>
 __global__ void __launch_bounds__(FWARPS * 32, 4)
 factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
               double tau_rel, long long limit) {
     const int gen = P.gens[0];
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    if (P.gemm_blocks > 0 && (int)blockIdx.x >= (int)gridDim.x - P.gemm_blocks) {
+        if constexpr (sizeof(T) == 4) gemm_role(P, smem_raw, limit);
+        return;
+    }
+    const int nrowblk = (int)gridDim.x - P.gemm_blocks;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem<T>* ws = reinterpret_cast<WarpSmem<T>*>(smem_raw) + wid;
     T* lb = ws->lb;
@@ -340,7 +518,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
     // early claiming pays only when every heavy row gets a warp at once; with
     // more heavy rows than heavy warps (batches of many systems) they would
     // hold warps while waiting on their own chains: plain level order instead
-    const int hcap = ((int64_t)P.n_heavy <= (int64_t)HEAVY_WPB * gridDim.x) ? P.n_heavy : 0;
+    const int hcap = ((int64_t)P.n_heavy <= (int64_t)HEAVY_WPB * nrowblk) ? P.n_heavy : 0;
     heavy_open = heavy_open && hcap > 0;
     for (;;) {
         int i = -1;
@@ -351,7 +529,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
             }
             while (i < 0 && main_open) {
                 const int qi = atomicAdd(P.status + ST_CNT_F, 1);
-                if (qi >= P.n + P.n_tasks) { main_open = false; break; }
+                if (qi >= P.n + P.n_tasks + P.n_diag) { main_open = false; break; }
                 const int c = P.row_order[qi];
                 if (c >= P.n || hcap == 0 || P.heavy_rank[c] >= hcap) i = c;
             }
@@ -364,11 +542,17 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         i = __shfl_sync(FULL, i, 0);
         if (i == INT_MAX) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
-        if (i >= P.n) {
+        // a diag task: the diagonal-block step of a GEMM destination's row,
+        // after its walk and the destination's tensor-core tasks
+        bool diag_only = false;
+        if (i >= P.n + P.n_tasks) {
+            i = P.diag_row[i - P.n - P.n_tasks];
+            diag_only = true;
+        } else if (i >= P.n) {
             if (!tail_task<T>(P, i - P.n, gen, limit, ws, lane)) return;
             continue;
         }
-        if (P.trace && lane == 0) P.trace[4 * (int64_t)i] = gtimer();
+        if (P.trace && lane == 0 && !diag_only) P.trace[4 * (int64_t)i] = gtimer();
         unsigned long long waited = 0;
         unsigned long long* wp = P.trace ? &waited : nullptr;
         const int D = P.node_of[i];
@@ -389,14 +573,20 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         Panel<T> pn;
         pn.r = r; pn.e = e; pn.s = s; pn.nL = nL; pn.nT = nT;
         pn.scols = reinterpret_cast<const int*>(ws->panel + sizeof(T) * (size_t)w);
+        // a row of a GEMM destination keeps its U part in its panel (global):
+        // the tensor-core tasks add their products there
+        const int gd = (P.n_gd > 0) ? P.gd_of_node[D] : -1;
         int range;
-        if ((int64_t)(maxcol - r + 1) * (int64_t)sizeof(T) <= PANEL_BYTES) {
+        if (gd >= 0) {
+            pn.mode = 2; pn.x = xu; range = w;
+        } else if ((int64_t)(maxcol - r + 1) * (int64_t)sizeof(T) <= PANEL_BYTES) {
             pn.mode = 0; pn.x = reinterpret_cast<T*>(ws->panel); range = maxcol - r + 1;
         } else if ((int64_t)w * (int64_t)sizeof(T) + (int64_t)nT * 4 <= PANEL_BYTES) {
             pn.mode = 1; pn.x = reinterpret_cast<T*>(ws->panel); range = w;
         } else {
             pn.mode = 2; pn.x = xu; range = w;
         }
+        if (!diag_only) {
         // ---- clear, column -> slot maps, scatter Ahat(i,:) (the value scatter).
         //      The first 32 L slots start in the shared-memory window; later
         //      L slots accumulate in global memory and are found through pos[]
@@ -410,7 +600,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         //      accumulates the U part in the dense vector (fire-and-forget
         //      reductions, no slot lookup, no load before the store) and
         //      gathers it into the panel after the last external update.
-        T* spau = (spa && pn.mode == 2) ? spa : nullptr;
+        T* spau = (spa && pn.mode == 2 && gd < 0) ? spa : nullptr;
         const bool need_pos = (!spa && nL > 32) || (pn.mode == 2 && !spau);
         win[lane] = T(0);
         if (spa) { for (int t = 32 + lane; t < nL; t += 32) spa[lc[t]] = T(0); }
@@ -535,7 +725,8 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                 if (pl >= nTS) continue;
                 const int64_t tS = __shfl_sync(FULL, tq0, qq);
                 const int64_t pS = __shfl_sync(FULL, pq0, qq);
-                apply_tail<T>(P.tcols + tS, PV<T>(P) + pS + 1, pl, nTS, win[qq], r, pos, xl, spa, spau, pn, lane);
+                apply_tail<T>(P.tcols + tS, PV<T>(P) + pS + 1, pl, nTS, win[qq], r, pos, xl, spa, spau, pn, lane,
+                              gd >= 0);
                 __syncwarp();
             }
             // any L slot past this window may have received atomic adds
@@ -594,20 +785,38 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                         }
                     } else if (spau) {
                         atomicAdd(spau + c, -acc);
+                    } else if (gd >= 0) {
+                        atomicAdd(pn.x + pn.idx(pos, c), -acc);
                     } else {
                         pn.x[pn.idx(pos, c)] -= acc;
                     }
                 };
+                // a large source of a GEMM destination: the multipliers go
+                // to the destination's split L block (the tensor-core tasks
+                // apply the tail entries at or past r); this row only takes
+                // the entries before r, a prefix of the sorted tail
+                const int pair = (gd >= 0) ? P.gd_slot[l0 + tt] : -1;
+                const int nTS_row = pair >= 0 ? P.pair_jr[pair] : nTS;
+                if (pair >= 0) {
+                    const int64_t ab = P.gd_a_off[gd] + (int64_t)(i - r) * P.gd_Kp[gd] + P.pair_u0[pair];
+                    for (int p = lane; p < sS; p += 32) {
+                        __nv_bfloat16 h3[3];
+                        tc::split_bf16<3>((float)lb[p], h3);
+                        P.a_term[0][ab + p] = __bfloat16_as_ushort(h3[0]);
+                        P.a_term[1][ab + p] = __bfloat16_as_ushort(h3[1]);
+                        P.a_term[2][ab + p] = __bfloat16_as_ushort(h3[2]);
+                    }
+                }
                 // GEMV x[T_S] -= l U_S,T_S: 4 columns per lane, rows unrolled
                 // by 4, so about 16 loads are in flight per lane (the FP64
                 // instruction count is the same whatever the shape)
-                for (int j0 = lane; j0 < nTS; j0 += 128) {
+                for (int j0 = lane; j0 < nTS_row; j0 += 128) {
                     T acc[4];
                     const T* Uj[4];
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         const int j = j0 + 32 * jj;
-                        Uj[jj] = U + sS + (j < nTS ? j : j0);
+                        Uj[jj] = U + sS + (j < nTS_row ? j : j0);
                         acc[jj] = T(0);
                     }
 #pragma unroll 4
@@ -619,12 +828,13 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
 #pragma unroll
                     for (int jj = 0; jj < 4; ++jj) {
                         const int j = j0 + 32 * jj;
-                        if (j < nTS) put(tcS[j], acc[jj]);
+                        if (j < nTS_row) put(tcS[j], acc[jj]);
                     }
                 }
                 for (int p = lane; p < sS; p += 32) xl[tt + p] = lb[p];
                 __threadfence();
                 __syncwarp();
+                if (pair >= 0 && lane == 0) atomicAdd(P.pair_cnt + pair, 1);
                 t = tt + sS;
                 pending = false;
             }
@@ -638,7 +848,22 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
             for (int j = lane; j < nT; j += 32) pn.x[s + j] = __ldcg(spau + tc[j]);
             __syncwarp();
         }
-        if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 1] = gtimer();
+        if (gd >= 0) {
+            // a GEMM destination's row: its diag task continues from here
+            if (P.trace && lane == 0) P.trace[4 * (int64_t)i + 1] = gtimer();
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release(P.walk_done + i, gen);
+            continue;
+        }
+        }   // walk
+        else {
+            // diag task: the row's own walk, then every tensor-core task of
+            // its destination (they add into its panel row)
+            if (!warp_wait(P.walk_done + i, gen, P.status, i, limit, wp)) return;
+            if (!warp_wait_ge(P.gd_done + gd, P.gd_ntask[gd], P.status, D, limit)) return;
+        }
+        if (P.trace && lane == 0 && !diag_only) P.trace[4 * (int64_t)i + 1] = gtimer();
         const unsigned long long waited_ext = waited;
         // a supernode with a U tail finishes it after the diagonal-block
         // step: by tail tasks, or (small nodes) by its last row right here
@@ -651,7 +876,8 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         // the panel (one entry) for a standalone row
         T* xd = (s > 1) ? lb : pn.x;
         if (s > 1) {
-            for (int c = lane; c < s; c += 32) lb[c] = pn.x[c];
+            // (a diag task reads from L2: the panel row was written by other SMs)
+            for (int c = lane; c < s; c += 32) lb[c] = diag_only ? __ldcg(pn.x + c) : pn.x[c];
             __syncwarp();
             // ---- diagonal-block step: earlier rows of the own supernode, each
             //      as soon as its own diagonal-block step is published
@@ -692,7 +918,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         if (lane == 0) {
             const int dl = (s > 1) ? (P.piv[i] - r) : 0;
             // the small-pivot check is taken in FP64 whatever the factor precision
-            double u = (double)xd[dl];
+            double u = (double)((diag_only && s == 1) ? __ldcg(xd + dl) : xd[dl]);
             if (fabs(u) < tau) {
                 u = (u >= 0.0) ? tau : -tau;
                 xd[dl] = (T)u;
@@ -1456,11 +1682,22 @@ int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t* gens, in
     return check("reset");
 }
 
+int gemm_smem_fits() { return sizeof(GemmSmem) + 1023 <= factor_smem<float>(); }
+
 int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a,
                   double tau_rel, long long spin_limit, int grid, cudaStream_t st, cudaEvent_t e0,
                   cudaEvent_t e1) {
     if (P.n_tasks > 0 && cudaMemsetAsync(P.node_done, 0, sizeof(int32_t) * P.nnodes, st) != cudaSuccess)
         return HYLU_ERR_CUDA;
+    if (P.n_gd > 0) {
+        // tensor-core sup-sup: counters, and the split multiplier blocks
+        // (entries no row writes -- padding rows and columns, and rows of a
+        // destination without the pair's source -- must read as zero)
+        if (cudaMemsetAsync(P.pair_cnt, 0, sizeof(int32_t) * P.n_pair, st) != cudaSuccess) return HYLU_ERR_CUDA;
+        if (cudaMemsetAsync(P.gd_done, 0, sizeof(int32_t) * P.n_gd, st) != cudaSuccess) return HYLU_ERR_CUDA;
+        for (int s = 0; s < 3; ++s)
+            if (cudaMemsetAsync(P.a_term[s], 0, sizeof(uint16_t) * P.a_elems, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    }
     int blocks = (int)std::min<int64_t>(2048, (nnz_a + 255) / 256 + 1);
     amax_kernel<<<blocks, 256, 0, st>>>(d_vals, P.ah_src, P.ah_scale, nnz_a, P.status);
     count_launch();

@@ -13,9 +13,10 @@ namespace hylu {
 //   [4] task counter of the forward solve, [5] of the backward solve,
 //   [6..7] max |Ahat| as the bit pattern of a non-negative double.
 //   [8..9] substitution: forward / backward claim counters ([10..11] unused).
-//   [12] task counter of the factor kernel's heavy-row queue.
+//   [12] task counter of the factor kernel's heavy-row queue, [13] of its
+//   tensor-core GEMM queue.
 enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_AMAX = 6, ST_CNT_FWD = 8,
-       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_CNT_H = 12, ST_WORDS = 14 };
+       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_CNT_H = 12, ST_CNT_G = 13, ST_WORDS = 14 };
 
 struct DevPlan {
     int32_t n, nnodes;
@@ -89,6 +90,35 @@ struct DevPlan {
     const int32_t* heavy_order;    // heavy rows by level (claimed first), null if none
     const int32_t* heavy_rank;     // per row: rank in heavy_order, INT32_MAX if not heavy
     int32_t n_heavy;
+    // precision form, tensor-core sup-sup update (GemmPlan on the host;
+    // n_gd == 0: off).  The last gemm_blocks blocks of the factor launch run
+    // the GEMM tasks; the rows' queue then also holds n_diag diag tasks.
+    int32_t n_gd, n_gtask, n_diag, gemm_blocks, n_pair;
+    int64_t a_elems;               // elements of each split-term array
+    const int32_t* gd_of_node;     // node -> destination, or -1
+    const int32_t* gd_node;
+    const int32_t* gd_Kp;
+    const int64_t* gd_a_off;
+    const int32_t* gd_ntask;
+    const int32_t* pair_gd;
+    const int32_t* pair_src;
+    const int32_t* pair_u0;
+    const int32_t* pair_jr;
+    const int32_t* pair_nj;
+    const int32_t* pair_need;
+    const int64_t* pair_x_off;
+    const int32_t* xmap;
+    const int32_t* gd_slot;        // per L slot: pair at the first slot of a large source segment, else -1
+    const int32_t* gt_pair;        // GEMM tasks in claim order
+    const int32_t* gt_mt;
+    const int32_t* gt_jt;
+    const int32_t* diag_row;       // diag task d: the diagonal-block step of this row
+    int32_t* pair_cnt;             // rows that wrote their multipliers for the pair (zeroed per factor)
+    int32_t* gd_done;              // GEMM tasks finished per destination (zeroed per factor)
+    int32_t* walk_done;            // per row: walk finished (factor generation)
+    uint16_t* a_term[3];           // L_{D,S} split into three BF16 terms (raw bits), per destination
+                                   //   an Mp x Kp row-major block (zeroed per factor)
+    const void* tmaps;             // TMA tensor maps, 3 per destination (term-major inside), device memory
     unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, waits / node complete)
     int32_t* status;
     // [0] factor generation, [1] substitution generation: the flags above
@@ -122,6 +152,13 @@ int dense_l_min();
 int64_t launches();
 int measure_fp64_peak(double* gflops, cudaStream_t st);
 bool tensor_maps_available();  // the driver's TMA tensor-map encoder was found
+// Encode the tensor maps of the split multipliers: for destination g and term
+// s, an Mp[g] x Kp[g] BF16 block at a_term[s] + a_off[g], boxes of 8 x 128;
+// written to host memory `out` (3 per destination, 128 bytes each).
+int encode_a_maps(int32_t ngd, const int32_t* Mp, const int32_t* Kp, const int64_t* a_off, uint16_t* const* a_term,
+                  void* out);
+size_t tensor_map_bytes();
+int gemm_smem_fits();          // the tile engine fits the factor kernel's shared memory
 void count_launch();
 void add_launches(int64_t k);
 

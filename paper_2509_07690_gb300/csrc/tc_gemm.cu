@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <mutex>
 
 #include "kernels.cuh"
@@ -190,6 +191,30 @@ int run_dense(const float* A, const float* B, float* C, int M, int N, int K, int
 }  // namespace
 
 bool tensor_maps_available() { return encode_fn() != nullptr; }
+
+size_t tensor_map_bytes() { return sizeof(CUtensorMap); }
+
+int encode_a_maps(int32_t ngd, const int32_t* Mp, const int32_t* Kp, const int64_t* a_off, uint16_t* const* a_term,
+                  void* out) {
+    auto enc = encode_fn();
+    if (!enc) return HYLU_ERR_CUDA;
+    CUtensorMap* m = static_cast<CUtensorMap*>(out);
+    for (int32_t g = 0; g < ngd; ++g)
+        for (int s = 0; s < 3; ++s) {
+            CUtensorMap& t = m[3 * g + s];
+            std::memset(&t, 0, sizeof(t));
+            if (Kp[g] == 0) continue;          // no pair: never loaded
+            cuuint64_t dims[2] = {(cuuint64_t)Kp[g], (cuuint64_t)Mp[g]};
+            cuuint64_t strides[1] = {(cuuint64_t)Kp[g] * 2};
+            cuuint32_t box[2] = {(cuuint32_t)tc::KB, (cuuint32_t)tc::TM};
+            cuuint32_t estr[2] = {1, 1};
+            if (enc(&t, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, a_term[s] + a_off[g], dims, strides, box, estr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+                return HYLU_ERR_CUDA;
+        }
+    return HYLU_OK;
+}
 
 }  // namespace hylu
 
