@@ -374,6 +374,25 @@ int hylu_plan_load(const void* buf, int64_t bytes, const hylu_options* opt, hylu
  * the own supernode.  HYLU_ERR_STATE when tracing is off. */
 int hylu_debug_trace(hylu_handle* h, unsigned long long* out);
 
+/* Diagnostics of the tensor-core sup-sup path after a factorization
+ * (synchronizes; HOST arrays, any may be NULL): pair_cnt int32[pairs] (rows
+ * that wrote their multipliers for each pair), gd_done int32[destinations]
+ * (GEMM tasks finished), walk_done int32[n] (factor generation at which each
+ * row's walk ended), status int32[16] (the device status words); with
+ * tracing on (opt.debug & 2), block_prog int32[4 * *nblocks]: per GEMM block
+ * the last task claimed, its stage (1 claimed, 2 waited, 3-6 per K chunk:
+ * loads issued, operands staged, products issued, products done, 7-8
+ * epilogue), the chunk and a spare word (*nblocks = 0 without tracing).
+ * HYLU_ERR_STATE when the path is off or nothing was factored. */
+int hylu_debug_gemm(hylu_handle* h, int32_t* pair_cnt, int32_t* gd_done, int32_t* walk_done, int32_t* status,
+                    int32_t* block_prog, int32_t* nblocks);
+
+/* Diagnostics: resident blocks per SM on the current device of the FP64
+ * factor kernel (out4[0]), of the FP32 one (out4[1]) and of its tensor-core
+ * variant (out4[2]); out4[3] = that variant's registers per thread * 10000 +
+ * shared bytes per block / 16. */
+int hylu_debug_occupancy(int* out4);
+
 /* Number of kernel launches this library has issued since it was loaded (a
  * graph replay counts the kernels recorded in it; recording counts none). */
 int64_t hylu_launch_count(void);

@@ -100,6 +100,8 @@ def load():
     lib.hylu_launch_count.restype = C.c_int64
     lib.hylu_launch_count.argtypes = []
     lib.hylu_measure_fp64_peak.argtypes = [C.POINTER(C.c_double), C.c_void_p]
+    lib.hylu_debug_gemm.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.POINTER(C.c_int32)]
     lib.hylu_export_gemm_plan.argtypes = [H, C.c_int, C.c_void_p, C.POINTER(C.c_int64)]
     lib.hylu_split_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                     C.c_int, C.c_int, C.c_int, C.c_void_p]
@@ -264,6 +266,18 @@ def hylu_export_gemm_plan(h: int, min_rows: int, n: int) -> dict:
         m = cnt[size] if cnt["ngd"] else 0
         out[name] = buf[pos:pos + m]
         pos += m
+    return out
+
+
+def hylu_debug_gemm(h: int, npair: int, ngd: int, n: int) -> dict:
+    """Counters of the tensor-core sup-sup path after a factorization."""
+    out = {"pair_cnt": np.zeros(npair, np.int32), "gd_done": np.zeros(ngd, np.int32),
+           "walk_done": np.zeros(n, np.int32), "status": np.zeros(16, np.int32)}
+    nb = C.c_int32(0)
+    prog = np.zeros(4 * 4096, np.int32)
+    _check(load().hylu_debug_gemm(h, *(out[k].ctypes.data for k in ("pair_cnt", "gd_done", "walk_done", "status")),
+                                  prog.ctypes.data, C.byref(nb)), "hylu_debug_gemm")
+    out["block_prog"] = prog[:4 * nb.value].reshape(-1, 4)
     return out
 
 

@@ -120,6 +120,8 @@ int upload_gemm(hylu_handle* h, cudaStream_t st) {
     d.tmaps = nullptr;
     if (h->opt.precision != 1 || h->opt.gemm_min_rows <= 0) return HYLU_OK;
     if (!hylu::tensor_maps_available() || !hylu::gemm_smem_fits()) return HYLU_OK;
+    const int tc_blocks = hylu::tc_grid(h->device);
+    if (tc_blocks < 1) return HYLU_OK;
     hylu::GemmPlan G;
     if (hylu::build_gemm_plan(h->P, h->opt.gemm_min_rows, G) != 0) return HYLU_ERR_INTERNAL;
     if (G.ngd == 0 || G.task_pair.empty()) return HYLU_OK;
@@ -149,6 +151,12 @@ int upload_gemm(hylu_handle* h, cudaStream_t st) {
     d.pair_x_off = pxo; d.xmap = xm; d.gd_slot = gs; d.gt_pair = tp; d.gt_mt = tm; d.gt_jt = tj;
     d.diag_row = dr;
     d.row_order = ro;
+    d.gemm_prog = nullptr;
+    if (h->opt.debug & 2) {
+        TRY(dalloc(h, &d.gemm_prog, 4 * (size_t)std::max(1, h->grid)));
+        if (cudaMemsetAsync(d.gemm_prog, 0xff, sizeof(int32_t) * 4 * (size_t)std::max(1, h->grid), st) != cudaSuccess)
+            return HYLU_ERR_CUDA;
+    }
     TRY(dalloc(h, &d.pair_cnt, G.pair_gd.size()));
     TRY(dalloc(h, &d.gd_done, G.ngd));
     TRY(dalloc(h, &d.walk_done, h->P.n));
@@ -160,6 +168,7 @@ int upload_gemm(hylu_handle* h, cudaStream_t st) {
     TRY(upload(h, &dm, maps, st));
     d.tmaps = dm;
     d.n_gd = G.ngd;
+    d.gemm_blocks = tc_blocks;
     d.n_pair = (int32_t)G.pair_gd.size();
     d.n_gtask = (int32_t)G.task_pair.size();
     d.n_diag = (int32_t)G.diag_row.size();
@@ -291,7 +300,7 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     TRY(dalloc(h, &d.tile_b, P.n));
     TRY(dalloc(h, &d.dinv, P.n));
     TRY(dalloc(h, &d.status, hylu::ST_WORDS));
-    h->grid = hylu::factor_grid(h->device);
+    h->grid = hylu::factor_grid(h->device, h->opt.precision == 1);
     TRY(upload_gemm(h, st));
     {
         int sms = 0;
@@ -375,9 +384,6 @@ int do_factor(hylu_handle* h, const double* d_vals, cudaStream_t st) {
     if (cudaMemcpyAsync(h->d_avals, d_vals, sizeof(double) * h->P.nnz_a, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
         return HYLU_ERR_CUDA;
     TRY(hylu::launch_reset(h->dp.status, h->dp.piv, h->dp.pinv, h->dp.gens, h->P.n, st));
-    // blocks of the factor launch that run the tensor-core GEMM tasks (one
-    // in eight; the rest take rows)
-    h->dp.gemm_blocks = h->dp.n_gd > 0 ? std::max(1, std::min(h->dp.n_gtask, h->grid / 8)) : 0;
     TRY(hylu::launch_factor(h->dp, h->d_avals, h->P.nnz_a, h->opt.pivot_tau,
                             h->opt.spin_limit, h->grid, st, h->opt.timing ? h->ev[0] : nullptr,
                             h->opt.timing ? h->ev[1] : nullptr));
@@ -955,6 +961,29 @@ int hylu_debug_trace(hylu_handle* h, unsigned long long* out) {
     if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemcpy(out, h->dp.trace, sizeof(unsigned long long) * 4 * (size_t)h->P.n, cudaMemcpyDeviceToHost) != cudaSuccess)
         return HYLU_ERR_CUDA;
+    return HYLU_OK;
+}
+
+int hylu_debug_occupancy(int* out4) {
+    if (!out4) return HYLU_ERR_ARG;
+    hylu::factor_occupancy(out4, out4 + 1, out4 + 2, out4 + 3);
+    return HYLU_OK;
+}
+
+int hylu_debug_gemm(hylu_handle* h, int32_t* pair_cnt, int32_t* gd_done, int32_t* walk_done, int32_t* status,
+                    int32_t* block_prog, int32_t* nblocks) {
+    if (!h) return HYLU_ERR_ARG;
+    const hylu::DevPlan& d = h->dp;
+    if (!h->uploaded || d.n_gd == 0) return HYLU_ERR_STATE;
+    if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
+    auto get = [](int32_t* dst, const int32_t* src, size_t n) {
+        return !dst || cudaMemcpy(dst, src, sizeof(int32_t) * n, cudaMemcpyDeviceToHost) == cudaSuccess;
+    };
+    if (!get(pair_cnt, d.pair_cnt, d.n_pair) || !get(gd_done, d.gd_done, d.n_gd) ||
+        !get(walk_done, d.walk_done, h->P.n) || !get(status, d.status, hylu::ST_WORDS))
+        return HYLU_ERR_CUDA;
+    if (nblocks) *nblocks = d.gemm_prog ? d.gemm_blocks : 0;
+    if (block_prog && d.gemm_prog && !get(block_prog, d.gemm_prog, 4 * (size_t)d.gemm_blocks)) return HYLU_ERR_CUDA;
     return HYLU_OK;
 }
 

@@ -170,6 +170,10 @@ struct WarpSmem {
 };
 template <typename T>
 constexpr size_t factor_smem() { return sizeof(WarpSmem<T>) * FWARPS; }
+// The precision form with tensor-core sup-sup tasks: a kernel holding
+// tcgen05 instructions gets one block per SM, so that variant runs one large
+// block per SM: TC_ROWW row warps, then one warpgroup of 4 GEMM warps.
+constexpr int TC_ROWW = 12;
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;
@@ -335,8 +339,7 @@ __device__ bool tail_task(const DevPlan& P, int t, int gen, long long limit, War
 
 
 // ------------------------------------------------ tensor-core sup-sup tasks
-// The last P.gemm_blocks blocks of the precision-form factor launch run the
-// GEMM tasks (Sec. 2.2, Fig. 1c, sup-sup): for a pair (destination D, source
+// P.gemm_blocks blocks of the precision-form factor launch run the GEMM tasks (Sec. 2.2, Fig. 1c, sup-sup): for a pair (destination D, source
 // supernode S), one 128-row tile of D and 64 entries of S's tail at or past
 // D's first row,
 //     X_D[rows, T_S cols] -= L_{D,S}[rows, :] * U_{S, T_S cols}
@@ -347,18 +350,26 @@ __device__ bool tail_task(const DevPlan& P, int t, int gen, long long limit, War
 // rows at the U-column index of each tail entry (FP32 reductions: the rows
 // add their updates from small sources to the same entries).  A task waits,
 // bounded, until every row of D that holds S has written its multipliers;
-// the last task of D lets D's diag tasks start.
+// the last task of D lets D's diag tasks start.  The first blocks of the
+// launch to start take this role (an atomic ticket, not the block index):
+// the rows wait on these tasks, so they must be among the resident blocks.
 struct GemmSmem {
     tc::TileSmem<3> t;
     int xm[tc::TN];      // U-column index in D of the tile's tail entries
     int task;
 };
 
-__device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw, long long limit) {
+// the GEMM warpgroup's own barrier (the block's row warps never join it)
+__device__ __forceinline__ void gemm_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw, int rank, int tid,
+                                       long long limit) {
     const uintptr_t base = (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023);
     GemmSmem& G = *reinterpret_cast<GemmSmem*>(base);
     tc::TileSmem<3>& sm = G.t;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // warps of the group are the block's last four: warp % 4 gives the TMEM
+    // lane quarter each may read, rows warp*32 .. of the tile
+    const int warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
         tc::mbar_init(&sm.bar_tma, 1);
         tc::mbar_init(&sm.bar_mma, 1);
@@ -367,16 +378,21 @@ __device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw
     }
     if (warp == 0) tc::tmem_alloc(&sm.tmem_base, tc::TMEM_COLS);
     tc::tc_fence_before();
-    __syncthreads();
+    gemm_bar();
     tc::tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
     const CUtensorMap* maps = static_cast<const CUtensorMap*>(P.tmaps);
     // an mbarrier try_wait may suspend for a while by itself: fewer tries
     const long long mlimit = limit < (1LL << 22) ? limit : (1LL << 22);
     uint32_t ph_tma = 0, ph_mma = 0;
+    int32_t* prog = P.gemm_prog ? P.gemm_prog + 4 * rank : nullptr;
+    auto stage = [&](int st, int c) {
+        if (prog && tid == 0) { prog[1] = st; prog[2] = c; __threadfence(); }
+    };
     for (;;) {
         if (tid == 0) {
             int q = atomicAdd(P.status + ST_CNT_G, 1);
+            if (prog) { prog[0] = q; prog[1] = 1; prog[2] = 0; prog[3] = (int32_t)(gtimer() >> 10); }
             if (q >= P.n_gtask || ld_relaxed(P.status + ST_ERR) != 0) q = -1;
             G.task = q;
             if (q >= 0) {
@@ -396,11 +412,19 @@ __device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw
                 // the multipliers were written through the generic proxy;
                 // the tensor copies below read them through the async proxy
                 asm volatile("fence.proxy.async.global;" ::: "memory");
+                // the tensor maps were copied to global memory by the host:
+                // make them visible to the tensor-map proxy before use
+                const CUtensorMap* mp = maps + 3 * P.pair_gd[p];
+                for (int s = 0; s < 3; ++s)
+                    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
+                                     reinterpret_cast<uint64_t>(mp + s))
+                                 : "memory");
             }
         }
-        __syncthreads();
+        gemm_bar();
         const int q = G.task;
         if (q < 0) break;
+        stage(2, 0);
         const int p = P.gt_pair[q], mt = P.gt_mt[q], jt = P.gt_jt[q];
         const int g = P.pair_gd[p], D = P.gd_node[g], S = P.pair_src[p];
         const int rD = P.sn_start[D], sD = P.sn_start[D + 1] - rD;
@@ -423,6 +447,7 @@ __device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw
                         tc::tma_load_2d(&sm.a[s][j * tc::KB * tc::TM], maps + 3 * g + s,
                                         u0 + c * tc::TK + j * tc::KB, mt * tc::TM, &sm.bar_tma);
             }
+            stage(3, c);
             // B: positions c*TK .. of S (rows of its panel), the tile's tail entries
             for (int e2 = tid; e2 < tc::TK * tc::TN; e2 += 128) {
                 const int k = e2 / tc::TN, t = e2 % tc::TN;
@@ -434,7 +459,8 @@ __device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw
                     *reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(sm.b[s]) + tc::b_off(t, k)) = h3[s];
             }
             tc::fence_async_smem();
-            __syncthreads();
+            gemm_bar();
+            stage(4, c);
             if (tid == 0) {
                 if (!tc::mbar_wait(&sm.bar_tma, ph_tma, mlimit)) {
                     sm.abort = 1;
@@ -447,7 +473,8 @@ __device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw
                 }
             }
             ph_tma ^= 1u;
-            __syncthreads();
+            stage(5, c);
+            gemm_bar();
             if (sm.abort) { ok = false; break; }
             if (!tc::mbar_wait(&sm.bar_mma, ph_mma, mlimit)) {
                 if (tid == 0) atomicCAS(P.status + ST_ERR, 0, HYLU_ERR_DEVICE_TIMEOUT);
@@ -455,10 +482,12 @@ __device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw
                 sm.abort = 1;
             }
             ph_mma ^= 1u;
-            __syncthreads();
+            stage(6, c);
+            gemm_bar();
             if (sm.abort) { ok = false; break; }
         }
         if (!ok) break;
+        stage(7, 0);
         // epilogue: this warp's 32 TMEM lanes are rows mt*128 + warp*32 + lane
         tc::tc_fence_after();
         const int m = mt * tc::TM + warp * 32 + lane;
@@ -474,35 +503,41 @@ __device__ __noinline__ void gemm_role(const DevPlan& P, unsigned char* smem_raw
             }
         }
         tc::tc_fence_before();
-        __syncthreads();
+        gemm_bar();
         if (tid == 0) {
             __threadfence();
             atomicAdd(P.gd_done + g, 1);
         }
+        stage(8, 0);
     }
     tc::tc_fence_before();
-    __syncthreads();
+    gemm_bar();
     if (warp == 0) tc::tmem_dealloc(tmem, tc::TMEM_COLS);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(FWARPS * 32, 4)
+// RW row warps per block; TC: the block's last four warps run the GEMM
+// tasks (the tensor-core variant of the precision form, one block per SM).
+template <typename T, int RW, bool TC>
+__global__ void __launch_bounds__((RW + (TC ? 4 : 0)) * 32, TC ? 1 : 4)
 factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
               double tau_rel, long long limit) {
     const int gen = P.gens[0];
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if (P.gemm_blocks > 0 && (int)blockIdx.x >= (int)gridDim.x - P.gemm_blocks) {
-        if constexpr (sizeof(T) == 4) gemm_role(P, smem_raw, limit);
-        return;
+    if constexpr (TC) {
+        if ((int)(threadIdx.x >> 5) >= RW) {
+            gemm_role(P, smem_raw + sizeof(WarpSmem<T>) * RW, blockIdx.x, threadIdx.x - RW * 32, limit);
+            return;
+        }
     }
-    const int nrowblk = (int)gridDim.x - P.gemm_blocks;
+    const int nrowblk = (int)gridDim.x;
+    constexpr int HW = HEAVY_WPB * RW / FWARPS;   // warps of every block that take the heavy rows first
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     WarpSmem<T>* ws = reinterpret_cast<WarpSmem<T>*>(smem_raw) + wid;
     T* lb = ws->lb;
     int* pb = ws->pb;
     T* win = ws->win;
     int* wcol = ws->wcol;
-    int* pos_warp = P.pos + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.pos_n;
+    int* pos_warp = P.pos + (size_t)(blockIdx.x * RW + wid) * (size_t)P.pos_n;
     const double amax = __longlong_as_double(*reinterpret_cast<const long long*>(P.status + ST_AMAX));
     const double tau = tau_rel * amax;
     // Rows are claimed from two queues, each in dependency-level order.  The
@@ -513,12 +548,12 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
     // skips the heavy rows.  Progress holds: a claimed row waits only on rows
     // of lower levels, and the lowest-level unfinished row is either claimed,
     // or next in its queue, whose claimed rows are all ready.
-    bool heavy_open = (P.n_heavy > 0) && (wid < HEAVY_WPB);
+    bool heavy_open = (P.n_heavy > 0) && (wid < HW);
     bool main_open = true;
     // early claiming pays only when every heavy row gets a warp at once; with
     // more heavy rows than heavy warps (batches of many systems) they would
     // hold warps while waiting on their own chains: plain level order instead
-    const int hcap = ((int64_t)P.n_heavy <= (int64_t)HEAVY_WPB * nrowblk) ? P.n_heavy : 0;
+    const int hcap = ((int64_t)P.n_heavy <= (int64_t)HW * nrowblk) ? P.n_heavy : 0;
     heavy_open = heavy_open && hcap > 0;
     for (;;) {
         int i = -1;
@@ -593,7 +628,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         //      (also used by a panel kept in global memory).
         //      A row with a long L list keeps its pending L values in a dense
         //      per-warp vector indexed by column instead (no slot lookup).
-        T* spa = (nL > DENSE_L_MIN && SPA<T>(P)) ? SPA<T>(P) + (size_t)(blockIdx.x * FWARPS + wid) * (size_t)P.pos_n
+        T* spa = (nL > DENSE_L_MIN && SPA<T>(P)) ? SPA<T>(P) + (size_t)(blockIdx.x * RW + wid) * (size_t)P.pos_n
                                                       - (P.node_base ? P.node_base[D] : 0)
                                                  : nullptr;
         //      Such a row with its U part in global memory (mode 2) also
@@ -1663,12 +1698,27 @@ static int check(const char* what) {
 int warps_per_block() { return FWARPS; }
 int dense_l_min() { return DENSE_L_MIN; }
 
-int factor_grid(int device) {
+constexpr size_t tc_smem() { return sizeof(WarpSmem<float>) * TC_ROWW + sizeof(GemmSmem) + 1024; }
+
+void set_smem_attrs() {
+    cudaFuncSetAttribute(factor_kernel<double, FWARPS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem<double>());
+    cudaFuncSetAttribute(factor_kernel<float, FWARPS, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)factor_smem<float>());
+    cudaFuncSetAttribute(factor_kernel<float, TC_ROWW, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)tc_smem());
+}
+
+int factor_grid(int device, bool fp32) {
     int sms = 0, per = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    cudaFuncSetAttribute(factor_kernel<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)factor_smem<double>());
-    cudaFuncSetAttribute(factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)factor_smem<float>());
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel<double>, FWARPS * 32, factor_smem<double>());
+    set_smem_attrs();
+    if (fp32)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel<float, FWARPS, false>, FWARPS * 32,
+                                                      factor_smem<float>());
+    else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel<double, FWARPS, false>, FWARPS * 32,
+                                                      factor_smem<double>());
     if (per < 1) per = 1;
     if (per > 4) per = 4;
     return sms * per;
@@ -1682,7 +1732,29 @@ int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t* gens, in
     return check("reset");
 }
 
-int gemm_smem_fits() { return sizeof(GemmSmem) + 1023 <= factor_smem<float>(); }
+void factor_occupancy(int* per64, int* per32, int* per_tc, int* regs_tc) {
+    cudaFuncAttributes a{};
+    set_smem_attrs();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(per64, factor_kernel<double, FWARPS, false>, FWARPS * 32,
+                                                  factor_smem<double>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(per32, factor_kernel<float, FWARPS, false>, FWARPS * 32,
+                                                  factor_smem<float>());
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_tc, factor_kernel<float, TC_ROWW, true>, (TC_ROWW + 4) * 32,
+                                                  tc_smem());
+    cudaFuncGetAttributes(&a, factor_kernel<float, TC_ROWW, true>);
+    *regs_tc = a.numRegs * 10000 + (int)(a.sharedSizeBytes + tc_smem()) / 16;
+}
+
+int gemm_smem_fits() { return tc_smem() <= 227 * 1024; }
+
+int tc_grid(int device) {
+    int sms = 0, per = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+    set_smem_attrs();
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, factor_kernel<float, TC_ROWW, true>, (TC_ROWW + 4) * 32,
+                                                  tc_smem());
+    return sms * std::max(per, 0);
+}
 
 int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a,
                   double tau_rel, long long spin_limit, int grid, cudaStream_t st, cudaEvent_t e0,
@@ -1702,10 +1774,15 @@ int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a,
     amax_kernel<<<blocks, 256, 0, st>>>(d_vals, P.ah_src, P.ah_scale, nnz_a, P.status);
     count_launch();
     if (e0) cudaEventRecord(e0, st);
-    if (P.lval32)
-        factor_kernel<float><<<grid, FWARPS * 32, factor_smem<float>(), st>>>(P, d_vals, P.dinv32, tau_rel, spin_limit);
+    if (P.lval32 && P.n_gd > 0)
+        factor_kernel<float, TC_ROWW, true><<<P.gemm_blocks, (TC_ROWW + 4) * 32, tc_smem(), st>>>(
+            P, d_vals, P.dinv32, tau_rel, spin_limit);
+    else if (P.lval32)
+        factor_kernel<float, FWARPS, false><<<grid, FWARPS * 32, factor_smem<float>(), st>>>(P, d_vals, P.dinv32,
+                                                                                            tau_rel, spin_limit);
     else
-        factor_kernel<double><<<grid, FWARPS * 32, factor_smem<double>(), st>>>(P, d_vals, P.dinv, tau_rel, spin_limit);
+        factor_kernel<double, FWARPS, false><<<grid, FWARPS * 32, factor_smem<double>(), st>>>(P, d_vals, P.dinv,
+                                                                                              tau_rel, spin_limit);
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     return check("factor");

@@ -14,9 +14,9 @@ namespace hylu {
 //   [6..7] max |Ahat| as the bit pattern of a non-negative double.
 //   [8..9] substitution: forward / backward claim counters ([10..11] unused).
 //   [12] task counter of the factor kernel's heavy-row queue, [13] of its
-//   tensor-core GEMM queue.
+//   tensor-core GEMM queue ([14..15] unused).
 enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_AMAX = 6, ST_CNT_FWD = 8,
-       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_CNT_H = 12, ST_CNT_G = 13, ST_WORDS = 14 };
+       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_CNT_H = 12, ST_CNT_G = 13, ST_WORDS = 16 };
 
 struct DevPlan {
     int32_t n, nnodes;
@@ -91,8 +91,9 @@ struct DevPlan {
     const int32_t* heavy_rank;     // per row: rank in heavy_order, INT32_MAX if not heavy
     int32_t n_heavy;
     // precision form, tensor-core sup-sup update (GemmPlan on the host;
-    // n_gd == 0: off).  The last gemm_blocks blocks of the factor launch run
-    // the GEMM tasks; the rows' queue then also holds n_diag diag tasks.
+    // n_gd == 0: off).  The factor launch is then gemm_blocks blocks (one
+    // per SM), each with row warps and one warpgroup that runs the GEMM
+    // tasks; the rows' queue also holds n_diag diag tasks.
     int32_t n_gd, n_gtask, n_diag, gemm_blocks, n_pair;
     int64_t a_elems;               // elements of each split-term array
     const int32_t* gd_of_node;     // node -> destination, or -1
@@ -119,6 +120,7 @@ struct DevPlan {
     uint16_t* a_term[3];           // L_{D,S} split into three BF16 terms (raw bits), per destination
                                    //   an Mp x Kp row-major block (zeroed per factor)
     const void* tmaps;             // TMA tensor maps, 3 per destination (term-major inside), device memory
+    int32_t* gemm_prog;            // diagnostics (debug & 2): per GEMM block, task / stage / chunk / tries
     unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, waits / node complete)
     int32_t* status;
     // [0] factor generation, [1] substitution generation: the flags above
@@ -146,7 +148,7 @@ int launch_residual(int32_t n, const int64_t* rp, const int32_t* ci, const doubl
                     const double* b, double* r, double* norms, int nrhs, int ld, cudaStream_t st);
 int launch_axpy(int32_t n, double* x, const double* d, int nrhs, int ld, cudaStream_t st);
 int launch_reset(int32_t* status, int32_t* piv, int32_t* pinv, int32_t* gens, int32_t n, cudaStream_t st);
-int factor_grid(int device);   // blocks of the persistent kernels
+int factor_grid(int device, bool fp32 = false);   // blocks of the persistent kernels
 int warps_per_block();
 int dense_l_min();
 int64_t launches();
@@ -159,6 +161,8 @@ int encode_a_maps(int32_t ngd, const int32_t* Mp, const int32_t* Kp, const int64
                   void* out);
 size_t tensor_map_bytes();
 int gemm_smem_fits();          // the tile engine fits the factor kernel's shared memory
+void factor_occupancy(int* per64, int* per32, int* per_tc, int* regs_tc);
+int tc_grid(int device);       // blocks of the tensor-core variant of the factor launch (0: it cannot run)
 void count_launch();
 void add_launches(int64_t k);
 

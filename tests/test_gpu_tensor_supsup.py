@@ -48,6 +48,16 @@ def _dense_lu(prp, pci, vals, piv, sn):
     return L, U
 
 
+def _info(s):
+    """hylu_get_info without raising on a device status, so that a failure
+    shows the node or row where a wait expired."""
+    import ctypes as C
+    from paper_2509_07690_gb300 import capi
+    info = capi.Info()
+    capi.load().hylu_get_info(s.h, C.byref(info))
+    return info
+
+
 CASES = [("convdiff_12_nd", 4), ("convdiff_12_nd", 64), ("aniso_32_nd", 8), ("grid5_30", 4), ("circuit_2000", 4)]
 
 
@@ -72,8 +82,8 @@ def test_tensor_supsup_matches_oracle(name, min_rows):
     for vals in (A.val, vals2):                   # factor, then refactor with new values
         s.factor(torch.from_numpy(vals).cuda())
         ref.factor(torch.from_numpy(vals).cuda())
-        info = s.get_info()
-        assert info.device_status == 0
+        info = _info(s)
+        assert info.device_status == 0, (info.device_status, info.failed_node)
         assert info.gemm_destinations > 0 and info.gemm_tasks > 0
         rp, cp, dr, dc, sn = s.export_perm()
         o = oracle.Oracle(A.n, A.rowptr, A.col, vals, rp, cp, dr, dc)
