@@ -76,6 +76,9 @@ def parse():
                     help="circuit_batch_512: systems in the batch (512 is the configuration)")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"],
                     help="fp32: the precision form (FP32 factors, FP64 refinement on every solve)")
+    ap.add_argument("--gemm-min-rows", type=int, default=None,
+                    help="precision form: smallest supernode that takes its sup-sup updates on the tensor "
+                         "cores (0: off; default: the library's)")
     args = ap.parse_args()
     global WORKLOAD, CIRCUIT_N
     WORKLOAD = args.workload
@@ -593,10 +596,18 @@ def run_hylu(args, ws, rank, local):
     if not (WORKLOAD.startswith("circuit") and args.ordering_trial):
         out = measure_hylu(args, ws, rank, local, ordering)
         if WORKLOAD == "convdiff3d_64" and args.precision == "fp64" and not args.no_precision_form:
+            # the precision form as specified (sup-sup on the tensor cores),
+            # and the same FP32 factorization on CUDA cores only
             gc.collect()
             out32 = measure_hylu(args, ws, rank, local, ordering, fp32=True, sub=True)
+            gc.collect()
+            saved, args.gemm_min_rows = args.gemm_min_rows, 0
+            out32c = measure_hylu(args, ws, rank, local, ordering, fp32=True, sub=True)
+            args.gemm_min_rows = saved
             if out is not None and out32 is not None:
                 out["precision_form"] = precision_summary(out, out32)
+            if out is not None and out32c is not None:
+                out["precision_form_cuda_cores"] = precision_summary(out, out32c)
         if out is not None:
             print(json.dumps(out), flush=True)
         return 0
@@ -638,7 +649,8 @@ def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fal
     A, sets, b = make_inputs(args.n, args.scale)
     if fp32 is None:
         fp32 = args.precision == "fp32"
-    s = Solver(A.n, A.rowptr, A.col, A.val, timing=1, ordering=ordering, precision=1 if fp32 else 0)
+    extra = {} if args.gemm_min_rows is None else {"gemm_min_rows": args.gemm_min_rows}
+    s = Solver(A.n, A.rowptr, A.col, A.val, timing=1, ordering=ordering, precision=1 if fp32 else 0, **extra)
     info = s.info
     flops = info.flops
     d_sets = [torch.from_numpy(v.val).to(dev) for v in sets]
@@ -756,6 +768,7 @@ def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fal
             "solve_ms": statistics.mean(solve_ms),
             "nperturb": inf.nperturb,
             "refine_iters": inf.refine_iters,
+            "tensor_supsup": tensor_summary(inf, kmean) if fp32 else None,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gflops / 1e3,
                          "unit": "TFLOP/s", "frac": achieved * 1e3 / peak_gflops,
                          "traffic": profiled_traffic(WORKLOAD, fp32), "kernel": "factor_kernel",
@@ -793,6 +806,26 @@ def measure_hylu(args, ws, rank, local, ordering: int, strict: bool = False, fal
     return None
 
 
+def measured_bf16_tflops() -> float:
+    """Measured dense BF16 tensor throughput (MEASURED_PEAKS.json), else 1900."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
+def tensor_summary(inf, kernel_ms: float) -> dict:
+    """The precision form's tensor-core sup-sup tasks: how many, their useful
+    FP32 flops (2 per multiply-add of L_{D,S} U_{S,T}) and the BF16 tensor
+    flops those take (six term products each), as a rate over the factor
+    kernel's time against the measured BF16 peak."""
+    bf16 = 6.0 * inf.gemm_flops
+    rate = bf16 / (kernel_ms * 1e-3) / 1e12 if kernel_ms > 0 else 0.0
+    return {"destinations": inf.gemm_destinations, "tasks": inf.gemm_tasks, "useful_fp32_flops": inf.gemm_flops,
+            "bf16_flops": bf16, "bf16_tflops_over_factor_kernel": rate, "bf16_peak_tflops": measured_bf16_tflops(),
+            "tensor_frac": rate / measured_bf16_tflops(), "products_per_fp32_product": 6}
+
+
 def precision_summary(fp64: dict, fp32: dict) -> dict:
     """The precision form measured on the same matrix, against the FP64 line:
     factor and step times (the FP32 step includes its FP64 refinement), the
@@ -800,7 +833,7 @@ def precision_summary(fp64: dict, fp32: dict) -> dict:
     return {"precision": fp32["config"]["precision"], "factor_ms": fp32["value"],
             "ms_per_step": fp32["ms_per_step"], "gflops": fp32["gflops"], "solve_ms": fp32["solve_ms"],
             "refine_iters": fp32["refine_iters"], "backward_error": fp32["backward_error"],
-            "e2e_ms": fp32["e2e"]["value"], "roofline": fp32["roofline"],
+            "e2e_ms": fp32["e2e"]["value"], "roofline": fp32["roofline"], "tensor_supsup": fp32["tensor_supsup"],
             "speedup_factor_vs_fp64": fp64["value"] / fp32["value"],
             "speedup_step_vs_fp64": fp64["ms_per_step"] / fp32["ms_per_step"],
             "gpu_launches": fp32["gpu_launches"], "clocks": fp32["clocks"]}

@@ -84,10 +84,11 @@ typedef struct {
     double heavy_ratio;    /* rows whose update work is at least heavy_ratio x the mean row (and
                               at least 1e6 flops) are claimed first, from a queue of their own,
                               by two warps of every block; 0 disables (32) */
-    int gemm_min_rows;     /* precision form (precision = 1): supernodes of at least this many rows,
-                              and every node downstream of one, take the updates of their diagonal
-                              block and U tail as split-BF16 tensor-core GEMM tiles (Sec. 2.2,
-                              Fig. 1c, sup-sup); 0 disables (64).  Ignored for FP64 factors. */
+    int gemm_min_rows;     /* precision form (precision = 1): supernodes of at least this many rows
+                              take the updates of their diagonal block and U tail from source
+                              supernodes of at least min(16, gemm_min_rows) rows as split-BF16
+                              tensor-core GEMM tasks (Sec. 2.2, Fig. 1c, sup-sup); 0 disables (64).
+                              Ignored for FP64 factors. */
 } hylu_options;
 
 typedef struct {

@@ -24,19 +24,9 @@ int build_gemm_plan(const Plan& P, int32_t min_rows, GemmPlan& G) {
     auto seg_len = [&](int32_t S) { return P.sn_start[S + 1] - P.sn_start[S]; };
     auto ntask = [&](int32_t S) { return P.node_ntask.empty() ? 0 : P.node_ntask[S]; };
 
-    // ---- destinations: large supernodes and every node downstream of one
+    // ---- destinations: the supernodes of at least min_rows rows
     std::vector<char> is(nn, 0);
-    for (int32_t D = 0; D < nn; ++D) {
-        const int32_t r = P.sn_start[D], e = P.sn_start[D + 1] - 1;
-        bool g = (e - r + 1) >= min_rows;
-        for (int32_t i = r; i <= e && !g; ++i)
-            for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
-                const int32_t S = P.node_of[P.lcols[t]];
-                if (is[S]) { g = true; break; }
-                t += seg_len(S);
-            }
-        is[D] = g;
-    }
+    for (int32_t D = 0; D < nn; ++D) is[D] = seg_len(D) >= min_rows;
     for (int32_t D = 0; D < nn; ++D)
         if (is[D]) {
             G.gd_of_node[D] = G.ngd++;
@@ -107,25 +97,26 @@ int build_gemm_plan(const Plan& P, int32_t min_rows, GemmPlan& G) {
         G.a_elems += (int64_t)G.gd_Mp.back() * kp;
     }
 
-    // ---- levels: nodes before any destination keep theirs; a destination
-    //      row walks after its sources complete, the destination's GEMM tasks
-    //      come after every walk, the diagonal-block steps after the tasks,
-    //      one row per level, and its tail tasks after the last step
+    // ---- levels (Sec. 2.2.1): a row of another node as in the plan (after
+    //      its sources complete and after the previous row of its node); a
+    //      destination row walks after its sources complete, the
+    //      destination's GEMM tasks come after every walk, the diagonal-block
+    //      steps after the tasks, one row per level; tail tasks after the
+    //      node's last row or step
     G.walk_level.assign(n, -1);
     G.diag_level.assign(n, -1);
     std::vector<int32_t> gemm_level(G.ngd, 0);
     auto done_level = [&](int32_t S) {
         const int32_t e = P.sn_start[S + 1] - 1;
-        const int32_t last = is[S] ? G.diag_level[e] : P.row_level[e];
+        const int32_t last = is[S] ? G.diag_level[e] : G.walk_level[e];
         return last + (ntask(S) > 0 ? 1 : 0);
     };
-    int32_t maxl = P.row_levels - 1;
-    for (int32_t g = 0; g < G.ngd; ++g) {
-        const int32_t D = G.gd_node[g];
+    int32_t maxl = 0;
+    for (int32_t D = 0; D < nn; ++D) {
         const int32_t r = P.sn_start[D], e = P.sn_start[D + 1] - 1;
         int32_t lg = 0;
         for (int32_t i = r; i <= e; ++i) {
-            int32_t l = 0;
+            int32_t l = (!is[D] && i > r) ? G.walk_level[i - 1] + 1 : 0;
             for (int64_t t = P.row_lptr[i]; t < P.row_lptr[i + 1];) {
                 const int32_t S = P.node_of[P.lcols[t]];
                 l = std::max(l, done_level(S) + 1);
@@ -134,21 +125,19 @@ int build_gemm_plan(const Plan& P, int32_t min_rows, GemmPlan& G) {
             G.walk_level[i] = l;
             lg = std::max(lg, l + 1);
         }
-        gemm_level[g] = lg;
-        for (int32_t i = r; i <= e; ++i) G.diag_level[i] = (i == r) ? lg + 1 : G.diag_level[i - 1] + 1;
+        if (is[D]) {
+            gemm_level[G.gd_of_node[D]] = lg;
+            for (int32_t i = r; i <= e; ++i) G.diag_level[i] = (i == r) ? lg + 1 : G.diag_level[i - 1] + 1;
+        }
         maxl = std::max(maxl, done_level(D));
+        maxl = std::max(maxl, is[D] ? G.diag_level[e] : G.walk_level[e]);
     }
-    for (int32_t i = 0; i < n; ++i)
-        if (!is[P.node_of[i]]) G.walk_level[i] = P.row_level[i];
     for (int32_t i = 0; i < n; ++i)
         if (G.diag_level[i] >= 0) G.diag_row.push_back(i);
     // rows' queue: tail tasks first inside a level, then diag tasks, then rows
     const int32_t nd = (int32_t)G.diag_row.size();
     std::vector<int32_t> task_lev(P.n_tasks);
-    for (int32_t t = 0; t < P.n_tasks; ++t) {
-        const int32_t S = P.task_node[t];
-        task_lev[t] = is[S] ? G.diag_level[P.sn_start[S + 1] - 1] + 1 : P.task_level[t];
-    }
+    for (int32_t t = 0; t < P.n_tasks; ++t) task_lev[t] = done_level(P.task_node[t]);
     std::vector<int32_t> cnt(maxl + 2, 0);
     for (int32_t t = 0; t < P.n_tasks; ++t) cnt[task_lev[t] + 1]++;
     for (int32_t d = 0; d < nd; ++d) cnt[G.diag_level[G.diag_row[d]] + 1]++;

@@ -138,8 +138,7 @@ int save_plan(const Plan& P, const BatchLayout& B, bool batch, const hylu_option
 int load_plan(const uint8_t* buf, size_t bytes, Plan& P, BatchLayout& B, bool& batch, hylu_options& opt);
 
 // Tensor-core tables of the precision form (gemm_plan.cpp).  A supernode of
-// at least min_rows rows, and every node with such a node (or one
-// downstream of it) among its sources, is a GEMM destination D.  Its rows
+// at least min_rows rows is a GEMM destination D.  Its rows
 // walk their sources as other rows do, but for a large source supernode S
 // (at least min_src = min(16, max(2, min_rows)) rows) a row only computes
 // its multipliers L(i, S) (the triangular solve with S's diagonal block)

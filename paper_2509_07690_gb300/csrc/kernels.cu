@@ -173,7 +173,7 @@ constexpr size_t factor_smem() { return sizeof(WarpSmem<T>) * FWARPS; }
 // The precision form with tensor-core sup-sup tasks: a kernel holding
 // tcgen05 instructions gets one block per SM, so that variant runs one large
 // block per SM: TC_ROWW row warps, then one warpgroup of 4 GEMM warps.
-constexpr int TC_ROWW = 12;
+constexpr int TC_ROWW = 16;
 
 __device__ __forceinline__ unsigned long long gtimer() {
     unsigned long long t;

@@ -1,7 +1,7 @@
 """Host tables of the precision form's tensor-core sup-sup update (HYLU
 Sec. 2.2, Fig. 1c), rebuilt here by brute force from the exported padded
-pattern and compared entry by entry: the destination set (large supernodes
-and everything downstream of one),
+pattern and compared entry by entry: the destination set (the supernodes of
+at least gemm_min_rows rows),
 the (destination, large source) pairs with their A columns, tail ranges and
 U-column maps, the pair named at each L slot, the GEMM task list, and the
 claim order (every task after everything it waits on)."""
@@ -37,9 +37,7 @@ def _brute(s, min_rows):
     lcols = [rows[i][rows[i] < sn[node_of[i]]] for i in range(n)]
     tail = [rows[sn[S]][rows[sn[S]] >= sn[S + 1]] for S in range(nn)]
     src = [sorted({int(node_of[k]) for i in range(sn[D], sn[D + 1]) for k in lcols[i]}) for D in range(nn)]
-    is_gd = np.zeros(nn, bool)
-    for D in range(nn):
-        is_gd[D] = (sn[D + 1] - sn[D]) >= min_rows or any(is_gd[S] for S in src[D])
+    is_gd = np.diff(sn) >= min_rows
     return dict(n=n, sn=sn, node_of=node_of, lcols=lcols, tail=tail, src=src, is_gd=is_gd)
 
 
@@ -155,6 +153,7 @@ def test_gemm_claim_order_respects_dependencies(name, A, opts):
             assert where[i] > max(complete(S)), (i, S)
         if D not in gd_of and i > sn[D]:
             assert where[i] > where[i - 1]
+        assert G["walk_level"][i] >= 0
     for D, g in gd_of.items():
         r, e = sn[D], sn[D + 1] - 1
         if g not in gemm_level:
