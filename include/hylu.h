@@ -388,6 +388,12 @@ int hylu_debug_trace(hylu_handle* h, unsigned long long* out);
 int hylu_debug_gemm(hylu_handle* h, int32_t* pair_cnt, int32_t* gd_done, int32_t* walk_done, int32_t* status,
                     int32_t* block_prog, int32_t* nblocks);
 
+/* Diagnostics: when the handle was analysed with (opt.debug & 4), copy the
+ * completion time (ns of %globaltimer) of every node in the last forward
+ * (out[2 * node]) and backward (out[2 * node + 1]) substitution to the HOST
+ * array out[2 * nnodes].  HYLU_ERR_STATE when that tracing is off. */
+int hylu_debug_solve_trace(hylu_handle* h, unsigned long long* out);
+
 /* Diagnostics: resident blocks per SM on the current device of the FP64
  * factor kernel (out4[0]), of the FP32 one (out4[1]) and of its tensor-core
  * variant (out4[2]); out4[3] = that variant's registers per thread * 10000 +

@@ -221,6 +221,12 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     }
     d.trace = nullptr;
     if (h->opt.debug & 2) TRY(dalloc(h, &d.trace, 4 * (size_t)P.n));
+    d.strace = nullptr;
+    if (h->opt.debug & 4) {
+        TRY(dalloc(h, &d.strace, 2 * (size_t)std::max(1, P.nnodes)));
+        if (cudaMemsetAsync(d.strace, 0, sizeof(unsigned long long) * 2 * std::max(1, P.nnodes), st) != cudaSuccess)
+            return HYLU_ERR_CUDA;
+    }
     d.lval = nullptr; d.pval = nullptr; d.lval32 = nullptr; d.pval32 = nullptr; d.dinv32 = nullptr;
     if (h->opt.precision == 1) {
         TRY(dalloc(h, &d.lval32, P.nnz_l));
@@ -259,6 +265,30 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
         d.n_bwd_levels = (int32_t)P.bwd_count.size();
         TRY(dalloc(h, &d.fwd_done, P.fwd_count.size()));
         TRY(dalloc(h, &d.bwd_done, P.bwd_count.size()));
+        // split points of the substitution's dot products: the entries whose
+        // sources lie two or more levels below the row's own
+        {
+            std::vector<int32_t> fs(P.n, 0), bs(P.nnodes, 0);
+            for (int32_t D = 0; D < P.nnodes; ++D) {
+                const int32_t L = P.fwd_level[D];
+                for (int32_t i = P.sn_start[D]; i < P.sn_start[D + 1]; ++i) {
+                    int64_t t = P.row_lptr[i];
+                    while (t < P.row_lptr[i + 1] && P.fwd_level[P.node_of[P.lcols[t]]] <= L - 2) ++t;
+                    fs[i] = (int32_t)(t - P.row_lptr[i]);
+                }
+                const int32_t Lb = P.bwd_level[D];
+                const int64_t a = P.node_tail_off[D];
+                int64_t sp = P.node_tail_off[D + 1];
+                while (sp > a && P.bwd_level[P.node_of[P.tcols[sp - 1]]] <= Lb - 2) --sp;
+                bs[D] = (int32_t)(sp - a);
+            }
+            int32_t *dfs, *dbs;
+            TRY(upload(h, &dfs, fs, st));
+            TRY(upload(h, &dbs, bs, st));
+            if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;   // fs, bs go out of scope
+            d.fwd_split = dfs;
+            d.bwd_split = dbs;
+        }
         int32_t *uo, *lo, *ul, *ll, *uc, *lcn;
         TRY(upload(h, &uo, P.ut_order, st));
         TRY(upload(h, &lo, P.lt_order, st));
@@ -960,6 +990,16 @@ int hylu_debug_trace(hylu_handle* h, unsigned long long* out) {
     if (!h->dp.trace) return HYLU_ERR_STATE;
     if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemcpy(out, h->dp.trace, sizeof(unsigned long long) * 4 * (size_t)h->P.n, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return HYLU_ERR_CUDA;
+    return HYLU_OK;
+}
+
+int hylu_debug_solve_trace(hylu_handle* h, unsigned long long* out) {
+    if (!h || !out) return HYLU_ERR_ARG;
+    if (!h->dp.strace) return HYLU_ERR_STATE;
+    if (cudaStreamSynchronize(h->last) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemcpy(out, h->dp.strace, sizeof(unsigned long long) * 2 * (size_t)h->P.nnodes, cudaMemcpyDeviceToHost) !=
+        cudaSuccess)
         return HYLU_ERR_CUDA;
     return HYLU_OK;
 }

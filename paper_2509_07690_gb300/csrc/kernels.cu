@@ -1131,9 +1131,10 @@ __device__ __forceinline__ bool wait_level(const int* wm, int need, int& cached,
 }
 
 
-// called by lane 0 after the node's results are written and fenced
+// called by lane 0 after the node's results are written and fenced; a
+// level of one node raises the watermark without the counter's round trip
 __device__ __forceinline__ void node_complete(int* done, const int* count, int L, int* wm) {
-    if (atom_add_acq_rel(done + L, 1) + 1 == count[L]) st_release(wm, L + 1);
+    if (count[L] == 1 || atom_add_acq_rel(done + L, 1) + 1 == count[L]) st_release(wm, L + 1);
 }
 
 // Dense block of a supernode in the substitution, by 32-row tiles.  The
@@ -1245,25 +1246,42 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int q = P.node_inst ? P.node_inst[D] : 0;
         if (q != cq) { cq = q; cached = 0; }
-        if (!__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
         const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
+        const int nL = (int)(l1 - l0);
+        // entries [0, sp) have sources at least two levels down: summed as
+        // soon as those levels complete, before the level barrier
+        const int sp = (P.fwd_split && L >= 1) ? P.fwd_split[i] : 0;
         if (nrhs == 1) {
-            const double a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), z, lane);
+            double a = 0.0;
+            if (sp > 0) {
+                if (!__all_sync(FULL, wait_level(P.wm_f + q, L - 1, cached, P.status, limit))) return;
+                a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, sp, z, lane);
+            }
+            if (!__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
+            a += sparse_dot<T>(LV<T>(P) + l0 + sp, P.lcols + l0 + sp, nL - sp, z, lane);
             if (lane == 0) z[i] -= a;
         } else {
+            if (sp > 0 && !__all_sync(FULL, wait_level(P.wm_f + q, L - 1, cached, P.status, limit))) return;
             for (int r0 = 0; r0 < nrhs; r0 += 8) {
-                double a[8];
+                double a[8], b[8];
                 const int nr = min(8, nrhs - r0);
-                sparse_dot_rhs<T, 8>(LV<T>(P) + l0, P.lcols + l0, (int)(l1 - l0), z + (int64_t)r0 * n, n, nr,
-                                     lane, a);
+                for (int u = 0; u < 8; ++u) a[u] = 0.0;
+                if (sp > 0)
+                    sparse_dot_rhs<T, 8>(LV<T>(P) + l0, P.lcols + l0, sp, z + (int64_t)r0 * n, n, nr, lane, a);
+                if (r0 == 0 && !__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
+                sparse_dot_rhs<T, 8>(LV<T>(P) + l0 + sp, P.lcols + l0 + sp, nL - sp, z + (int64_t)r0 * n, n, nr,
+                                     lane, b);
                 if (lane == 0)
-                    for (int u = 0; u < nr; ++u) z[(int64_t)(r0 + u) * n + i] -= a[u];
+                    for (int u = 0; u < nr; ++u) z[(int64_t)(r0 + u) * n + i] -= a[u] + b[u];
             }
         }
         __threadfence();
         __syncwarp();
         if (s == 1) {
-            if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
+            if (lane == 0) {
+                if (P.strace) P.strace[2 * (int64_t)D + 0] = gtimer();
+                node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
+            }
             continue;
         }
         if (lane == 0) st_release(P.fwd_row + i, gen);
@@ -1288,7 +1306,10 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         __syncwarp();
         if (lane == 0) st_release(P.tile_f + tlast, gen);
         if (tlast != e) continue;
-        if (lane == 0) node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
+        if (lane == 0) {
+            if (P.strace) P.strace[2 * (int64_t)D + 0] = gtimer();
+            node_complete(P.fwd_done + P.fwd_off[q], P.fwd_count + P.fwd_off[q], L, P.wm_f + q);
+        }
     }
 }
 
@@ -1322,12 +1343,22 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         const T* Ui = PV<T>(P) + P.node_panel_off[D] + (int64_t)(i - r) * w;
         const int q = P.node_inst ? P.node_inst[D] : 0;
         if (q != cq) { cq = q; cached = 0; }
-        if (!__all_sync(FULL, wait_level(P.wm_b + q, L, cached, P.status, limit))) return;
+        // tail entries [sp, nT) have sources at least two levels down (the
+        // late ones come first in the tail): summed before the level barrier
+        const int sp = (P.bwd_split && L >= 1) ? P.bwd_split[D] : nT;
+        if (sp < nT && !__all_sync(FULL, wait_level(P.wm_b + q, L - 1, cached, P.status, limit))) return;
         for (int r0 = 0; r0 < nrhs; r0 += 8) {
-            double a[8];
+            double a[8], b[8];
             const int nr = min(8, nrhs - r0);
-            if (nr == 1) a[0] = sparse_dot<T>(Ui + s, tc, nT, xh + (int64_t)r0 * n, lane);
-            else sparse_dot_rhs<T, 8>(Ui + s, tc, nT, xh + (int64_t)r0 * n, n, nr, lane, a);
+            for (int u = 0; u < 8; ++u) { a[u] = 0.0; b[u] = 0.0; }
+            if (sp < nT) {
+                if (nr == 1) b[0] = sparse_dot<T>(Ui + s + sp, tc + sp, nT - sp, xh + (int64_t)r0 * n, lane);
+                else sparse_dot_rhs<T, 8>(Ui + s + sp, tc + sp, nT - sp, xh + (int64_t)r0 * n, n, nr, lane, b);
+            }
+            if (r0 == 0 && !__all_sync(FULL, wait_level(P.wm_b + q, L, cached, P.status, limit))) return;
+            if (nr == 1) a[0] = sparse_dot<T>(Ui + s, tc, sp, xh + (int64_t)r0 * n, lane);
+            else sparse_dot_rhs<T, 8>(Ui + s, tc, sp, xh + (int64_t)r0 * n, n, nr, lane, a);
+            for (int u = 0; u < nr; ++u) a[u] += b[u];
             if (lane == 0)
                 for (int u = 0; u < nr; ++u) {
                     const int64_t o = (int64_t)(r0 + u) * n + i;
@@ -1338,7 +1369,10 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         __threadfence();
         __syncwarp();
         if (s == 1) {
-            if (lane == 0) node_complete(P.bwd_done + P.bwd_off[q], P.bwd_count + P.bwd_off[q], L, P.wm_b + q);
+            if (lane == 0) {
+                if (P.strace) P.strace[2 * (int64_t)D + 1] = gtimer();
+                node_complete(P.bwd_done + P.bwd_off[q], P.bwd_count + P.bwd_off[q], L, P.wm_b + q);
+            }
             continue;
         }
         if (lane == 0) st_release(P.bwd_row + i, gen);
@@ -1365,7 +1399,10 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         __syncwarp();
         if (lane == 0) st_release(P.tile_b + T0, gen);
         if (T0 != r) continue;
-        if (lane == 0) node_complete(P.bwd_done + P.bwd_off[q], P.bwd_count + P.bwd_off[q], L, P.wm_b + q);
+        if (lane == 0) {
+            if (P.strace) P.strace[2 * (int64_t)D + 1] = gtimer();
+            node_complete(P.bwd_done + P.bwd_off[q], P.bwd_count + P.bwd_off[q], L, P.wm_b + q);
+        }
     }
 }
 

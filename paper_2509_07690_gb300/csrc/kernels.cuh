@@ -76,6 +76,13 @@ struct DevPlan {
     int32_t* wm_f;
     int32_t* wm_b;
     int32_t n_inst;
+    // early parts of the substitution's dot products (null: none): forward,
+    // row i's L entries [0, fwd_split[i]) have sources two or more levels
+    // below the row's, so the row sums them once those levels are complete
+    // and only the rest after the last level; backward, node D's tail
+    // entries [bwd_split[D], nT) likewise (its late sources come first)
+    const int32_t* fwd_split;
+    const int32_t* bwd_split;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
     int32_t* tile_f;               // per 32-row tile of a supernode block (at its owner row):
@@ -122,6 +129,7 @@ struct DevPlan {
     const void* tmaps;             // TMA tensor maps, 3 per destination (term-major inside), device memory
     int32_t* gemm_prog;            // diagnostics (debug & 2): per GEMM block, task / stage / chunk / tries
     unsigned long long* trace;     // optional: 4 words per row (claim, external done, published, waits / node complete)
+    unsigned long long* strace;    // optional: per node, forward and backward substitution completion times
     int32_t* status;
     // [0] factor generation, [1] substitution generation: the flags above
     // compare against them.  The first kernel of every factor / substitution
