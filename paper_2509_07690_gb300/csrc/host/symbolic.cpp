@@ -424,6 +424,10 @@ void build_nodes(Plan& P, const SymbolicRows& F) {
 // whose sources lie at no more than half its level carries at least half of
 // its flops.  Top separators of nested dissection fail the test: their
 // sources finish late, and claiming them early would only idle warps.
+// Share of a heavy row's work that must come from sources at no more than
+// half its level.  0: every row past the work cut is heavy.
+constexpr double kHeavyEarlyFrac = 0.0;
+
 void split_heavy_rows(Plan& P, double heavy_ratio) {
     const int32_t n = P.n;
     P.heavy_order.clear();
@@ -448,7 +452,7 @@ void split_heavy_rows(Plan& P, double heavy_ratio) {
             if (P.row_level[eS] > lam) break;
             early += 1.0 + 2.0 * (double)(ulen[k] - 1);
         }
-        if (early >= 0.5 * P.row_flops[i]) {
+        if (early >= kHeavyEarlyFrac * P.row_flops[i]) {
             P.heavy_rank[i] = (int32_t)P.heavy_order.size();
             P.heavy_order.push_back(i);
         }
