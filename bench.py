@@ -64,6 +64,9 @@ def parse():
                     help="circuit workload: untimed AMD / nested dissection trial first, the faster one timed")
     ap.add_argument("--no-precision-form", action="store_true",
                     help="convdiff3d_64: skip the second measurement (the precision form)")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="convdiff3d_64: skip the secondary configurations (5-point grid, circuit, "
+                         "anisotropic diffusion) measured into the same line")
     ap.add_argument("--workload", default="convdiff3d_64",
                     choices=["circuit_100k", "circuit", "grid5_64", "aniso9_512", "convdiff3d_64",
                              "circuit_batch_512"],
@@ -397,6 +400,9 @@ def run_batch(args, ws, rank, local):
     bs.factor(vals)
     bs.solve(db, dx)                          # sizes the right-hand-side workspace the graph uses
     best = bs.tune(vals)
+    tinfo = bs.get_info()
+    tuned = {"factor_blocks_per_sm": tinfo.factor_blocks_per_sm, "solve_blocks_per_sm": tinfo.solve_blocks_per_sm,
+             "heavy_queue": tinfo.heavy_queue}
     side = torch.cuda.Stream(dev)
     side.wait_stream(torch.cuda.current_stream())
     # the graph cannot test the backward error on the host: where the
@@ -468,7 +474,8 @@ def run_batch(args, ws, rank, local):
             "config": {"workload": "circuit_batch_512" if nsys == 512 else f"circuit_batch_{nsys}",
                        "systems": nsys, "systems_rank0": k, "value_sets": BATCH_SETS,
                        "instances": inst_all, "nrhs": BATCH_RHS, "rows_rank0": bs.n, "flops": bs_flops,
-                       "nnz_store_rank0": info.nnz_store, "tuned_blocks_per_sm": best, "analyze_s": analyze_s,
+                       "nnz_store_rank0": info.nnz_store, "tuned_blocks_per_sm": best, "tuned": tuned,
+                       "analyze_s": analyze_s,
                        "flops_by_kernel": kernel_mix(info), "graph_refinement_steps": corrections,
                        "l2": "factor storage far above the 126 MB L2, no flush",
                        "parallelism": f"systems split over {ws} ranks (no exchange)" if ws > 1 else "1 GPU"},
@@ -608,6 +615,25 @@ def run_hylu(args, ws, rank, local):
                 out["precision_form"] = precision_summary(out, out32)
             if out is not None and out32c is not None:
                 out["precision_form_cuda_cores"] = precision_summary(out, out32c)
+        if WORKLOAD == "convdiff3d_64" and args.precision == "fp64" and not args.no_secondary:
+            # the other single-matrix configurations, device-timed on the same
+            # code (no CPU baseline, fewer steps): config 1 (5-point grid),
+            # config 2 (circuit) and config 4 (anisotropic diffusion)
+            sec = {}
+            for wl in ("grid5_64", "circuit_100k", "aniso9_512"):
+                gc.collect()
+                saved_w, saved_s = WORKLOAD, args.steps
+                set_workload(wl)
+                args.steps = max(4, min(args.steps, 8))
+                try:
+                    o2 = measure_hylu(args, ws, rank, local, ordering_for(wl), sub=True)
+                finally:
+                    set_workload(saved_w)
+                    args.steps = saved_s
+                if o2 is not None:
+                    sec[wl] = secondary_summary(o2)
+            if out is not None and sec:
+                out["secondary_workloads"] = sec
         if out is not None:
             print(json.dumps(out), flush=True)
         return 0
@@ -824,6 +850,23 @@ def tensor_summary(inf, kernel_ms: float) -> dict:
     return {"destinations": inf.gemm_destinations, "tasks": inf.gemm_tasks, "useful_fp32_flops": inf.gemm_flops,
             "bf16_flops": bf16, "bf16_tflops_over_factor_kernel": rate, "bf16_peak_tflops": measured_bf16_tflops(),
             "tensor_frac": rate / measured_bf16_tflops(), "products_per_fp32_product": 6}
+
+
+def set_workload(name: str) -> None:
+    global WORKLOAD
+    WORKLOAD = name
+
+
+def secondary_summary(o: dict) -> dict:
+    """A secondary configuration's measurement inside the default line."""
+    keep = ("value", "unit", "ms_per_step", "steps", "gflops", "backward_error", "solve_ms", "nperturb",
+            "refine_iters", "gpu_launches")
+    out = {k: o[k] for k in keep}
+    out["config"] = {k: o["config"][k] for k in ("workload", "n", "nnz", "ordering", "flops", "critical_path_levels")}
+    out["roofline"] = o["roofline"]
+    out["e2e_ms"] = o["e2e"]["value"]
+    out["clocks"] = o["clocks"]
+    return out
 
 
 def precision_summary(fp64: dict, fp32: dict) -> dict:

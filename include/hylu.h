@@ -135,6 +135,10 @@ typedef struct {
     int32_t gemm_tasks;         /* its tensor-core GEMM tasks per factorization           */
     double gemm_flops;          /* useful FP32 flops of those tasks (2 per multiply-add of
                                    L_{D,S} U_{S,T}); 6 BF16 products carry each          */
+    int32_t tuned;              /* 1 after hylu_tune                                      */
+    int32_t factor_blocks_per_sm; /* blocks per SM of the factor / substitution launches   */
+    int32_t solve_blocks_per_sm;
+    int32_t heavy_queue;        /* 1: heavy rows are claimed first (see heavy_ratio)       */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */
@@ -251,9 +255,14 @@ int hylu_graph_capture(hylu_handle* h, const double* d_vals, const double* d_b, 
                        int corrections, void* stream);
 int hylu_graph_launch(hylu_handle* h, void* stream);
 
-/* Autotune the persistent grid (thread blocks per SM, 1..4) of the factor
- * and substitution kernels on d_vals (refactorizes; synchronizes).  The best
- * setting stays in the handle; *blocks_per_sm receives it. */
+/* Autotune the handle on d_vals by short timed trials (refactorizes several
+ * times; synchronizes; allocates two n-vectors for the duration): blocks per
+ * SM (1..4) of the factor launch (fixed at one for the tensor-core variant of
+ * the precision form), the heavy-row queue on or off at that grid, and blocks
+ * per SM of the substitution launches.  The chosen point stays in the handle
+ * (hylu_info reports it: tuned, factor_blocks_per_sm, solve_blocks_per_sm,
+ * heavy_queue), the factors of d_vals are left in place, and *blocks_per_sm
+ * receives the factor launch's setting. */
 int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream);
 
 /* Synchronize the handle's last stream and report sizes, flop counts,

@@ -62,7 +62,9 @@ class Info(C.Structure):
                 ("bwd_levels", C.c_int32), ("flops_row_row", C.c_double), ("flops_sup_row", C.c_double),
                 ("flops_sup_sup", C.c_double), ("flops_in_supernode", C.c_double), ("ordering", C.c_int32),
                 ("analyze_phase_ms", C.c_double * 4), ("gemm_destinations", C.c_int32),
-                ("gemm_tasks", C.c_int32), ("gemm_flops", C.c_double)]
+                ("gemm_tasks", C.c_int32), ("gemm_flops", C.c_double), ("tuned", C.c_int32),
+                ("factor_blocks_per_sm", C.c_int32), ("solve_blocks_per_sm", C.c_int32),
+                ("heavy_queue", C.c_int32)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -40,7 +40,10 @@ struct hylu_handle {
     double* d_colsum = nullptr;
     double* h_norms = nullptr;   // pinned
     int32_t* h_status = nullptr; // pinned
-    int grid = 0;
+    int grid = 0;                        // blocks of the factor launch
+    int solve_grid = 0;                  // blocks of the substitution launches
+    int tuned = 0;                       // hylu_tune ran: tuned_* below are its choice
+    bool heavy_off = false;              // the tuner found the heavy-row queue slower
     cudaStream_t last = nullptr;
     int32_t nperturb = 0, refine_iters = 0, device_status = 0, failed_node = -1;
     double backward_error = -1.0;
@@ -331,6 +334,7 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     TRY(dalloc(h, &d.dinv, P.n));
     TRY(dalloc(h, &d.status, hylu::ST_WORDS));
     h->grid = hylu::factor_grid(h->device, h->opt.precision == 1);
+    h->solve_grid = h->grid;
     TRY(upload_gemm(h, st));
     {
         int sms = 0;
@@ -447,7 +451,7 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
     if (h->opt.refine >= 0) TRY(read_status(h, st));
     hylu::DevPlan& P = h->dp;
     TRY(hylu::launch_solve(P, d_b, d_x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
-                           nrhs, ld, h->opt.spin_limit, h->grid, st,
+                           nrhs, ld, h->opt.spin_limit, h->solve_grid, st,
                            h->opt.timing ? h->ev[2] : nullptr, h->opt.timing ? h->ev[3] : nullptr));
     if (h->opt.timing) h->timed_solve = true;
     h->refine_iters = 0;
@@ -470,7 +474,7 @@ int do_solve(hylu_handle* h, const double* d_b, double* d_x, int nrhs, int ld, c
         be_prev = be;
         Range step("hylu_refine_step");
         TRY(hylu::launch_solve(P, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
-                               h->d_dc, nrhs, ld, h->opt.spin_limit, h->grid, st));
+                               h->d_dc, nrhs, ld, h->opt.spin_limit, h->solve_grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
         ++h->refine_iters;
     }
@@ -485,7 +489,7 @@ int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs,
     TRY(read_status(h, st));
     hylu::DevPlan& P = h->dp;
     TRY(hylu::launch_solve_transpose(P, d_b, d_x, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc, nrhs, ld,
-                                     h->opt.spin_limit, h->grid, st));
+                                     h->opt.spin_limit, h->solve_grid, st));
     h->refine_iters = 0;
     h->backward_error = -1.0;
     h->last = st;
@@ -504,7 +508,7 @@ int do_solve_transpose(hylu_handle* h, const double* d_b, double* d_x, int nrhs,
         be_prev = be;
         Range step("hylu_refine_step");
         TRY(hylu::launch_solve_transpose(P, h->d_r, h->d_d, h->d_z, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc,
-                                         nrhs, ld, h->opt.spin_limit, h->grid, st));
+                                         nrhs, ld, h->opt.spin_limit, h->solve_grid, st));
         TRY(hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st));
         ++h->refine_iters;
     }
@@ -536,7 +540,7 @@ int solve_into(hylu_handle* h, const double* d_b, double* d_x, double* z, double
     if (ready != HYLU_OK) return ready < 0 ? ready : HYLU_OK;
     h->last = st;
     return launch_solve(h->dp, d_b, d_x, z, xh, h->d_rowperm, h->d_colperm, h->d_dr, h->d_dc, 1, h->P.n,
-                        h->opt.spin_limit, h->grid, st);
+                        h->opt.spin_limit, h->solve_grid, st);
 }
 }  // namespace hylu
 
@@ -669,6 +673,15 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
     info->flops_in_supernode = P.flops_in_sn;
     info->ordering = P.ordering;
     for (int ph = 0; ph < 4; ++ph) info->analyze_phase_ms[ph] = P.analyze_phase_ms[ph];
+    info->tuned = h->tuned;
+    {
+        int sms = 1;
+        if (h->uploaded) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+        sms = std::max(1, sms);
+        info->factor_blocks_per_sm = h->uploaded ? h->grid / sms : 0;
+        info->solve_blocks_per_sm = h->uploaded ? h->solve_grid / sms : 0;
+    }
+    info->heavy_queue = (h->dp.n_heavy > 0) ? 1 : 0;
     info->gemm_destinations = h->dp.n_gd;
     info->gemm_tasks = h->dp.n_gtask;
     info->gemm_flops = h->gemm_flops;
@@ -905,7 +918,7 @@ static int graph_capture_impl(hylu_handle* h, const double* d_vals, const double
                                    ld, st);
         if (rc >= 0 && c < corrections)
             rc = hylu::launch_solve(h->dp, h->d_r, h->d_d, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
-                                    h->d_dc, nrhs, ld, h->opt.spin_limit, h->grid, st);
+                                    h->d_dc, nrhs, ld, h->opt.spin_limit, h->solve_grid, st);
         if (rc >= 0 && c < corrections) rc = hylu::launch_axpy(h->P.n, d_x, h->d_d, nrhs, ld, st);
     }
     h->graph_launches = hylu::launches() - l0;
@@ -943,6 +956,11 @@ int hylu_graph_launch(hylu_handle* h, void* stream) {
     return HYLU_OK;
 }
 
+// Short timed trials on the handle's own values (Sec. 3.2's repeated mode
+// makes them pay: the chosen point serves every later refactorization):
+// blocks per SM of the factor launch, the heavy-row queue on or off at that
+// grid, and blocks per SM of the substitution launches (one right-hand side
+// of ones).  Each point is timed twice after a first untimed run.
 static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {
     if (!h || !d_vals) return HYLU_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -953,30 +971,84 @@ static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, v
     }
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-    const int maxper = std::max(1, h->grid_max / std::max(1, sms));
+    sms = std::max(1, sms);
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
-    int best = h->grid / std::max(1, sms);
-    float best_ms = 1e30f;
-    for (int per = 1; per <= maxper; ++per) {
-        h->grid = sms * per;
+    auto timed = [&](auto&& run, float* out) -> int {
         float tot = 0.f;
-        for (int rep = 0; rep < 2; ++rep) {
+        for (int rep = 0; rep < 3; ++rep) {
             cudaEventRecord(e0, st);
-            int rc = do_factor(h, d_vals, st);
+            const int rc = run();
             cudaEventRecord(e1, st);
-            if (rc < 0 || cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc < 0 ? rc : HYLU_ERR_CUDA; }
+            if (rc < 0) return rc;
+            if (cudaEventSynchronize(e1) != cudaSuccess) return HYLU_ERR_CUDA;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep) tot += ms;
         }
-        if (tot < best_ms) { best_ms = tot; best = per; }
+        *out = tot;
+        return HYLU_OK;
+    };
+    int rc = HYLU_OK;
+    // 1. factor grid (the tensor-core variant runs one block per SM: fixed)
+    int best = h->grid / sms;
+    if (h->dp.n_gd == 0) {
+        const int maxper = std::max(1, h->grid_max / sms);
+        float best_ms = 1e30f;
+        for (int per = 1; per <= maxper && rc == HYLU_OK; ++per) {
+            h->grid = sms * per;
+            float ms = 0.f;
+            rc = timed([&] { return do_factor(h, d_vals, st); }, &ms);
+            if (ms < best_ms) { best_ms = ms; best = per; }
+        }
+        h->grid = sms * best;
     }
+    // 2. heavy-row queue on or off
+    const int32_t nheavy = (int32_t)h->P.heavy_order.size();
+    if (rc == HYLU_OK && nheavy > 0) {
+        float on = 0.f, off = 0.f;
+        h->dp.n_heavy = nheavy;
+        rc = timed([&] { return do_factor(h, d_vals, st); }, &on);
+        if (rc == HYLU_OK) {
+            h->dp.n_heavy = 0;
+            rc = timed([&] { return do_factor(h, d_vals, st); }, &off);
+        }
+        h->heavy_off = (rc == HYLU_OK && off < on);
+        h->dp.n_heavy = h->heavy_off ? 0 : nheavy;
+    }
+    // 3. substitution grid
+    if (rc == HYLU_OK) rc = ensure_rhs(h, 1, h->P.n);
+    double *b = nullptr, *x = nullptr;
+    if (rc == HYLU_OK && (cudaMalloc(&b, sizeof(double) * h->P.n) != cudaSuccess ||
+                          cudaMalloc(&x, sizeof(double) * h->P.n) != cudaSuccess))
+        rc = HYLU_ERR_NOMEM;
+    if (rc == HYLU_OK) {
+        std::vector<double> ones(h->P.n, 1.0);
+        if (cudaMemcpy(b, ones.data(), sizeof(double) * h->P.n, cudaMemcpyHostToDevice) != cudaSuccess)
+            rc = HYLU_ERR_CUDA;
+        const int maxper = std::max(1, h->grid_max / sms);
+        int sbest = h->solve_grid / sms;
+        float best_ms = 1e30f;
+        for (int per = 1; per <= maxper && rc == HYLU_OK; ++per) {
+            h->solve_grid = sms * per;
+            float ms = 0.f;
+            rc = timed([&] {
+                return hylu::launch_solve(h->dp, b, x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
+                                          h->d_dc, 1, h->P.n, h->opt.spin_limit, h->solve_grid, st);
+            }, &ms);
+            if (ms < best_ms) { best_ms = ms; sbest = per; }
+        }
+        h->solve_grid = sms * sbest;
+    }
+    if (b) cudaFree(b);
+    if (x) cudaFree(x);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->grid = sms * best;
+    if (rc < 0) return rc;
+    h->tuned = 1;
     if (blocks_per_sm) *blocks_per_sm = best;
+    TRY(do_factor(h, d_vals, st));   // leave the factors of d_vals at the chosen point
     return read_status(h, st);
 }
 

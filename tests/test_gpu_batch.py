@@ -74,6 +74,8 @@ def test_batch_matches_oracle_and_graph_replay():
     # one graph: refactor + solve, replayed on a created stream
     best = bs.tune(vals)
     assert 1 <= best <= 4
+    ti = bs.get_info()
+    assert ti.tuned == 1 and ti.factor_blocks_per_sm == best and 1 <= ti.solve_blocks_per_sm <= 4
     dx = torch.empty_like(db)
     side = torch.cuda.Stream()
     side.wait_stream(torch.cuda.current_stream())
