@@ -262,7 +262,8 @@ int hylu_graph_launch(hylu_handle* h, void* stream);
  * per SM of the substitution launches.  The chosen point stays in the handle
  * (hylu_info reports it: tuned, factor_blocks_per_sm, solve_blocks_per_sm,
  * heavy_queue), the factors of d_vals are left in place, and *blocks_per_sm
- * receives the factor launch's setting. */
+ * receives the factor launch's setting.  The substitution is timed with as
+ * many right-hand sides as the handle's solves used so far (1 to 8). */
 int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream);
 
 /* Synchronize the handle's last stream and report sizes, flop counts,

@@ -959,8 +959,9 @@ int hylu_graph_launch(hylu_handle* h, void* stream) {
 // Short timed trials on the handle's own values (Sec. 3.2's repeated mode
 // makes them pay: the chosen point serves every later refactorization):
 // blocks per SM of the factor launch, the heavy-row queue on or off at that
-// grid, and blocks per SM of the substitution launches (one right-hand side
-// of ones).  Each point is timed twice after a first untimed run.
+// grid, and blocks per SM of the substitution launches (right-hand sides of
+// ones, as many as the handle's solves used, 1 to 8).  Each point is timed
+// twice after a first untimed run.
 static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream) {
     if (!h || !d_vals) return HYLU_ERR_ARG;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1017,15 +1018,18 @@ static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, v
         h->heavy_off = (rc == HYLU_OK && off < on);
         h->dp.n_heavy = h->heavy_off ? 0 : nheavy;
     }
-    // 3. substitution grid
-    if (rc == HYLU_OK) rc = ensure_rhs(h, 1, h->P.n);
+    // 3. substitution grid, with as many right-hand sides as the handle's
+    //    solves have used so far (at least one, at most eight)
+    const int nr = std::max(1, std::min(8, h->cap_rhs));
+    const size_t nv = (size_t)h->P.n * nr;
+    if (rc == HYLU_OK) rc = ensure_rhs(h, nr, h->P.n);
     double *b = nullptr, *x = nullptr;
-    if (rc == HYLU_OK && (cudaMalloc(&b, sizeof(double) * h->P.n) != cudaSuccess ||
-                          cudaMalloc(&x, sizeof(double) * h->P.n) != cudaSuccess))
+    if (rc == HYLU_OK && (cudaMalloc(&b, sizeof(double) * nv) != cudaSuccess ||
+                          cudaMalloc(&x, sizeof(double) * nv) != cudaSuccess))
         rc = HYLU_ERR_NOMEM;
     if (rc == HYLU_OK) {
-        std::vector<double> ones(h->P.n, 1.0);
-        if (cudaMemcpy(b, ones.data(), sizeof(double) * h->P.n, cudaMemcpyHostToDevice) != cudaSuccess)
+        std::vector<double> ones(nv, 1.0);
+        if (cudaMemcpy(b, ones.data(), sizeof(double) * nv, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = HYLU_ERR_CUDA;
         const int maxper = std::max(1, h->grid_max / sms);
         int sbest = h->solve_grid / sms;
@@ -1035,7 +1039,7 @@ static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, v
             float ms = 0.f;
             rc = timed([&] {
                 return hylu::launch_solve(h->dp, b, x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
-                                          h->d_dc, 1, h->P.n, h->opt.spin_limit, h->solve_grid, st);
+                                          h->d_dc, nr, h->P.n, h->opt.spin_limit, h->solve_grid, st);
             }, &ms);
             if (ms < best_ms) { best_ms = ms; sbest = per; }
         }
