@@ -89,6 +89,11 @@ typedef struct {
                               supernodes of at least min(16, gemm_min_rows) rows as split-BF16
                               tensor-core GEMM tasks (Sec. 2.2, Fig. 1c, sup-sup); 0 disables (64).
                               Ignored for FP64 factors. */
+    int solve_seq_rows;    /* substitution, bulk-sequential (Sec. 2.3, Fig. 3): a chain of two or
+                              more consecutive light levels (at most this many rows, see
+                              hylu_export_solve_segments) is solved level after level by one
+                              thread block with block barriers instead of the level watermark's
+                              hand-off; 0 solves every level in bulk (default 8) */
 } hylu_options;
 
 typedef struct {
@@ -292,6 +297,23 @@ int hylu_export_schedule(hylu_handle* h, int32_t* order, int32_t* heavy, int32_t
  * only.  HYLU_ERR_INTERNAL when the pattern is not closed under the
  * supernode tails (never for a plan of this library). */
 int hylu_export_gemm_plan(hylu_handle* h, int min_rows, int64_t* buf, int64_t* len);
+
+/* Bulk-sequential partition of the forward (backward = 0) or backward
+ * (backward = 1) substitution for solve_seq_rows = max_rows (Sec. 2.3,
+ * Fig. 3), as int32 in HOST memory.  A level of one instance is light when it
+ * holds at most max_rows rows, no node of more rows, and at most 1024 max_rows
+ * entries of work (its rows' L lists, or its nodes' U tails times their rows,
+ * plus the squares of its node sizes); a segment is a maximal chain of two or
+ * more consecutive light levels, solved by one thread block; the other rows
+ * are solved in bulk.  Layout: a header [ntask, nseg, nlevels, nrows,
+ * nsnodes], then task (ntask: the bulk rows in claim order), meta (3 nseg:
+ * instance, first level, last level; segments sorted by first level), seg_off
+ * (nseg + 1, into the level table), lvl_row (nlevels + 1, into rows), lvl_node
+ * (nlevels + 1, into snodes), rows (nrows: the segments' rows, level by level,
+ * node by node) and snodes (nsnodes: the segments' nodes of more than one
+ * row).  buf = NULL returns the length in *len; HYLU_ERR_ARG when *len is too
+ * small (*len then holds the length needed).  Host work only. */
+int hylu_export_solve_segments(hylu_handle* h, int backward, int max_rows, int32_t* buf, int64_t* len);
 
 /* Padded storage pattern in CSR form (HOST arrays, any may be NULL):
  * rowptr int64[n+1], col int32[info.nnz_store]; columns sorted per row. */

@@ -46,7 +46,8 @@ class Options(C.Structure):
                 ("refine_tol", C.c_double), ("refine_maxit", C.c_int), ("refine", C.c_int),
                 ("spin_limit", C.c_longlong), ("rows_per_task", C.c_int), ("debug", C.c_int),
                 ("amd_dense", C.c_double), ("timing", C.c_int), ("precision", C.c_int),
-                ("heavy_ratio", C.c_double), ("gemm_min_rows", C.c_int)]
+                ("heavy_ratio", C.c_double), ("gemm_min_rows", C.c_int),
+                ("solve_seq_rows", C.c_int)]
 
 
 class Info(C.Structure):
@@ -105,6 +106,7 @@ def load():
     lib.hylu_debug_gemm.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                     C.POINTER(C.c_int32)]
     lib.hylu_export_gemm_plan.argtypes = [H, C.c_int, C.c_void_p, C.POINTER(C.c_int64)]
+    lib.hylu_export_solve_segments.argtypes = [H, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_int64)]
     lib.hylu_split_gemm.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int,
                                     C.c_int, C.c_int, C.c_int, C.c_void_p]
     lib.hylu_solve_static.argtypes = [H, C.c_void_p, C.c_void_p, C.c_void_p]
@@ -268,6 +270,29 @@ def hylu_export_gemm_plan(h: int, min_rows: int, n: int) -> dict:
         m = cnt[size] if cnt["ngd"] else 0
         out[name] = buf[pos:pos + m]
         pos += m
+    return out
+
+
+def hylu_export_solve_segments(h: int, backward: bool, max_rows: int) -> dict:
+    """Bulk-sequential partition of a substitution (see include/hylu.h): the
+    bulk claim list `task`, per segment `meta` (instance, first level, last
+    level) and `seg_off`, per level `lvl_row` / `lvl_node`, and `rows`,
+    `snodes`."""
+    lib = load()
+    ln = C.c_int64(0)
+    _check(lib.hylu_export_solve_segments(h, int(bool(backward)), int(max_rows), None, C.byref(ln)),
+           "hylu_export_solve_segments")
+    buf = np.zeros(ln.value, np.int32)
+    _check(lib.hylu_export_solve_segments(h, int(bool(backward)), int(max_rows), buf.ctypes.data, C.byref(ln)),
+           "hylu_export_solve_segments")
+    nt, ns, nl, nr, nn = (int(v) for v in buf[:5])
+    pos = 5
+    out = {}
+    for name, m in (("task", nt), ("meta", 3 * ns), ("seg_off", ns + 1), ("lvl_row", nl + 1),
+                    ("lvl_node", nl + 1), ("rows", nr), ("snodes", nn)):
+        out[name] = buf[pos:pos + m].copy()
+        pos += m
+    out["meta"] = out["meta"].reshape(-1, 3)
     return out
 
 

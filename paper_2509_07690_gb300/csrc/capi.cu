@@ -185,6 +185,40 @@ int upload_gemm(hylu_handle* h, cudaStream_t st) {
     return HYLU_OK;
 }
 
+// Bulk-sequential substitution (Sec. 2.3, Fig. 3): the bulk claim lists and
+// the segments of light levels under opt.solve_seq_rows, for both directions.
+// One block takes the segments of a single system (they form one chain of
+// levels); a batch gets one block per 8 segments, at most an eighth of the
+// launch, since its instances' segments are independent.
+static int upload_seq_segments(hylu_handle* h, cudaStream_t st) {
+    hylu::DevPlan& d = h->dp;
+    int32_t nseg_max = 0;
+    for (int dir = 0; dir < 2; ++dir) {
+        hylu::SeqSegments S;
+        hylu::build_seq_segments(h->P, dir == 1, h->opt.solve_seq_rows, S);
+        hylu::SegTable T{};
+        T.nseg = (int32_t)(S.seg_off.size() - 1);
+        nseg_max = std::max(nseg_max, T.nseg);
+        for (std::vector<int32_t>* v : {&S.meta, &S.rows, &S.snodes})
+            if (v->empty()) v->push_back(0);   // keep every array non-empty
+        int32_t *task, *meta, *so, *lr, *ln, *rows, *sn;
+        TRY(upload(h, &task, S.task, st));
+        TRY(upload(h, &meta, S.meta, st));
+        TRY(upload(h, &so, S.seg_off, st));
+        TRY(upload(h, &lr, S.lvl_row, st));
+        TRY(upload(h, &ln, S.lvl_node, st));
+        TRY(upload(h, &rows, S.rows, st));
+        TRY(upload(h, &sn, S.snodes, st));
+        if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;   // S goes out of scope
+        T.meta = meta; T.seg_off = so; T.lvl_row = lr; T.lvl_node = ln; T.rows = rows; T.snodes = sn;
+        if (dir == 0) { d.fwd_task = task; d.n_fwd_tasks = (int32_t)S.task.size(); d.fseg = T; }
+        else { d.bwd_task = task; d.n_bwd_tasks = (int32_t)S.task.size(); d.bseg = T; }
+    }
+    const bool batch = !h->P.node_inst.empty();
+    d.seq_blocks = nseg_max == 0 ? 0 : batch ? std::max(1, (nseg_max + 7) / 8) : 1;   // capped at launch
+    return HYLU_OK;
+}
+
 int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
     if (h->uploaded) return HYLU_OK;
     if (cudaGetDevice(&h->device) != cudaSuccess) return HYLU_ERR_CUDA;
@@ -292,6 +326,7 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
             d.fwd_split = dfs;
             d.bwd_split = dbs;
         }
+        TRY(upload_seq_segments(h, st));
         int32_t *uo, *lo, *ul, *ll, *uc, *lcn;
         TRY(upload(h, &uo, P.ut_order, st));
         TRY(upload(h, &lo, P.lt_order, st));
@@ -566,6 +601,7 @@ int hylu_default_options(hylu_options* o) {
     o->precision = 0;
     o->heavy_ratio = 32.0;
     o->gemm_min_rows = 64;
+    o->solve_seq_rows = 8;
     return HYLU_OK;
 }
 
@@ -755,6 +791,24 @@ int hylu_export_gemm_plan(hylu_handle* h, int min_rows, int64_t* buf, int64_t* l
         if (!buf) { *len = need; return HYLU_OK; }
         if (*len < need) { *len = need; return HYLU_ERR_ARG; }
         std::memcpy(buf, out.data(), sizeof(int64_t) * out.size());
+        *len = need;
+        return HYLU_OK;
+    });
+}
+
+int hylu_export_solve_segments(hylu_handle* h, int backward, int max_rows, int32_t* buf, int64_t* len) {
+    if (!h || !len) return HYLU_ERR_ARG;
+    return guarded([&] {
+        hylu::SeqSegments S;
+        hylu::build_seq_segments(h->P, backward != 0, max_rows, S);
+        std::vector<int32_t> out = {(int32_t)S.task.size(), (int32_t)(S.seg_off.size() - 1),
+                                    (int32_t)(S.lvl_row.size() - 1), (int32_t)S.rows.size(), (int32_t)S.snodes.size()};
+        for (const std::vector<int32_t>* v : {&S.task, &S.meta, &S.seg_off, &S.lvl_row, &S.lvl_node, &S.rows, &S.snodes})
+            out.insert(out.end(), v->begin(), v->end());
+        const int64_t need = (int64_t)out.size();
+        if (!buf) { *len = need; return HYLU_OK; }
+        if (*len < need) { *len = need; return HYLU_ERR_ARG; }
+        std::memcpy(buf, out.data(), sizeof(int32_t) * out.size());
         *len = need;
         return HYLU_OK;
     });

@@ -128,6 +128,23 @@ struct SymbolicRows {
     int64_t nnz_l = 0;                   // unpadded entries of L (strictly lower)
 };
 
+// Sequential part of the bulk-sequential substitution (Sec. 2.3, Fig. 3;
+// seq_runs.cpp).  A level of one instance is light when it holds at most
+// max_rows rows, no node larger than that, and at most 1024 max_rows entries
+// of work (its rows' L lists or U tails plus its dense diagonal blocks);
+// every maximal chain of two or more consecutive light levels is a segment,
+// solved level after level by one thread block (0: no segments).
+//   task      the bulk claim list: the rows outside the segments, in claim order
+//   meta      per segment: instance, first level, last level (segments sorted
+//             by first level)
+//   seg_off   segments + 1, into the level table
+//   lvl_row   level table + 1, into rows (a level's rows, node by node)
+//   lvl_node  level table + 1, into snodes (a level's nodes of more than one row)
+struct SeqSegments {
+    std::vector<int32_t> task, meta, seg_off, lvl_row, lvl_node, rows, snodes;
+};
+void build_seq_segments(const Plan& P, bool backward, int32_t max_rows, SeqSegments& S);
+
 // Checkpoint of an analysis (serialize.cpp): the plan, the batch layout and
 // the options as one flat byte image with a checksum, and back.  load_plan
 // returns HYLU_ERR_PATTERN for an image that is not one (wrong magic,

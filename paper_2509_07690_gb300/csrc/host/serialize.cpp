@@ -21,7 +21,7 @@ namespace hylu {
 namespace {
 
 constexpr char kMagic[8] = {'H', 'Y', 'L', 'U', 'P', 'L', 'A', 'N'};
-constexpr uint32_t kVersion = 2;
+constexpr uint32_t kVersion = 3;
 constexpr uint32_t kOrder = 0x01020304u;
 
 uint64_t fnv1a(const uint8_t* p, size_t n) {
@@ -77,7 +77,7 @@ bool visit(V& f, Plan& P, BatchLayout& B, int32_t& batch, hylu_options& o) {
     ok = ok && f(o.ordering) && f(o.static_pivot) && f(o.scale) && f(o.sn_max) && f(o.nd_leaf);
     ok = ok && f(o.pivot_tau) && f(o.refine_tol) && f(o.refine_maxit) && f(o.refine) && f(o.spin_limit);
     ok = ok && f(o.rows_per_task) && f(o.debug) && f(o.amd_dense) && f(o.timing) && f(o.precision);
-    ok = ok && f(o.heavy_ratio) && f(o.gemm_min_rows);
+    ok = ok && f(o.heavy_ratio) && f(o.gemm_min_rows) && f(o.solve_seq_rows);
     // plan scalars
     ok = ok && f(P.n) && f(P.nnz_a) && f(P.nnodes) && f(P.nnz_l) && f(P.nnz_panel) && f(P.nnz_store);
     ok = ok && f(P.nnz_f) && f(P.flops_unpadded) && f(P.flops_padded) && f(P.n_tasks) && f(P.row_levels);

@@ -1121,7 +1121,10 @@ __device__ __forceinline__ bool wait_level(const int* wm, int need, int& cached,
                 break;
             }
             if ((it & 255) == 0 && ld_relaxed(status + ST_ERR) != 0) { ok = 0; break; }
-            if (it > 8) __nanosleep(64);
+            // a warp two or more levels short of its wait polls rarely: the
+            // warps of the next level then find the watermark's line free
+            if (need - v > 1) __nanosleep(1024);
+            else if (it > 8) __nanosleep(64);
         }
     }
     ok = __shfl_sync(FULL, ok, 0);
@@ -1221,6 +1224,157 @@ __device__ void tile_upper(const T* __restrict__ Ub, int w, int r, int T0, int n
     }
 }
 
+// Sequential mode of the bulk-sequential substitution (Sec. 2.3, Fig. 3:
+// levels with many nodes are solved in bulk, the long chain sequentially).
+// One thread block solves a segment of consecutive light levels: it waits
+// once for the levels below the segment, then per level the warps share its
+// rows (each row's dot product), a block barrier, the warps share the level's
+// supernodes (the dense block by 32-row tiles), a block barrier; the level
+// watermark is raised once, past the segment's last level.  Every thread of
+// the block calls these; false when a wait expired or the solve failed.
+__device__ __forceinline__ void seg_stamp(const DevPlan& P, const SegTable& S, int k, int dir) {
+    if (!P.strace) return;
+    for (int t = S.lvl_row[k] + threadIdx.x; t < S.lvl_row[k + 1]; t += blockDim.x) {
+        const int i = S.rows[t], D = P.node_of[i];
+        if (i == P.sn_start[D]) P.strace[2 * (int64_t)D + dir] = gtimer();
+    }
+}
+
+template <typename T>
+__device__ bool fwd_segment(const DevPlan& P, int g, double* __restrict__ z, int nrhs, long long limit) {
+    const SegTable& S = P.fseg;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n = P.n;
+    const int q = S.meta[3 * g], L0 = S.meta[3 * g + 1], L1 = S.meta[3 * g + 2];
+    int cached = 0;
+    const bool ok = wait_level(P.wm_f + q, L0, cached, P.status, limit);
+    if (__syncthreads_or(!ok)) return false;
+    for (int k = S.seg_off[g]; k < S.seg_off[g + 1]; ++k) {
+        for (int t = S.lvl_row[k] + wid; t < S.lvl_row[k + 1]; t += WARPS) {
+            const int i = S.rows[t];
+            const int64_t l0 = P.row_lptr[i];
+            const int nL = (int)(P.row_lptr[i + 1] - l0);
+            for (int r0 = 0; r0 < nrhs; r0 += 8) {
+                double a[8];
+                const int nr = min(8, nrhs - r0);
+                if (nr == 1) a[0] = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, nL, z + (int64_t)r0 * n, lane);
+                else sparse_dot_rhs<T, 8>(LV<T>(P) + l0, P.lcols + l0, nL, z + (int64_t)r0 * n, n, nr, lane, a);
+                if (lane == 0)
+                    for (int u = 0; u < nr; ++u) z[(int64_t)(r0 + u) * n + i] -= a[u];
+            }
+        }
+        __syncthreads();
+        if (S.lvl_node[k + 1] > S.lvl_node[k]) {
+            for (int t = S.lvl_node[k] + wid; t < S.lvl_node[k + 1]; t += WARPS) {
+                const int D = S.snodes[t];
+                const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+                const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+                const T* Ub = PV<T>(P) + P.node_panel_off[D];
+                for (int T0 = r; T0 <= e; T0 += 32) {
+                    const int nt = min(32, e - T0 + 1);
+                    for (int K0 = r; K0 < T0; K0 += 32)
+                        tile_apply<T>(Ub, w, r, T0, nt, K0, 32, P.piv, z, n, nrhs, lane);
+                    __syncwarp();
+                    tile_lower<T>(Ub, w, r, T0, nt, P.piv, z, n, nrhs, lane);
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+        seg_stamp(P, S, k, 0);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(P.wm_f + q, L1 + 1);
+    return true;
+}
+
+template <typename T>
+__device__ bool bwd_segment(const DevPlan& P, int g, const T* __restrict__ dinv, double* __restrict__ z,
+                            double* __restrict__ xh, int nrhs, long long limit) {
+    const SegTable& S = P.bseg;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n = P.n;
+    const int q = S.meta[3 * g], L0 = S.meta[3 * g + 1], L1 = S.meta[3 * g + 2];
+    int cached = 0;
+    const bool ok = wait_level(P.wm_b + q, L0, cached, P.status, limit);
+    if (__syncthreads_or(!ok)) return false;
+    for (int k = S.seg_off[g]; k < S.seg_off[g + 1]; ++k) {
+        for (int t = S.lvl_row[k] + wid; t < S.lvl_row[k + 1]; t += WARPS) {
+            const int i = S.rows[t];
+            const int D = P.node_of[i];
+            const int r = P.sn_start[D], s = P.sn_start[D + 1] - r;
+            const int64_t t0 = P.node_tail_off[D];
+            const int nT = (int)(P.node_tail_off[D + 1] - t0);
+            const T* Ui = PV<T>(P) + P.node_panel_off[D] + (int64_t)(i - r) * (s + nT);
+            for (int r0 = 0; r0 < nrhs; r0 += 8) {
+                double a[8];
+                const int nr = min(8, nrhs - r0);
+                if (nr == 1) a[0] = sparse_dot<T>(Ui + s, P.tcols + t0, nT, xh + (int64_t)r0 * n, lane);
+                else sparse_dot_rhs<T, 8>(Ui + s, P.tcols + t0, nT, xh + (int64_t)r0 * n, n, nr, lane, a);
+                if (lane == 0)
+                    for (int u = 0; u < nr; ++u) {
+                        const int64_t o = (int64_t)(r0 + u) * n + i;
+                        if (s == 1) xh[o] = (z[o] - a[u]) * (double)dinv[i];
+                        else z[o] -= a[u];
+                    }
+            }
+        }
+        __syncthreads();
+        if (S.lvl_node[k + 1] > S.lvl_node[k]) {
+            for (int t = S.lvl_node[k] + wid; t < S.lvl_node[k + 1]; t += WARPS) {
+                const int D = S.snodes[t];
+                const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
+                const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+                const T* Ub = PV<T>(P) + P.node_panel_off[D];
+                for (int T0 = r + ((e - r) & ~31); T0 >= r; T0 -= 32) {
+                    const int nt = min(32, e - T0 + 1);
+                    for (int K0 = r + ((e - r) & ~31); K0 > T0; K0 -= 32)
+                        tile_apply<T>(Ub, w, r, T0, nt, K0, min(32, e - K0 + 1), P.piv, z, n, nrhs, lane);
+                    __syncwarp();
+                    tile_upper<T>(Ub, w, r, T0, nt, P.piv, dinv, z, n, nrhs, lane);
+                    __syncwarp();
+                    for (int rr = 0; rr < nrhs; ++rr)
+                        if (lane < nt) xh[(int64_t)rr * n + P.piv[T0 + lane]] = z[(int64_t)rr * n + T0 + lane];
+                    __syncwarp();
+                }
+            }
+            __syncthreads();
+        }
+        seg_stamp(P, S, k, 1);
+    }
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) st_release(P.wm_b + q, L1 + 1);
+    return true;
+}
+
+// The first seq_blocks blocks to start take the segments, in order, before
+// they join the bulk claims; the other blocks go to the bulk claims directly.
+// Decisions are block-uniform (a shared word between two barriers).
+template <typename T>
+__device__ bool run_segments(const DevPlan& P, bool bwd, const T* __restrict__ dinv, double* __restrict__ z,
+                             double* __restrict__ xh, int nrhs, long long limit) {
+    __shared__ int s_claim;
+    const SegTable& S = bwd ? P.bseg : P.fseg;
+    if (threadIdx.x == 0) s_claim = atomicAdd(P.status + (bwd ? ST_ROLE_B : ST_ROLE_F), 1);
+    __syncthreads();
+    const bool seq = s_claim < P.seq_blocks;
+    __syncthreads();
+    if (!seq) return true;
+    for (;;) {
+        if (threadIdx.x == 0)
+            s_claim = ld_relaxed(P.status + ST_ERR) != 0 ? -1 : atomicAdd(P.status + (bwd ? ST_SEG_B : ST_SEG_F), 1);
+        __syncthreads();
+        const int g = s_claim;
+        __syncthreads();
+        if (g < 0) return false;
+        if (g >= S.nseg) return true;
+        if (!(bwd ? bwd_segment<T>(P, g, dinv, z, xh, nrhs, limit) : fwd_segment<T>(P, g, z, nrhs, limit)))
+            return false;
+    }
+}
+
 // Forward substitution L z = bhat (unit L, by position); z holds bhat on
 // entry.  Each warp claims the next row in level order, waits for the lower
 // levels of its instance, subtracts the row's L list; the warp of the last
@@ -1230,6 +1384,7 @@ __device__ void tile_upper(const T* __restrict__ Ub, int w, int r, int T0, int n
 template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
+    if (P.fseg.nseg > 0 && !run_segments<T>(P, false, nullptr, z, nullptr, nrhs, limit)) return;
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
@@ -1238,9 +1393,9 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         int qi = 0;
         if (lane == 0) qi = atomicAdd(P.status + ST_CNT_FWD, 1);
         qi = __shfl_sync(FULL, qi, 0);
-        if (qi >= n) return;
+        if (qi >= P.n_fwd_tasks) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
-        const int i = P.fwd_order[qi];
+        const int i = P.fwd_task[qi];
         const int D = P.node_of[i];
         const int L = P.fwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
@@ -1322,6 +1477,7 @@ template <typename T>
 __global__ void __launch_bounds__(WARPS * 32)
 bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
            double* __restrict__ xh, int nrhs, long long limit) {
+    if (P.bseg.nseg > 0 && !run_segments<T>(P, true, dinv, z, xh, nrhs, limit)) return;
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
     const int n = P.n;
@@ -1330,9 +1486,9 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         int qi = 0;
         if (lane == 0) qi = atomicAdd(P.status + ST_CNT_BWD, 1);
         qi = __shfl_sync(FULL, qi, 0);
-        if (qi >= n) return;
+        if (qi >= P.n_bwd_tasks) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
-        const int i = P.bwd_order[qi];
+        const int i = P.bwd_task[qi];
         const int D = P.node_of[i];
         const int L = P.bwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
@@ -1832,19 +1988,25 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     const int64_t tot = (int64_t)P.n * nrhs;
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
     if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
+    if (cudaMemsetAsync(P.status + ST_SEG_F, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.fwd_done, 0, sizeof(int32_t) * P.n_fwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.wm_f, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.wm_b, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.bwd_done, 0, sizeof(int32_t) * P.n_bwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
     permute_in_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld, P.gens);
     count_launch();
-    const int blocks = grid;
+    // the segments' rows are not in the bulk claim lists: at least one block
+    // takes the segments and at least half of the launch stays in bulk
+    DevPlan Q = P;
+    const bool seg = P.fseg.nseg > 0 || P.bseg.nseg > 0;
+    const int blocks = seg ? std::max(grid, 2) : grid;
+    if (seg) Q.seq_blocks = std::max(1, std::min(P.seq_blocks, blocks / 2));
     if (e0) cudaEventRecord(e0, st);
-    if (P.lval32) fwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, spin_limit);
-    else fwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, d_z, nrhs, spin_limit);
+    if (P.lval32) fwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
+    else fwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
     count_launch();
-    if (P.lval32) bwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv32, d_z, d_xh, nrhs, spin_limit);
-    else bwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(P, P.dinv, d_z, d_xh, nrhs, spin_limit);
+    if (P.lval32) bwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, d_z, d_xh, nrhs, spin_limit);
+    else bwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv, d_z, d_xh, nrhs, spin_limit);
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     permute_out_kernel<<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);

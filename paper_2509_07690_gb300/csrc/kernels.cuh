@@ -16,7 +16,23 @@ namespace hylu {
 //   [12] task counter of the factor kernel's heavy-row queue, [13] of its
 //   tensor-core GEMM queue ([14..15] unused).
 enum { ST_ERR = 0, ST_FAILED = 1, ST_NPERT = 2, ST_CNT_F = 3, ST_AMAX = 6, ST_CNT_FWD = 8,
-       ST_CNT_BWD = 9, ST_WM_F = 10, ST_WM_B = 11, ST_CNT_H = 12, ST_CNT_G = 13, ST_WORDS = 16 };
+       ST_CNT_BWD = 9, ST_ROLE_F = 10, ST_ROLE_B = 11, ST_CNT_H = 12, ST_CNT_G = 13, ST_SEG_F = 14,
+       ST_SEG_B = 15, ST_WORDS = 16 };
+
+// Segments of light levels of one substitution direction (the sequential
+// mode of Sec. 2.3's bulk-sequential solve): per segment its instance, first
+// and last level (meta), its levels (seg_off, into the level table), and per
+// level its rows (lvl_row into rows) and its nodes of more than one row
+// (lvl_node into snodes).
+struct SegTable {
+    const int32_t* meta;
+    const int32_t* seg_off;
+    const int32_t* lvl_row;
+    const int32_t* lvl_node;
+    const int32_t* rows;
+    const int32_t* snodes;
+    int32_t nseg;
+};
 
 struct DevPlan {
     int32_t n, nnodes;
@@ -83,6 +99,14 @@ struct DevPlan {
     // entries [bwd_split[D], nT) likewise (its late sources come first)
     const int32_t* fwd_split;
     const int32_t* bwd_split;
+    // bulk-sequential substitution (Sec. 2.3, Fig. 3): the bulk claim lists
+    // (rows outside the segments) and the segments of light levels, which the
+    // first seq_blocks blocks to start claim and solve one after another
+    const int32_t* fwd_task;
+    const int32_t* bwd_task;
+    int32_t n_fwd_tasks, n_bwd_tasks;
+    SegTable fseg, bseg;
+    int32_t seq_blocks;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
     int32_t* tile_f;               // per 32-row tile of a supernode block (at its owner row):

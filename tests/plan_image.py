@@ -11,7 +11,7 @@ import numpy as np
 _OPTS = [("ordering", "i"), ("static_pivot", "i"), ("scale", "i"), ("sn_max", "i"), ("nd_leaf", "i"),
          ("pivot_tau", "d"), ("refine_tol", "d"), ("refine_maxit", "i"), ("refine", "i"),
          ("spin_limit", "q"), ("rows_per_task", "i"), ("debug", "i"), ("amd_dense", "d"), ("timing", "i"),
-         ("precision", "i"), ("heavy_ratio", "d"), ("gemm_min_rows", "i")]
+         ("precision", "i"), ("heavy_ratio", "d"), ("gemm_min_rows", "i"), ("solve_seq_rows", "i")]
 _SCALARS = [("n", "i"), ("nnz_a", "q"), ("nnodes", "i"), ("nnz_l", "q"), ("nnz_panel", "q"),
             ("nnz_store", "q"), ("nnz_f", "q"), ("flops_unpadded", "d"), ("flops_padded", "d"),
             ("n_tasks", "i"), ("row_levels", "i"), ("flops_row_row", "d"), ("flops_sup_row", "d"),
@@ -40,7 +40,7 @@ class PlanImage:
         self._b = image
         self._p = 8
         version, order = self._scalar("I"), self._scalar("I")
-        assert version == 2 and order == 0x01020304
+        assert version == 3 and order == 0x01020304
         self.opt = {name: self._scalar(f) for name, f in _OPTS}
         for name, f in _SCALARS:
             setattr(self, name, self._scalar(f))

@@ -774,11 +774,11 @@ def test_plan_checkpoint_rejects_damaged_images():
     assert code(image[:40]) == -2
     assert code(b"XYLUPLAN" + image[8:]) == -2          # foreign magic
     body = bytearray(image[:-8])
-    body[8] = 3                                        # a later version
+    body[8] = 4                                        # a later version
     assert code(resealed(bytes(body))) == -2
     body = bytearray(image[:-8])
-    assert int.from_bytes(body[104:108], "little") == A.n
-    body[104:108] = (A.n + 1).to_bytes(4, "little")    # n no longer fits the arrays
+    assert int.from_bytes(body[108:112], "little") == A.n
+    body[108:112] = (A.n + 1).to_bytes(4, "little")    # n no longer fits the arrays
     assert code(resealed(bytes(body))) == -2
     h = capi.hylu_plan_load(resealed(image[:-8]))     # resealing alone changes nothing
     assert h
