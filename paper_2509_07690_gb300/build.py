@@ -16,7 +16,7 @@ NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 HOST_SRCS = ["host/mwm.cpp", "host/amd.cpp", "host/nd.cpp", "host/symbolic.cpp", "host/analyze.cpp",
              "host/batch.cpp", "host/serialize.cpp", "host/gemm_plan.cpp",
-             "host/seq_runs.cpp"]
+             "host/seq_segments.cpp"]
 CUDA_SRCS = ["kernels.cu", "capi.cu", "peak.cu", "static_solve.cu", "tc_gemm.cu"]
 
 

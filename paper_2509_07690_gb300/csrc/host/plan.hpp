@@ -129,7 +129,7 @@ struct SymbolicRows {
 };
 
 // Sequential part of the bulk-sequential substitution (Sec. 2.3, Fig. 3;
-// seq_runs.cpp).  A level of one instance is light when it holds at most
+// seq_segments.cpp).  A level of one instance is light when it holds at most
 // max_rows rows, no node larger than that, and at most 1024 max_rows entries
 // of work (its rows' L lists or U tails plus its dense diagonal blocks);
 // every maximal chain of two or more consecutive light levels is a segment,
