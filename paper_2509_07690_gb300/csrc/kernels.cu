@@ -1169,28 +1169,38 @@ __device__ void tile_apply(const T* __restrict__ Ub, int w, int r, int R0, int n
         const double zt = (lane < nt) ? z[u * ldz + P0 + lane] : 0.0;
         double a = 0.0;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) a = fma((double)Rrow[c], __shfl_sync(FULL, zt, c), a);
+        for (int c = 0; c < 32; ++c)
+            if (c < nt) a = fma((double)Rrow[c], __shfl_sync(FULL, zt, c), a);   // nt is warp-uniform
         if (ok) z[u * ldz + row] -= a;
     }
 }
 
 // tile_lower: unit lower triangle of the tile at positions [T0, T0 + nt)
-// (rows T0 .. too), forward substitution in place.
+// (rows T0 .. too), forward substitution in place.  The load part reads only
+// factor data, so a warp can issue it before it waits for the solve's inputs.
 template <typename T>
-__device__ void tile_lower(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
-                           double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+__device__ __forceinline__ void tile_lower_load(const T* __restrict__ Ub, int w, int r, int T0, int nt,
+                                                const int32_t* __restrict__ piv, int lane, T (&Lrow)[32]) {
     const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
-    T Lrow[32];
     const T* Ui = Ub + (int64_t)(T0 - r + (lane < nt ? lane : 0)) * w;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
-        const int lc = __shfl_sync(FULL, lp, c);
-        Lrow[c] = (lane < nt && c < lane) ? Ui[lc] : T(0);
+        Lrow[c] = T(0);
+        if (c + 1 < nt) {                            // nt is warp-uniform
+            const int lc = __shfl_sync(FULL, lp, c);
+            if (lane < nt && c < lane) Lrow[c] = Ui[lc];
+        }
     }
+}
+
+template <typename T>
+__device__ __forceinline__ void tile_lower_solve(const T (&Lrow)[32], int T0, int nt, double* __restrict__ z,
+                                                 int64_t ldz, int nrhs, int lane) {
     for (int u = 0; u < nrhs; ++u) {
         double my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
+        for (int c = 0; c < 31; ++c) {
+            if (c + 1 >= nt) break;                  // only nt - 1 steps
             const double zc = __shfl_sync(FULL, my, c);
             if (c < lane) my -= (double)Lrow[c] * zc;
         }
@@ -1198,30 +1208,56 @@ __device__ void tile_lower(const T* __restrict__ Ub, int w, int r, int T0, int n
     }
 }
 
-// tile_upper: upper triangle of the tile (pivots through dinv), backward
-// substitution in place.
 template <typename T>
-__device__ void tile_upper(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
-                           const T* __restrict__ dinv, double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+__device__ void tile_lower(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
+                           double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+    T Lrow[32];
+    tile_lower_load<T>(Ub, w, r, T0, nt, piv, lane, Lrow);
+    tile_lower_solve<T>(Lrow, T0, nt, z, ldz, nrhs, lane);
+}
+
+// tile_upper: upper triangle of the tile (pivots through dinv), backward
+// substitution in place.  The load part folds the pivots' inverses into the
+// columns, U'_pc = U_pc di_c, so that the dependent chain is one FMA per
+// step on a_p = z_p - sum_c U'_pc a_c, and w_p = di_p a_p at the end.
+template <typename T>
+__device__ __forceinline__ void tile_upper_load(const T* __restrict__ Ub, int w, int r, int T0, int nt,
+                                                const int32_t* __restrict__ piv, const T* __restrict__ dinv,
+                                                int lane, double (&Urow)[32], double& di) {
     const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
-    const double di = (lane < nt) ? (double)dinv[T0 + lane] : 0.0;
-    T Urow[32];
+    di = (lane < nt) ? (double)dinv[T0 + lane] : 0.0;
     const T* Ui = Ub + (int64_t)(T0 - r + (lane < nt ? lane : 0)) * w;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
-        const int lc = __shfl_sync(FULL, lp, c);
-        Urow[c] = (lane < nt && c > lane && c < nt) ? Ui[lc] : T(0);
+        Urow[c] = 0.0;
+        if (c >= 1 && c < nt) {                      // nt is warp-uniform
+            const int lc = __shfl_sync(FULL, lp, c);
+            const double dc = __shfl_sync(FULL, di, c);
+            if (lane < c) Urow[c] = (double)Ui[lc] * dc;
+        }
     }
+}
+
+__device__ __forceinline__ void tile_upper_solve(const double (&Urow)[32], double di, int T0, int nt,
+                                                 double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
     for (int u = 0; u < nrhs; ++u) {
         double my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
 #pragma unroll
-        for (int c = 31; c >= 0; --c) {
-            if (lane == c) my *= di;
-            const double wc = __shfl_sync(FULL, my, c);
-            if (lane < c) my -= (double)Urow[c] * wc;
+        for (int c = 31; c >= 1; --c) {
+            if (c >= nt) continue;                   // only nt - 1 steps
+            const double ac = __shfl_sync(FULL, my, c);
+            if (lane < c) my -= Urow[c] * ac;
         }
-        if (lane < nt) z[u * ldz + T0 + lane] = my;
+        if (lane < nt) z[u * ldz + T0 + lane] = my * di;
     }
+}
+
+template <typename T>
+__device__ void tile_upper(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
+                           const T* __restrict__ dinv, double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+    double Urow[32], di;
+    tile_upper_load<T>(Ub, w, r, T0, nt, piv, dinv, lane, Urow, di);
+    tile_upper_solve(Urow, di, T0, nt, z, ldz, nrhs, lane);
 }
 
 // Sequential mode of the bulk-sequential substitution (Sec. 2.3, Fig. 3:
@@ -1381,9 +1417,10 @@ __device__ bool run_segments(const DevPlan& P, bool bwd, const T* __restrict__ d
 // row of each 32-row tile of a supernode then solves the tile (tile_apply /
 // tile_lower) once its rows have their external part and the earlier tiles
 // are published.  Right-hand sides are columns of z (stride n).
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(WARPS * 32)
 fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
+    if (ONE) nrhs = 1;   // the one-right-hand-side variant: fewer registers, room for the tile prefetch
     if (P.fseg.nseg > 0 && !run_segments<T>(P, false, nullptr, z, nullptr, nrhs, limit)) return;
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
@@ -1401,6 +1438,15 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
         const int q = P.node_inst ? P.node_inst[D] : 0;
         if (q != cq) { cq = q; cached = 0; }
+        // 32-row tiles of a supernode's block: the warp of a tile's last row
+        // owns it and loads its factor part before it waits
+        const int T0 = r + ((i - r) & ~31);
+        const int tlast = min(T0 + 31, e);
+        const int nt = tlast - T0 + 1;
+        const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
+        const T* Ub = PV<T>(P) + P.node_panel_off[D];
+        T Lt[32];
+        if (ONE && s > 1 && i == tlast) tile_lower_load<T>(Ub, w, r, T0, nt, P.piv, lane, Lt);
         const int64_t l0 = P.row_lptr[i], l1 = P.row_lptr[i + 1];
         const int nL = (int)(l1 - l0);
         // entries [0, sp) have sources at least two levels down: summed as
@@ -1440,23 +1486,18 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
             continue;
         }
         if (lane == 0) st_release(P.fwd_row + i, gen);
-        // 32-row tiles of the block: the warp of a tile's last row owns it
-        const int T0 = r + ((i - r) & ~31);
-        const int tlast = min(T0 + 31, e);
         if (i != tlast) continue;
-        const int nt = tlast - T0 + 1;
         int ok = 1;
         for (int k = T0 + lane; k < tlast && ok; k += 32) ok = lane_wait(P.fwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
-        const int w = s + (int)(P.node_tail_off[D + 1] - P.node_tail_off[D]);
-        const T* Ub = PV<T>(P) + P.node_panel_off[D];
         // earlier tiles, each once its owner has published it
         for (int K0 = r; K0 < T0; K0 += 32) {
             if (!warp_wait(P.tile_f + K0 + 31, gen, P.status, K0 + 31, limit)) return;
             tile_apply<T>(Ub, w, r, T0, nt, K0, 32, P.piv, z, n, nrhs, lane);
         }
         __syncwarp();
-        tile_lower<T>(Ub, w, r, T0, nt, P.piv, z, n, nrhs, lane);
+        if (ONE) tile_lower_solve<T>(Lt, T0, nt, z, n, nrhs, lane);
+        else tile_lower<T>(Ub, w, r, T0, nt, P.piv, z, n, nrhs, lane);
         __threadfence();
         __syncwarp();
         if (lane == 0) st_release(P.tile_f + tlast, gen);
@@ -1473,10 +1514,11 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
 // a level); each subtracts its U tail, and the warp of the first row of each
 // 32-row tile of a supernode then back-substitutes the tile once the later
 // tiles are published.  z is overwritten.
-template <typename T>
+template <typename T, bool ONE>
 __global__ void __launch_bounds__(WARPS * 32)
 bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
            double* __restrict__ xh, int nrhs, long long limit) {
+    if (ONE) nrhs = 1;
     if (P.bseg.nseg > 0 && !run_segments<T>(P, true, dinv, z, xh, nrhs, limit)) return;
     const int gen = P.gens[1];
     const int lane = threadIdx.x & 31;
@@ -1499,6 +1541,14 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         const T* Ui = PV<T>(P) + P.node_panel_off[D] + (int64_t)(i - r) * w;
         const int q = P.node_inst ? P.node_inst[D] : 0;
         if (q != cq) { cq = q; cached = 0; }
+        // 32-row tiles of a supernode's block: the warp of a tile's first row
+        // owns it and loads its factor part before it waits
+        const T* Ub = PV<T>(P) + P.node_panel_off[D];
+        const int T0 = r + ((i - r) & ~31);
+        const int tl = min(T0 + 31, e);
+        const int nt = tl - T0 + 1;
+        double Ut[32], dt = 0.0;
+        if (ONE && s > 1 && i == T0) tile_upper_load<T>(Ub, w, r, T0, nt, P.piv, dinv, lane, Ut, dt);
         // tail entries [sp, nT) have sources at least two levels down (the
         // late ones come first in the tail): summed before the level barrier
         const int sp = (P.bwd_split && L >= 1) ? P.bwd_split[D] : nT;
@@ -1532,22 +1582,18 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
             continue;
         }
         if (lane == 0) st_release(P.bwd_row + i, gen);
-        // 32-row tiles of the block: the warp of a tile's first row owns it
-        const int T0 = r + ((i - r) & ~31);
         if (i != T0) continue;
-        const int tl = min(T0 + 31, e);
-        const int nt = tl - T0 + 1;
         int ok = 1;
         for (int k = T0 + 1 + lane; k <= tl && ok; k += 32) ok = lane_wait(P.bwd_row + k, gen, P.status, k, limit);
         if (!__all_sync(FULL, ok)) return;
-        const T* Ub = PV<T>(P) + P.node_panel_off[D];
         // later tiles, last first, each once its owner has published it
         for (int K0 = r + ((e - r) & ~31); K0 > T0; K0 -= 32) {
             if (!warp_wait(P.tile_b + K0, gen, P.status, K0, limit)) return;
             tile_apply<T>(Ub, w, r, T0, nt, K0, min(32, e - K0 + 1), P.piv, z, n, nrhs, lane);
         }
         __syncwarp();
-        tile_upper<T>(Ub, w, r, T0, nt, P.piv, dinv, z, n, nrhs, lane);
+        if (ONE) tile_upper_solve(Ut, dt, T0, nt, z, n, nrhs, lane);
+        else tile_upper<T>(Ub, w, r, T0, nt, P.piv, dinv, z, n, nrhs, lane);
         __syncwarp();
         for (int rr = 0; rr < nrhs; ++rr)
             if (lane < nt) xh[(int64_t)rr * n + P.piv[T0 + lane]] = z[(int64_t)rr * n + T0 + lane];
@@ -2002,11 +2048,19 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     const int blocks = seg ? std::max(grid, 2) : grid;
     if (seg) Q.seq_blocks = std::max(1, std::min(P.seq_blocks, blocks / 2));
     if (e0) cudaEventRecord(e0, st);
-    if (P.lval32) fwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
-    else fwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
-    count_launch();
-    if (P.lval32) bwd_kernel<float><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, d_z, d_xh, nrhs, spin_limit);
-    else bwd_kernel<double><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv, d_z, d_xh, nrhs, spin_limit);
+    if (nrhs == 1) {
+        if (P.lval32) fwd_kernel<float, true><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
+        else fwd_kernel<double, true><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
+        count_launch();
+        if (P.lval32) bwd_kernel<float, true><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, d_z, d_xh, nrhs, spin_limit);
+        else bwd_kernel<double, true><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv, d_z, d_xh, nrhs, spin_limit);
+    } else {
+        if (P.lval32) fwd_kernel<float, false><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
+        else fwd_kernel<double, false><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
+        count_launch();
+        if (P.lval32) bwd_kernel<float, false><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, d_z, d_xh, nrhs, spin_limit);
+        else bwd_kernel<double, false><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv, d_z, d_xh, nrhs, spin_limit);
+    }
     count_launch();
     if (e1) cudaEventRecord(e1, st);
     permute_out_kernel<<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);
