@@ -144,6 +144,9 @@ typedef struct {
     int32_t factor_blocks_per_sm; /* blocks per SM of the factor / substitution launches   */
     int32_t solve_blocks_per_sm;
     int32_t heavy_queue;        /* 1: heavy rows are claimed first (see heavy_ratio)       */
+    int32_t solve_seq_rows;     /* the bulk-sequential threshold in use (hylu_tune may set 0) */
+    int32_t solve_segments[2];  /* segments of light levels of the forward / backward
+                                   substitution in use (0 before the first factorization) */
 } hylu_info;
 
 /* Fill *opt with the defaults listed above.  Returns HYLU_ERR_ARG on NULL. */
@@ -264,11 +267,13 @@ int hylu_graph_launch(hylu_handle* h, void* stream);
  * times; synchronizes; allocates two n-vectors for the duration): blocks per
  * SM (1..4) of the factor launch (fixed at one for the tensor-core variant of
  * the precision form), the heavy-row queue on or off at that grid, and blocks
- * per SM of the substitution launches.  The chosen point stays in the handle
- * (hylu_info reports it: tuned, factor_blocks_per_sm, solve_blocks_per_sm,
- * heavy_queue), the factors of d_vals are left in place, and *blocks_per_sm
- * receives the factor launch's setting.  The substitution is timed with as
- * many right-hand sides as the handle's solves used so far (1 to 8). */
+ * per SM of the substitution launches, with the handle's solve_seq_rows and
+ * with every level in bulk (solve_seq_rows = 0).  The chosen point stays in
+ * the handle (hylu_info reports it: tuned, factor_blocks_per_sm,
+ * solve_blocks_per_sm, heavy_queue, solve_seq_rows), the factors of d_vals
+ * are left in place, and *blocks_per_sm receives the factor launch's
+ * setting.  The substitution is timed with as many right-hand sides as the
+ * handle's solves used so far (1 to 8). */
 int hylu_tune(hylu_handle* h, const double* d_vals, int* blocks_per_sm, void* stream);
 
 /* Synchronize the handle's last stream and report sizes, flop counts,

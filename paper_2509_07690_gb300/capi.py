@@ -65,7 +65,8 @@ class Info(C.Structure):
                 ("analyze_phase_ms", C.c_double * 4), ("gemm_destinations", C.c_int32),
                 ("gemm_tasks", C.c_int32), ("gemm_flops", C.c_double), ("tuned", C.c_int32),
                 ("factor_blocks_per_sm", C.c_int32), ("solve_blocks_per_sm", C.c_int32),
-                ("heavy_queue", C.c_int32)]
+                ("heavy_queue", C.c_int32), ("solve_seq_rows", C.c_int32),
+                ("solve_segments", C.c_int32 * 2)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

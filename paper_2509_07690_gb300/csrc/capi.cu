@@ -6,6 +6,7 @@
 #include <cstring>
 #include <new>
 #include <thread>
+#include <map>
 #include <vector>
 
 #if defined(__has_include)
@@ -60,6 +61,14 @@ struct hylu_handle {
     bool graph_norms_pending = false;    // a replay wrote residual norms not yet read
     int grid_max = 0;
     bool timed_factor = false, timed_solve = false;
+    // device tables of the bulk-sequential substitution, per solve_seq_rows
+    // value built so far (the tuner tries several)
+    struct SeqTables {
+        const int32_t *fwd_task, *bwd_task;
+        int32_t n_fwd_tasks, n_bwd_tasks, seq_blocks;
+        hylu::SegTable fseg, bseg;
+    };
+    std::map<int, SeqTables> seq_tables;
 };
 
 namespace {
@@ -186,36 +195,48 @@ int upload_gemm(hylu_handle* h, cudaStream_t st) {
 }
 
 // Bulk-sequential substitution (Sec. 2.3, Fig. 3): the bulk claim lists and
-// the segments of light levels under opt.solve_seq_rows, for both directions.
-// One block takes the segments of a single system (they form one chain of
-// levels); a batch gets one block per 8 segments, at most an eighth of the
-// launch, since its instances' segments are independent.
-static int upload_seq_segments(hylu_handle* h, cudaStream_t st) {
+// the segments of light levels for solve_seq_rows = max_rows, both
+// directions, built and uploaded once per value and made current.  One block
+// takes the segments of a single system (they form one chain of levels); a
+// batch gets one block per 8 segments (capped at launch), since its
+// instances' segments are independent.
+static int use_seq_segments(hylu_handle* h, int max_rows, cudaStream_t st) {
     hylu::DevPlan& d = h->dp;
-    int32_t nseg_max = 0;
-    for (int dir = 0; dir < 2; ++dir) {
-        hylu::SeqSegments S;
-        hylu::build_seq_segments(h->P, dir == 1, h->opt.solve_seq_rows, S);
-        hylu::SegTable T{};
-        T.nseg = (int32_t)(S.seg_off.size() - 1);
-        nseg_max = std::max(nseg_max, T.nseg);
-        for (std::vector<int32_t>* v : {&S.meta, &S.rows, &S.snodes})
-            if (v->empty()) v->push_back(0);   // keep every array non-empty
-        int32_t *task, *meta, *so, *lr, *ln, *rows, *sn;
-        TRY(upload(h, &task, S.task, st));
-        TRY(upload(h, &meta, S.meta, st));
-        TRY(upload(h, &so, S.seg_off, st));
-        TRY(upload(h, &lr, S.lvl_row, st));
-        TRY(upload(h, &ln, S.lvl_node, st));
-        TRY(upload(h, &rows, S.rows, st));
-        TRY(upload(h, &sn, S.snodes, st));
-        if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;   // S goes out of scope
-        T.meta = meta; T.seg_off = so; T.lvl_row = lr; T.lvl_node = ln; T.rows = rows; T.snodes = sn;
-        if (dir == 0) { d.fwd_task = task; d.n_fwd_tasks = (int32_t)S.task.size(); d.fseg = T; }
-        else { d.bwd_task = task; d.n_bwd_tasks = (int32_t)S.task.size(); d.bseg = T; }
+    max_rows = std::max(0, max_rows);
+    auto it = h->seq_tables.find(max_rows);
+    if (it == h->seq_tables.end()) {
+        hylu_handle::SeqTables Q{};
+        int32_t nseg_max = 0;
+        for (int dir = 0; dir < 2; ++dir) {
+            hylu::SeqSegments S;
+            hylu::build_seq_segments(h->P, dir == 1, max_rows, S);
+            hylu::SegTable T{};
+            T.nseg = (int32_t)(S.seg_off.size() - 1);
+            nseg_max = std::max(nseg_max, T.nseg);
+            for (std::vector<int32_t>* v : {&S.meta, &S.rows, &S.snodes})
+                if (v->empty()) v->push_back(0);   // keep every array non-empty
+            int32_t *task, *meta, *so, *lr, *ln, *rows, *sn;
+            TRY(upload(h, &task, S.task, st));
+            TRY(upload(h, &meta, S.meta, st));
+            TRY(upload(h, &so, S.seg_off, st));
+            TRY(upload(h, &lr, S.lvl_row, st));
+            TRY(upload(h, &ln, S.lvl_node, st));
+            TRY(upload(h, &rows, S.rows, st));
+            TRY(upload(h, &sn, S.snodes, st));
+            if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;   // S goes out of scope
+            T.meta = meta; T.seg_off = so; T.lvl_row = lr; T.lvl_node = ln; T.rows = rows; T.snodes = sn;
+            if (dir == 0) { Q.fwd_task = task; Q.n_fwd_tasks = (int32_t)S.task.size(); Q.fseg = T; }
+            else { Q.bwd_task = task; Q.n_bwd_tasks = (int32_t)S.task.size(); Q.bseg = T; }
+        }
+        const bool batch = !h->P.node_inst.empty();
+        Q.seq_blocks = nseg_max == 0 ? 0 : batch ? std::max(1, (nseg_max + 7) / 8) : 1;
+        it = h->seq_tables.emplace(max_rows, Q).first;
     }
-    const bool batch = !h->P.node_inst.empty();
-    d.seq_blocks = nseg_max == 0 ? 0 : batch ? std::max(1, (nseg_max + 7) / 8) : 1;   // capped at launch
+    const hylu_handle::SeqTables& Q = it->second;
+    d.fwd_task = Q.fwd_task; d.n_fwd_tasks = Q.n_fwd_tasks; d.fseg = Q.fseg;
+    d.bwd_task = Q.bwd_task; d.n_bwd_tasks = Q.n_bwd_tasks; d.bseg = Q.bseg;
+    d.seq_blocks = Q.seq_blocks;
+    h->opt.solve_seq_rows = max_rows;
     return HYLU_OK;
 }
 
@@ -326,7 +347,7 @@ int ensure_uploaded(hylu_handle* h, cudaStream_t st) {
             d.fwd_split = dfs;
             d.bwd_split = dbs;
         }
-        TRY(upload_seq_segments(h, st));
+        TRY(use_seq_segments(h, h->opt.solve_seq_rows, st));
         int32_t *uo, *lo, *ul, *ll, *uc, *lcn;
         TRY(upload(h, &uo, P.ut_order, st));
         TRY(upload(h, &lo, P.lt_order, st));
@@ -718,6 +739,9 @@ int hylu_get_info(hylu_handle* h, hylu_info* info) {
         info->solve_blocks_per_sm = h->uploaded ? h->solve_grid / sms : 0;
     }
     info->heavy_queue = (h->dp.n_heavy > 0) ? 1 : 0;
+    info->solve_seq_rows = h->opt.solve_seq_rows;
+    info->solve_segments[0] = h->uploaded ? h->dp.fseg.nseg : 0;
+    info->solve_segments[1] = h->uploaded ? h->dp.bseg.nseg : 0;
     info->gemm_destinations = h->dp.n_gd;
     info->gemm_tasks = h->dp.n_gtask;
     info->gemm_flops = h->gemm_flops;
@@ -1085,18 +1109,29 @@ static int tune_impl(hylu_handle* h, const double* d_vals, int* blocks_per_sm, v
         std::vector<double> ones(nv, 1.0);
         if (cudaMemcpy(b, ones.data(), sizeof(double) * nv, cudaMemcpyHostToDevice) != cudaSuccess)
             rc = HYLU_ERR_CUDA;
+        // with the bulk-sequential segments of the handle's own solve_seq_rows,
+        // and with every level in bulk (Sec. 2.3, Fig. 3)
         const int maxper = std::max(1, h->grid_max / sms);
         int sbest = h->solve_grid / sms;
+        const int seq0 = h->opt.solve_seq_rows;
+        int seq_best = seq0;
         float best_ms = 1e30f;
-        for (int per = 1; per <= maxper && rc == HYLU_OK; ++per) {
-            h->solve_grid = sms * per;
-            float ms = 0.f;
-            rc = timed([&] {
-                return hylu::launch_solve(h->dp, b, x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
-                                          h->d_dc, nr, h->P.n, h->opt.spin_limit, h->solve_grid, st);
-            }, &ms);
-            if (ms < best_ms) { best_ms = ms; sbest = per; }
+        std::vector<int> seqs = {seq0};
+        if (seq0 > 0) seqs.push_back(0);
+        for (int seq : seqs) {
+            if (rc != HYLU_OK) break;
+            rc = use_seq_segments(h, seq, st);
+            for (int per = 1; per <= maxper && rc == HYLU_OK; ++per) {
+                h->solve_grid = sms * per;
+                float ms = 0.f;
+                rc = timed([&] {
+                    return hylu::launch_solve(h->dp, b, x, h->d_z, h->d_xh, h->d_rowperm, h->d_colperm, h->d_dr,
+                                              h->d_dc, nr, h->P.n, h->opt.spin_limit, h->solve_grid, st);
+                }, &ms);
+                if (ms < best_ms) { best_ms = ms; sbest = per; seq_best = seq; }
+            }
         }
+        if (rc == HYLU_OK) rc = use_seq_segments(h, seq_best, st);
         h->solve_grid = sms * sbest;
     }
     if (b) cudaFree(b);

@@ -120,3 +120,24 @@ def test_segments_batch():
                 assert np.linalg.norm(x[r, sl] - xo) <= 1e-9 * np.linalg.norm(xo), (v, q, r)
     assert bs.get_info().device_status == 0
     bs.close()
+
+
+def test_tuner_picks_a_segment_threshold():
+    """hylu_tune times the substitution with the handle's solve_seq_rows and
+    with every level in bulk, keeps the faster, and reports it; the solve is
+    right either way."""
+    torch = _torch()
+    A = synth.circuit(12000, seed=9)
+    s = Solver(A.n, A.rowptr, A.col, A.val, solve_seq_rows=16)
+    dv = torch.from_numpy(A.val).cuda()
+    s.factor(dv)
+    info = s.get_info()
+    assert info.solve_seq_rows == 16 and sum(info.solve_segments) > 0
+    capi.hylu_tune(s.h, dv.data_ptr())
+    info = s.get_info()
+    assert info.tuned == 1 and info.solve_seq_rows in (16, 0)
+    assert (sum(info.solve_segments) == 0) == (info.solve_seq_rows == 0)
+    _, b = synth.rhs(A, 3, 1)
+    x = s.solve(torch.from_numpy(b[0]).cuda()).cpu().numpy()
+    assert oracle.backward_error(A.n, A.rowptr, A.col, A.val, x, b[0]) <= 1e-12
+    s.close()
