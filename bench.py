@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--ordering-trial", action="store_true",
                     help="circuit workload: untimed AMD / nested dissection trial first, the faster one timed")
     ap.add_argument("--no-precision-form", action="store_true",
-                    help="convdiff3d_64: skip the second measurement (the precision form)")
+                    help="convdiff3d_64: skip the measurements of the precision form (its own and the secondary configurations')")
     ap.add_argument("--no-secondary", action="store_true",
                     help="convdiff3d_64: skip the secondary configurations (5-point grid, circuit, "
                          "anisotropic diffusion) measured into the same line")
@@ -641,11 +641,18 @@ def run_hylu(args, ws, rank, local):
                 args.steps = max(4, min(args.steps, 8))
                 try:
                     o2 = measure_hylu(args, ws, rank, local, ordering_for(wl), sub=True)
+                    o2p = None
+                    if not args.no_precision_form:
+                        # the precision form on the same matrix, against its FP64 line
+                        gc.collect()
+                        o2p = measure_hylu(args, ws, rank, local, ordering_for(wl), fp32=True, sub=True)
                 finally:
                     set_workload(saved_w)
                     args.steps = saved_s
                 if o2 is not None:
                     sec[wl] = secondary_summary(o2)
+                    if o2p is not None:
+                        sec[wl]["precision_form"] = precision_summary(o2, o2p)
             if out is not None and sec:
                 out["secondary_workloads"] = sec
         if out is not None:

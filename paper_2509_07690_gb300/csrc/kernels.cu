@@ -1000,26 +1000,28 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
 }
 
 // -------------------------------------------------------------- solve
+template <typename A>
 __global__ void permute_in_kernel(int32_t n, const int32_t* __restrict__ rowperm,
                                   const double* __restrict__ dr, const double* __restrict__ b,
-                                  double* __restrict__ bh, int nrhs, int ld, int32_t* gens) {
+                                  A* __restrict__ bh, int nrhs, int ld, int32_t* gens) {
     if (blockIdx.x == 0 && threadIdx.x == 0) gens[1] += 1;   // substitution generation of this call
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n * nrhs;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(q / n), i = (int)(q % n);
         const int o = rowperm[i];
-        bh[q] = dr[o] * b[(int64_t)rr * ld + o];
+        bh[q] = (A)(dr[o] * b[(int64_t)rr * ld + o]);
     }
 }
 
+template <typename A>
 __global__ void permute_out_kernel(int32_t n, const int32_t* __restrict__ colperm,
-                                   const double* __restrict__ dc, const double* __restrict__ xh,
+                                   const double* __restrict__ dc, const A* __restrict__ xh,
                                    double* __restrict__ x, int nrhs, int ld) {
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < (int64_t)n * nrhs;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int rr = (int)(q / n), k = (int)(q % n);
         const int o = colperm[k];
-        x[(int64_t)rr * ld + o] = dc[o] * xh[q];
+        x[(int64_t)rr * ld + o] = dc[o] * (double)xh[q];
     }
 }
 
@@ -1040,9 +1042,9 @@ __device__ __forceinline__ bool lane_wait(const int* flag, int gen, int* status,
 // Warp-wide sum of v[t] * x[c[t]], t < m, with UNR independent gathers in
 // flight per lane; the result is valid in every lane.
 template <typename T>
-__device__ __forceinline__ double sparse_dot(const T* __restrict__ v, const int32_t* __restrict__ c, int m,
-                                             const double* __restrict__ x, int lane) {
-    double acc[UNR];
+__device__ __forceinline__ T sparse_dot(const T* __restrict__ v, const int32_t* __restrict__ c, int m,
+                                             const T* __restrict__ x, int lane) {
+    T acc[UNR];
 #pragma unroll
     for (int u = 0; u < UNR; ++u) acc[u] = 0.0;
     for (int t0 = 0; t0 < m; t0 += 32 * UNR) {
@@ -1056,9 +1058,9 @@ __device__ __forceinline__ double sparse_dot(const T* __restrict__ v, const int3
         }
 #pragma unroll
         for (int u = 0; u < UNR; ++u)
-            if (cc[u] >= 0) acc[u] = fma((double)vv[u], x[cc[u]], acc[u]);
+            if (cc[u] >= 0) acc[u] = fma((T)vv[u], x[cc[u]], acc[u]);
     }
-    double a = 0.0;
+    T a = 0.0;
 #pragma unroll
     for (int u = 0; u < UNR; ++u) a += acc[u];
     for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
@@ -1071,9 +1073,9 @@ __device__ __forceinline__ double sparse_dot(const T* __restrict__ v, const int3
 // valid in every lane.
 template <typename T, int RB>
 __device__ __forceinline__ void sparse_dot_rhs(const T* __restrict__ v, const int32_t* __restrict__ c, int m,
-                                               const double* __restrict__ x, int64_t ldx, int nr, int lane,
-                                               double* out) {
-    double acc[RB];
+                                               const T* __restrict__ x, int64_t ldx, int nr, int lane,
+                                               T* out) {
+    T acc[RB];
 #pragma unroll
     for (int u = 0; u < RB; ++u) acc[u] = 0.0;
     for (int t0 = 0; t0 < m; t0 += 64) {
@@ -1090,12 +1092,12 @@ __device__ __forceinline__ void sparse_dot_rhs(const T* __restrict__ v, const in
             if (cc[b] >= 0) {
 #pragma unroll
                 for (int u = 0; u < RB; ++u)
-                    if (u < nr) acc[u] = fma((double)vv[b], x[u * ldx + cc[b]], acc[u]);
+                    if (u < nr) acc[u] = fma((T)vv[b], x[u * ldx + cc[b]], acc[u]);
             }
     }
 #pragma unroll
     for (int u = 0; u < RB; ++u) {
-        double a = acc[u];
+        T a = acc[u];
         for (int off = 16; off; off >>= 1) a += __shfl_xor_sync(FULL, a, off);
         out[u] = a;
     }
@@ -1153,7 +1155,7 @@ __device__ __forceinline__ void node_complete(int* done, const int* count, int L
 // loads in flight together), then one FMA chain per right-hand side.
 template <typename T>
 __device__ void tile_apply(const T* __restrict__ Ub, int w, int r, int R0, int nr_rows, int P0, int nt,
-                           const int32_t* __restrict__ piv, double* __restrict__ z, int64_t ldz, int nrhs,
+                           const int32_t* __restrict__ piv, T* __restrict__ z, int64_t ldz, int nrhs,
                            int lane) {
     const int lp = (lane < nt) ? piv[P0 + lane] - r : 0;
     const int row = R0 + lane;
@@ -1166,11 +1168,11 @@ __device__ void tile_apply(const T* __restrict__ Ub, int w, int r, int R0, int n
         Rrow[c] = (ok && c < nt) ? Ur[lc] : T(0);
     }
     for (int u = 0; u < nrhs; ++u) {
-        const double zt = (lane < nt) ? z[u * ldz + P0 + lane] : 0.0;
-        double a = 0.0;
+        const T zt = (lane < nt) ? z[u * ldz + P0 + lane] : 0.0;
+        T a = 0.0;
 #pragma unroll
         for (int c = 0; c < 32; ++c)
-            if (c < nt) a = fma((double)Rrow[c], __shfl_sync(FULL, zt, c), a);   // nt is warp-uniform
+            if (c < nt) a = fma((T)Rrow[c], __shfl_sync(FULL, zt, c), a);   // nt is warp-uniform
         if (ok) z[u * ldz + row] -= a;
     }
 }
@@ -1194,15 +1196,15 @@ __device__ __forceinline__ void tile_lower_load(const T* __restrict__ Ub, int w,
 }
 
 template <typename T>
-__device__ __forceinline__ void tile_lower_solve(const T (&Lrow)[32], int T0, int nt, double* __restrict__ z,
+__device__ __forceinline__ void tile_lower_solve(const T (&Lrow)[32], int T0, int nt, T* __restrict__ z,
                                                  int64_t ldz, int nrhs, int lane) {
     for (int u = 0; u < nrhs; ++u) {
-        double my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
+        T my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
 #pragma unroll
         for (int c = 0; c < 31; ++c) {
             if (c + 1 >= nt) break;                  // only nt - 1 steps
-            const double zc = __shfl_sync(FULL, my, c);
-            if (c < lane) my -= (double)Lrow[c] * zc;
+            const T zc = __shfl_sync(FULL, my, c);
+            if (c < lane) my -= (T)Lrow[c] * zc;
         }
         if (lane < nt) z[u * ldz + T0 + lane] = my;
     }
@@ -1210,7 +1212,7 @@ __device__ __forceinline__ void tile_lower_solve(const T (&Lrow)[32], int T0, in
 
 template <typename T>
 __device__ void tile_lower(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
-                           double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+                           T* __restrict__ z, int64_t ldz, int nrhs, int lane) {
     T Lrow[32];
     tile_lower_load<T>(Ub, w, r, T0, nt, piv, lane, Lrow);
     tile_lower_solve<T>(Lrow, T0, nt, z, ldz, nrhs, lane);
@@ -1223,29 +1225,30 @@ __device__ void tile_lower(const T* __restrict__ Ub, int w, int r, int T0, int n
 template <typename T>
 __device__ __forceinline__ void tile_upper_load(const T* __restrict__ Ub, int w, int r, int T0, int nt,
                                                 const int32_t* __restrict__ piv, const T* __restrict__ dinv,
-                                                int lane, double (&Urow)[32], double& di) {
+                                                int lane, T (&Urow)[32], T& di) {
     const int lp = (lane < nt) ? piv[T0 + lane] - r : 0;
-    di = (lane < nt) ? (double)dinv[T0 + lane] : 0.0;
+    di = (lane < nt) ? (T)dinv[T0 + lane] : 0.0;
     const T* Ui = Ub + (int64_t)(T0 - r + (lane < nt ? lane : 0)) * w;
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
         Urow[c] = 0.0;
         if (c >= 1 && c < nt) {                      // nt is warp-uniform
             const int lc = __shfl_sync(FULL, lp, c);
-            const double dc = __shfl_sync(FULL, di, c);
-            if (lane < c) Urow[c] = (double)Ui[lc] * dc;
+            const T dc = __shfl_sync(FULL, di, c);
+            if (lane < c) Urow[c] = (T)Ui[lc] * dc;
         }
     }
 }
 
-__device__ __forceinline__ void tile_upper_solve(const double (&Urow)[32], double di, int T0, int nt,
-                                                 double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+template <typename T>
+__device__ __forceinline__ void tile_upper_solve(const T (&Urow)[32], T di, int T0, int nt,
+                                                 T* __restrict__ z, int64_t ldz, int nrhs, int lane) {
     for (int u = 0; u < nrhs; ++u) {
-        double my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
+        T my = (lane < nt) ? z[u * ldz + T0 + lane] : 0.0;
 #pragma unroll
         for (int c = 31; c >= 1; --c) {
             if (c >= nt) continue;                   // only nt - 1 steps
-            const double ac = __shfl_sync(FULL, my, c);
+            const T ac = __shfl_sync(FULL, my, c);
             if (lane < c) my -= Urow[c] * ac;
         }
         if (lane < nt) z[u * ldz + T0 + lane] = my * di;
@@ -1254,8 +1257,8 @@ __device__ __forceinline__ void tile_upper_solve(const double (&Urow)[32], doubl
 
 template <typename T>
 __device__ void tile_upper(const T* __restrict__ Ub, int w, int r, int T0, int nt, const int32_t* __restrict__ piv,
-                           const T* __restrict__ dinv, double* __restrict__ z, int64_t ldz, int nrhs, int lane) {
-    double Urow[32], di;
+                           const T* __restrict__ dinv, T* __restrict__ z, int64_t ldz, int nrhs, int lane) {
+    T Urow[32], di;
     tile_upper_load<T>(Ub, w, r, T0, nt, piv, dinv, lane, Urow, di);
     tile_upper_solve(Urow, di, T0, nt, z, ldz, nrhs, lane);
 }
@@ -1277,7 +1280,7 @@ __device__ __forceinline__ void seg_stamp(const DevPlan& P, const SegTable& S, i
 }
 
 template <typename T>
-__device__ bool fwd_segment(const DevPlan& P, int g, double* __restrict__ z, int nrhs, long long limit) {
+__device__ bool fwd_segment(const DevPlan& P, int g, T* __restrict__ z, int nrhs, long long limit) {
     const SegTable& S = P.fseg;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = P.n;
@@ -1291,7 +1294,7 @@ __device__ bool fwd_segment(const DevPlan& P, int g, double* __restrict__ z, int
             const int64_t l0 = P.row_lptr[i];
             const int nL = (int)(P.row_lptr[i + 1] - l0);
             for (int r0 = 0; r0 < nrhs; r0 += 8) {
-                double a[8];
+                T a[8];
                 const int nr = min(8, nrhs - r0);
                 if (nr == 1) a[0] = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, nL, z + (int64_t)r0 * n, lane);
                 else sparse_dot_rhs<T, 8>(LV<T>(P) + l0, P.lcols + l0, nL, z + (int64_t)r0 * n, n, nr, lane, a);
@@ -1326,8 +1329,8 @@ __device__ bool fwd_segment(const DevPlan& P, int g, double* __restrict__ z, int
 }
 
 template <typename T>
-__device__ bool bwd_segment(const DevPlan& P, int g, const T* __restrict__ dinv, double* __restrict__ z,
-                            double* __restrict__ xh, int nrhs, long long limit) {
+__device__ bool bwd_segment(const DevPlan& P, int g, const T* __restrict__ dinv, T* __restrict__ z,
+                            T* __restrict__ xh, int nrhs, long long limit) {
     const SegTable& S = P.bseg;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int n = P.n;
@@ -1344,14 +1347,14 @@ __device__ bool bwd_segment(const DevPlan& P, int g, const T* __restrict__ dinv,
             const int nT = (int)(P.node_tail_off[D + 1] - t0);
             const T* Ui = PV<T>(P) + P.node_panel_off[D] + (int64_t)(i - r) * (s + nT);
             for (int r0 = 0; r0 < nrhs; r0 += 8) {
-                double a[8];
+                T a[8];
                 const int nr = min(8, nrhs - r0);
                 if (nr == 1) a[0] = sparse_dot<T>(Ui + s, P.tcols + t0, nT, xh + (int64_t)r0 * n, lane);
                 else sparse_dot_rhs<T, 8>(Ui + s, P.tcols + t0, nT, xh + (int64_t)r0 * n, n, nr, lane, a);
                 if (lane == 0)
                     for (int u = 0; u < nr; ++u) {
                         const int64_t o = (int64_t)(r0 + u) * n + i;
-                        if (s == 1) xh[o] = (z[o] - a[u]) * (double)dinv[i];
+                        if (s == 1) xh[o] = (z[o] - a[u]) * (T)dinv[i];
                         else z[o] -= a[u];
                     }
             }
@@ -1389,8 +1392,8 @@ __device__ bool bwd_segment(const DevPlan& P, int g, const T* __restrict__ dinv,
 // they join the bulk claims; the other blocks go to the bulk claims directly.
 // Decisions are block-uniform (a shared word between two barriers).
 template <typename T>
-__device__ bool run_segments(const DevPlan& P, bool bwd, const T* __restrict__ dinv, double* __restrict__ z,
-                             double* __restrict__ xh, int nrhs, long long limit) {
+__device__ bool run_segments(const DevPlan& P, bool bwd, const T* __restrict__ dinv, T* __restrict__ z,
+                             T* __restrict__ xh, int nrhs, long long limit) {
     __shared__ int s_claim;
     const SegTable& S = bwd ? P.bseg : P.fseg;
     if (threadIdx.x == 0) s_claim = atomicAdd(P.status + (bwd ? ST_ROLE_B : ST_ROLE_F), 1);
@@ -1419,7 +1422,7 @@ __device__ bool run_segments(const DevPlan& P, bool bwd, const T* __restrict__ d
 // are published.  Right-hand sides are columns of z (stride n).
 template <typename T, bool ONE>
 __global__ void __launch_bounds__(WARPS * 32)
-fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
+fwd_kernel(DevPlan P, T* __restrict__ z, int nrhs, long long limit) {
     if (ONE) nrhs = 1;   // the one-right-hand-side variant: fewer registers, room for the tile prefetch
     if (P.fseg.nseg > 0 && !run_segments<T>(P, false, nullptr, z, nullptr, nrhs, limit)) return;
     const int gen = P.gens[1];
@@ -1453,7 +1456,7 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         // soon as those levels complete, before the level barrier
         const int sp = (P.fwd_split && L >= 1) ? P.fwd_split[i] : 0;
         if (nrhs == 1) {
-            double a = 0.0;
+            T a = 0.0;
             if (sp > 0) {
                 if (!__all_sync(FULL, wait_level(P.wm_f + q, L - 1, cached, P.status, limit))) return;
                 a = sparse_dot<T>(LV<T>(P) + l0, P.lcols + l0, sp, z, lane);
@@ -1464,7 +1467,7 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
         } else {
             if (sp > 0 && !__all_sync(FULL, wait_level(P.wm_f + q, L - 1, cached, P.status, limit))) return;
             for (int r0 = 0; r0 < nrhs; r0 += 8) {
-                double a[8], b[8];
+                T a[8], b[8];
                 const int nr = min(8, nrhs - r0);
                 for (int u = 0; u < 8; ++u) a[u] = 0.0;
                 if (sp > 0)
@@ -1516,8 +1519,8 @@ fwd_kernel(DevPlan P, double* __restrict__ z, int nrhs, long long limit) {
 // tiles are published.  z is overwritten.
 template <typename T, bool ONE>
 __global__ void __launch_bounds__(WARPS * 32)
-bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
-           double* __restrict__ xh, int nrhs, long long limit) {
+bwd_kernel(DevPlan P, const T* __restrict__ dinv, T* __restrict__ z,
+           T* __restrict__ xh, int nrhs, long long limit) {
     if (ONE) nrhs = 1;
     if (P.bseg.nseg > 0 && !run_segments<T>(P, true, dinv, z, xh, nrhs, limit)) return;
     const int gen = P.gens[1];
@@ -1547,14 +1550,14 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
         const int T0 = r + ((i - r) & ~31);
         const int tl = min(T0 + 31, e);
         const int nt = tl - T0 + 1;
-        double Ut[32], dt = 0.0;
+        T Ut[32], dt = 0.0;
         if (ONE && s > 1 && i == T0) tile_upper_load<T>(Ub, w, r, T0, nt, P.piv, dinv, lane, Ut, dt);
         // tail entries [sp, nT) have sources at least two levels down (the
         // late ones come first in the tail): summed before the level barrier
         const int sp = (P.bwd_split && L >= 1) ? P.bwd_split[D] : nT;
         if (sp < nT && !__all_sync(FULL, wait_level(P.wm_b + q, L - 1, cached, P.status, limit))) return;
         for (int r0 = 0; r0 < nrhs; r0 += 8) {
-            double a[8], b[8];
+            T a[8], b[8];
             const int nr = min(8, nrhs - r0);
             for (int u = 0; u < 8; ++u) { a[u] = 0.0; b[u] = 0.0; }
             if (sp < nT) {
@@ -1568,7 +1571,7 @@ bwd_kernel(DevPlan P, const T* __restrict__ dinv, double* __restrict__ z,
             if (lane == 0)
                 for (int u = 0; u < nr; ++u) {
                     const int64_t o = (int64_t)(r0 + u) * n + i;
-                    if (s == 1) xh[o] = (z[o] - a[u]) * (double)dinv[i];
+                    if (s == 1) xh[o] = (z[o] - a[u]) * (T)dinv[i];
                     else z[o] -= a[u];
                 }
         }
@@ -2039,7 +2042,13 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     if (cudaMemsetAsync(P.wm_f, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.wm_b, 0, sizeof(int32_t) * P.n_inst, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.bwd_done, 0, sizeof(int32_t) * P.n_bwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
-    permute_in_kernel<<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld, P.gens);
+    // the substitution computes in the factors' type: FP32 factors (the
+    // precision form) are solved in FP32, their refinement's residual and
+    // update stay in FP64; the FP32 vectors use the first halves of z and xh
+    float* z32 = reinterpret_cast<float*>(d_z);
+    float* xh32 = reinterpret_cast<float*>(d_xh);
+    if (P.lval32) permute_in_kernel<float><<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, z32, nrhs, ld, P.gens);
+    else permute_in_kernel<double><<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld, P.gens);
     count_launch();
     // the segments' rows are not in the bulk claim lists: at least one block
     // takes the segments and at least half of the launch stays in bulk
@@ -2049,21 +2058,22 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     if (seg) Q.seq_blocks = std::max(1, std::min(P.seq_blocks, blocks / 2));
     if (e0) cudaEventRecord(e0, st);
     if (nrhs == 1) {
-        if (P.lval32) fwd_kernel<float, true><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
+        if (P.lval32) fwd_kernel<float, true><<<blocks, WARPS * 32, 0, st>>>(Q, z32, nrhs, spin_limit);
         else fwd_kernel<double, true><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
         count_launch();
-        if (P.lval32) bwd_kernel<float, true><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, d_z, d_xh, nrhs, spin_limit);
+        if (P.lval32) bwd_kernel<float, true><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, z32, xh32, nrhs, spin_limit);
         else bwd_kernel<double, true><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv, d_z, d_xh, nrhs, spin_limit);
     } else {
-        if (P.lval32) fwd_kernel<float, false><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
+        if (P.lval32) fwd_kernel<float, false><<<blocks, WARPS * 32, 0, st>>>(Q, z32, nrhs, spin_limit);
         else fwd_kernel<double, false><<<blocks, WARPS * 32, 0, st>>>(Q, d_z, nrhs, spin_limit);
         count_launch();
-        if (P.lval32) bwd_kernel<float, false><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, d_z, d_xh, nrhs, spin_limit);
+        if (P.lval32) bwd_kernel<float, false><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv32, z32, xh32, nrhs, spin_limit);
         else bwd_kernel<double, false><<<blocks, WARPS * 32, 0, st>>>(Q, P.dinv, d_z, d_xh, nrhs, spin_limit);
     }
     count_launch();
     if (e1) cudaEventRecord(e1, st);
-    permute_out_kernel<<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);
+    if (P.lval32) permute_out_kernel<float><<<eb, 256, 0, st>>>(P.n, colperm, dc, xh32, d_x, nrhs, ld);
+    else permute_out_kernel<double><<<eb, 256, 0, st>>>(P.n, colperm, dc, d_xh, d_x, nrhs, ld);
     count_launch();
     return check("solve");
 }
