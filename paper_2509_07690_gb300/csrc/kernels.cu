@@ -2030,12 +2030,41 @@ int launch_factor(const DevPlan& P, const double* d_vals, int64_t nnz_a,
     return check("factor");
 }
 
+// Blocks of the substitution kernels that can be resident at once (the
+// fewest over the forward / backward and one / several right-hand-side
+// variants of the factors' type), cached per device and type.
+static int solve_resident_blocks(bool fp32) {
+    static int cache[64][2] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    int& c = cache[dev][fp32 ? 1 : 0];
+    if (c > 0) return c;
+    int sms = 0, per[4] = {0, 0, 0, 0};
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (fp32) {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], fwd_kernel<float, true>, WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], fwd_kernel<float, false>, WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], bwd_kernel<float, true>, WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], bwd_kernel<float, false>, WARPS * 32, 0);
+    } else {
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[0], fwd_kernel<double, true>, WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[1], fwd_kernel<double, false>, WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[2], bwd_kernel<double, true>, WARPS * 32, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per[3], bwd_kernel<double, false>, WARPS * 32, 0);
+    }
+    c = sms * std::max(1, std::min(std::min(per[0], per[1]), std::min(per[2], per[3])));
+    return c;
+}
+
 int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, double* d_xh,
                  const int32_t* rowperm, const int32_t* colperm, const double* dr, const double* dc,
                  int nrhs, int ld, long long spin_limit, int grid, cudaStream_t st,
                  cudaEvent_t e0, cudaEvent_t e1) {
     const int64_t tot = (int64_t)P.n * nrhs;
     const int eb = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
+    // segments need a block of their own beside resident bulk blocks
+    if ((P.fseg.nseg > 0 || P.bseg.nseg > 0) && (grid < 2 || solve_resident_blocks(P.lval32 != nullptr) < 2))
+        return HYLU_ERR_INTERNAL;
     if (cudaMemsetAsync(P.status + ST_CNT_FWD, 0, sizeof(int32_t) * 4, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.status + ST_SEG_F, 0, sizeof(int32_t) * 2, st) != cudaSuccess) return HYLU_ERR_CUDA;
     if (cudaMemsetAsync(P.fwd_done, 0, sizeof(int32_t) * P.n_fwd_levels, st) != cudaSuccess) return HYLU_ERR_CUDA;
@@ -2051,11 +2080,15 @@ int launch_solve(const DevPlan& P, const double* d_b, double* d_x, double* d_z, 
     else permute_in_kernel<double><<<eb, 256, 0, st>>>(P.n, rowperm, dr, d_b, d_z, nrhs, ld, P.gens);
     count_launch();
     // the segments' rows are not in the bulk claim lists: at least one block
-    // takes the segments and at least half of the launch stays in bulk
+    // takes the segments, and at least three quarters of the blocks that can
+    // be resident at once stay in bulk (the first blocks to start take the
+    // segments, so a launch larger than what is resident must not let them
+    // fill the GPU: their waits need bulk rows)
     DevPlan Q = P;
     const bool seg = P.fseg.nseg > 0 || P.bseg.nseg > 0;
-    const int blocks = seg ? std::max(grid, 2) : grid;
-    if (seg) Q.seq_blocks = std::max(1, std::min(P.seq_blocks, blocks / 2));
+    const int resident = seg ? solve_resident_blocks(P.lval32 != nullptr) : 0;
+    const int blocks = grid;
+    if (seg) Q.seq_blocks = std::max(1, std::min(P.seq_blocks, std::min(resident, blocks) / 4));
     if (e0) cudaEventRecord(e0, st);
     if (nrhs == 1) {
         if (P.lval32) fwd_kernel<float, true><<<blocks, WARPS * 32, 0, st>>>(Q, z32, nrhs, spin_limit);

@@ -141,3 +141,31 @@ def test_tuner_picks_a_segment_threshold():
     x = s.solve(torch.from_numpy(b[0]).cuda()).cpu().numpy()
     assert oracle.backward_error(A.n, A.rowptr, A.col, A.val, x, b[0]) <= 1e-12
     s.close()
+
+
+def test_many_segments_larger_launch_than_resident():
+    """A batch with thousands of segments: the blocks that take the segments
+    are the first to start, so their number is capped by what can be resident
+    at once (a quarter of it), whatever the launch size; otherwise they could
+    fill the GPU and wait for bulk rows that no resident block claims.  A short
+    spin limit turns such a deadlock into an error within seconds."""
+    torch = _torch()
+    mats = [synth.circuit(400 + (q % 7) * 50, seed=900 + q) for q in range(700)]
+    bs = BatchSolver([(m.n, m.rowptr, m.col, m.val) for m in mats], 4, solve_seq_rows=8, spin_limit=1 << 22)
+    assert min(_nseg(bs.h, 8)) > 2000
+    k = len(mats)
+    vals = [[m.val if v == 0 else synth.circuit_values(m.rowptr, m.col, 40 + v * 1000 + q)
+             for q, m in enumerate(mats)] for v in range(4)]
+    bs.factor(torch.from_numpy(bs.concat_values(vals)).cuda())
+    b = np.random.default_rng(6).standard_normal((2, bs.n))
+    for _ in range(2):
+        x = bs.solve(torch.from_numpy(b).cuda()).cpu().numpy()
+    assert bs.get_info().device_status == 0
+    for q in range(0, 4 * k, 97):
+        v, sidx = divmod(q, k)
+        m = mats[sidx]
+        rb = bs.row_base[q]
+        for r in range(2):
+            assert oracle.backward_error(m.n, m.rowptr, m.col, vals[v][sidx], x[r, rb:rb + m.n],
+                                         b[r, rb:rb + m.n]) <= 1e-12
+    bs.close()
