@@ -910,6 +910,7 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
         // the diagonal block (by label) of the row: lb for a supernode row,
         // the panel (one entry) for a standalone row
         T* xd = (s > 1) ? lb : pn.x;
+        int dlab = 0;   // label offset of the row's pivot
         if (s > 1) {
             // (a diag task reads from L2: the panel row was written by other SMs)
             for (int c = lane; c < s; c += 32) lb[c] = diag_only ? __ldcg(pn.x + c) : pn.x[c];
@@ -917,41 +918,78 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
             // ---- diagonal-block step: earlier rows of the own supernode, each
             //      as soon as its own diagonal-block step is published
             const T* Ub = PV<T>(P) + P.node_panel_off[D];
+            int pv[SN_SMEM / 32];   // position of label c = lane + 32 m
             for (int k = r; k < i; ++k) {
                 if (!warp_wait(P.dready + k, gen, P.status, k, limit, wp)) return;
-                const int lab = ld_relaxed(P.piv + k) - r;
+                // row k's pivot, inverse, block row and the positions of the
+                // labels, all loaded together (none depends on another): a
+                // label at a position past k stays past k under later swaps
+                const int pk = ld_relaxed(P.piv + k);
+                const T dk = dinv[k];
                 const T* Uk = Ub + (int64_t)(k - r) * w;
-                const T l = lb[lab] * dinv[k];
-                for (int c = lane; c < s; c += 32)
-                    if (c != lab && ld_relaxed(P.pinv + r + c) > k) lb[c] -= l * Uk[c];
+                T uk[SN_SMEM / 32];
+#pragma unroll
+                for (int m = 0; m < SN_SMEM / 32; ++m) {
+                    const int c = lane + 32 * m;
+                    uk[m] = (c < s) ? Uk[c] : T(0);
+                    pv[m] = (c < s) ? ld_relaxed(P.pinv + r + c) : -1;
+                }
+                const int lab = pk - r;
+                const T l = lb[lab] * dk;
+#pragma unroll
+                for (int m = 0; m < SN_SMEM / 32; ++m) {
+                    const int c = lane + 32 * m;
+                    if (c < s && c != lab && pv[m] > k) lb[c] -= l * uk[m];
+                }
                 __syncwarp();
                 if (lane == 0) lb[lab] = l;
                 __syncwarp();
             }
             // ---- supernode diagonal pivoting: largest |x| among positions i..e,
-            //      first position on ties
-            double best = -1.0;
-            int bp = i;
-            for (int p = i + lane; p <= e; p += 32) {
-                const double a = fabs((double)lb[P.piv[p] - r]);
-                if (a > best) { best = a; bp = p; }
+            //      first position on ties.  The labels' positions are the ones
+            //      loaded for row i - 1's step (no row past i - 1 swaps before
+            //      row i); the first row reads them.  Compared in the factors'
+            //      type: the order is the same as in FP64.
+            if (i == r) {
+#pragma unroll
+                for (int m = 0; m < SN_SMEM / 32; ++m) {
+                    const int c = lane + 32 * m;
+                    pv[m] = (c < s) ? ld_relaxed(P.pinv + r + c) : -1;
+                }
+            }
+            T best = T(-1);
+            int bpos = INT_MAX, blab = -1, alab = -1;   // best position and label; the label at i
+#pragma unroll
+            for (int m = 0; m < SN_SMEM / 32; ++m) {
+                const int c = lane + 32 * m;
+                if (c < s && pv[m] >= i) {
+                    const T a = fabs(lb[c]);
+                    if (a > best || (a == best && pv[m] < bpos)) { best = a; bpos = pv[m]; blab = c; }
+                    if (pv[m] == i) alab = c;
+                }
             }
             for (int off = 16; off; off >>= 1) {
-                const double ob = __shfl_down_sync(FULL, best, off);
-                const int op = __shfl_down_sync(FULL, bp, off);
-                if (ob > best || (ob == best && op < bp)) { best = ob; bp = op; }
+                const T ob = __shfl_down_sync(FULL, best, off);
+                const int op = __shfl_down_sync(FULL, bpos, off);
+                const int ol = __shfl_down_sync(FULL, blab, off);
+                const int oa = __shfl_down_sync(FULL, alab, off);
+                if (ob > best || (ob == best && op < bpos)) { best = ob; bpos = op; blab = ol; }
+                alab = max(alab, oa);
             }
-            bp = __shfl_sync(FULL, bp, 0);
-            if (lane == 0 && bp != i) {
-                const int a = P.piv[i], b = P.piv[bp];
-                P.piv[i] = b; P.piv[bp] = a;
-                P.pinv[b] = i; P.pinv[a] = bp;
+            bpos = __shfl_sync(FULL, bpos, 0);
+            blab = __shfl_sync(FULL, blab, 0);
+            alab = __shfl_sync(FULL, alab, 0);
+            if (bpos == INT_MAX) { bpos = i; blab = alab; }   // no comparable value (NaN): keep position i
+            if (lane == 0 && bpos != i) {
+                P.piv[i] = r + blab; P.piv[bpos] = r + alab;
+                P.pinv[r + blab] = i; P.pinv[r + alab] = bpos;
             }
+            dlab = blab;
             __syncwarp();
         }
         // ---- pivot, small-pivot perturbation
         if (lane == 0) {
-            const int dl = (s > 1) ? (P.piv[i] - r) : 0;
+            const int dl = (s > 1) ? dlab : 0;
             // the small-pivot check is taken in FP64 whatever the factor precision
             double u = (double)((diag_only && s == 1) ? __ldcg(xd + dl) : xd[dl]);
             if (fabs(u) < tau) {
