@@ -792,19 +792,49 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                 const int wS = sS + nTS;
                 const T* __restrict__ U = PV<T>(P) + pS;
                 const int32_t* __restrict__ tcS = P.tcols + tS;
+                // the source's pivot inverses staged in shared memory (the
+                // window's prefetch area is free until the next window)
+                T* dS = &ws->pfu[0][0];
                 for (int p = lane; p < sS; p += 32) {
                     const int lab = P.piv[rS + p] - rS;
                     pb[p] = lab;
                     lb[p] = spa ? spa[rS + lab] : xl[tt + lab];
+                    dS[p] = dinv[rS + p];
                 }
                 __syncwarp();
-                for (int p = 0; p < sS; ++p) {
-                    const T* Up = U + (int64_t)p * wS;
-                    const T lp = lb[p] * dinv[rS + p];
-                    __syncwarp();
-                    for (int qq = p + 1 + lane; qq < sS; qq += 32) lb[qq] -= lp * Up[pb[qq]];
-                    if (lane == 0) lb[p] = lp;
-                    __syncwarp();
+                // l U_SS = x_S by positions: each lane owns positions lane + 32 j,
+                // and the U entries of step p + 1 are loaded while step p runs
+                // (the arithmetic and its order are the plain forward
+                // substitution's)
+                {
+                    int lq[SN_SMEM / 32];
+                    T cur[SN_SMEM / 32];
+#pragma unroll
+                    for (int j = 0; j < SN_SMEM / 32; ++j) {
+                        const int qq = lane + 32 * j;
+                        lq[j] = (qq < sS) ? pb[qq] : 0;
+                        cur[j] = (qq > 0 && qq < sS) ? U[lq[j]] : T(0);
+                    }
+                    for (int p = 0; p < sS; ++p) {
+                        T nxt[SN_SMEM / 32];
+                        const T* Un = U + (int64_t)(p + 1) * wS;
+#pragma unroll
+                        for (int j = 0; j < SN_SMEM / 32; ++j) {
+                            const int qq = lane + 32 * j;
+                            nxt[j] = (qq > p + 1 && qq < sS) ? Un[lq[j]] : T(0);
+                        }
+                        const T lp = lb[p] * dS[p];
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < SN_SMEM / 32; ++j) {
+                            const int qq = lane + 32 * j;
+                            if (qq > p && qq < sS) lb[qq] -= lp * cur[j];
+                        }
+                        if (lane == 0) lb[p] = lp;
+                        __syncwarp();
+#pragma unroll
+                        for (int j = 0; j < SN_SMEM / 32; ++j) cur[j] = nxt[j];
+                    }
                 }
                 // scatter one GEMV result into the row: a later L slot (by
                 // column in the dense L vector, through pos[], or, for a row
