@@ -74,8 +74,33 @@ def check_tasks(img):
             assert sorted(img.task_chunk[tasks].tolist()) == list(range(m))
             covered = sorted(g for t in tasks for g in range(img.task_chunk[t], ngroups, m))
             assert covered == list(range(ngroups))
-            # a tail task sits one level after its node's last row
-            assert np.all(img.task_level[tasks] == img.row_level[sn[D + 1] - 1] + 1)
+    check_claim_order(img)
+
+
+def check_claim_order(img):
+    """The factor kernel's main queue is a topological order of its
+    dependencies: a supernode's rows in index order, its tail tasks after its
+    last row, and a row after every row and tail task of each node its L list
+    reads (progress of the persistent kernel rests on that)."""
+    n, sn = img.n, img.sn_start
+    order = img.row_order
+    assert sorted(order.tolist()) == list(range(n + len(img.task_node)))
+    at = np.empty(len(order), np.int64)
+    at[order] = np.arange(len(order))
+    done = np.empty(img.nnodes, np.int64)      # position of the node's last claim
+    for D in range(img.nnodes):
+        rows = np.arange(sn[D], sn[D + 1])
+        assert np.all(np.diff(at[rows]) > 0)
+        done[D] = at[rows[-1]]
+        tasks = np.nonzero(img.task_node == D)[0]
+        if len(tasks):
+            assert np.all(at[n + tasks] > at[rows[-1]])
+            done[D] = at[n + tasks].max()
+    node_of = img.node_of
+    for i in range(n):
+        lc = img.lcols[img.row_lptr[i]:img.row_lptr[i + 1]]
+        if len(lc):
+            assert at[i] > done[np.unique(node_of[lc])].max(), i
 
 
 @pytest.mark.parametrize("name,make,opts", CASES, ids=[c[0] for c in CASES])
