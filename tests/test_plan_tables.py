@@ -74,6 +74,8 @@ def check_tasks(img):
             assert sorted(img.task_chunk[tasks].tolist()) == list(range(m))
             covered = sorted(g for t in tasks for g in range(img.task_chunk[t], ngroups, m))
             assert covered == list(range(ngroups))
+            # a tail task sits one level after its node's last row
+            assert np.all(img.task_level[tasks] == img.row_level[sn[D + 1] - 1] + 1)
     check_claim_order(img)
 
 
