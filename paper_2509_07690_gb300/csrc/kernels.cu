@@ -1027,7 +1027,9 @@ factor_kernel(DevPlan P, const double* __restrict__ vals, T* __restrict__ dinv,
                 xd[dl] = (T)u;
                 atomicAdd(P.status + ST_NPERT, 1);
             }
-            dinv[i] = (T)(1.0 / (double)xd[dl]);
+            // the reciprocal in the factors' type (an FP64 division is a long
+            // chain on the FP64 pipe, on the diagonal-block chain's path)
+            dinv[i] = T(1) / xd[dl];
         }
         __syncwarp();
         // ---- write the row back, publish
