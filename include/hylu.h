@@ -310,14 +310,22 @@ int hylu_export_gemm_plan(hylu_handle* h, int min_rows, int64_t* buf, int64_t* l
  * entries of work (its rows' L lists, or its nodes' U tails times their rows,
  * plus the squares of its node sizes); a segment is a maximal chain of two or
  * more consecutive light levels, solved by one thread block; the other rows
- * are solved in bulk.  Layout: a header [ntask, nseg, nlevels, nrows,
- * nsnodes], then task (ntask: the bulk rows in claim order), meta (3 nseg:
+ * are solved in bulk.  In the forward direction a bulk row with at least
+ * 2048 L entries has its list split into chunks of about 1024 entries (the
+ * rectangular blocks of Sec. 2.3 with their nonzeros spread evenly), each
+ * claimed on its own once the levels of its entries complete; the row adds
+ * their sums (the one-right-hand-side substitution; with several right-hand
+ * sides rows sum their whole lists).  Layout: a header [ntask, nseg, nlevels,
+ * nrows, nsnodes, nchunks], then task (ntask: the bulk rows in claim order,
+ * and n + c for chunk c before the rows of its level), meta (3 nseg:
  * instance, first level, last level; segments sorted by first level), seg_off
  * (nseg + 1, into the level table), lvl_row (nlevels + 1, into rows), lvl_node
  * (nlevels + 1, into snodes), rows (nrows: the segments' rows, level by level,
- * node by node) and snodes (nsnodes: the segments' nodes of more than one
- * row).  buf = NULL returns the length in *len; HYLU_ERR_ARG when *len is too
- * small (*len then holds the length needed).  Host work only. */
+ * node by node), snodes (nsnodes: the segments' nodes of more than one row),
+ * then per chunk its row, first and end entry (in the row's L list) and the
+ * level it waits for (4 arrays of nchunks), and each row's chunk offsets
+ * (n + 1).  buf = NULL returns the length in *len; HYLU_ERR_ARG when *len is
+ * too small (*len then holds the length needed).  Host work only. */
 int hylu_export_solve_segments(hylu_handle* h, int backward, int max_rows, int32_t* buf, int64_t* len);
 
 /* Padded storage pattern in CSR form (HOST arrays, any may be NULL):

@@ -277,8 +277,9 @@ def hylu_export_gemm_plan(h: int, min_rows: int, n: int) -> dict:
 def hylu_export_solve_segments(h: int, backward: bool, max_rows: int) -> dict:
     """Bulk-sequential partition of a substitution (see include/hylu.h): the
     bulk claim list `task`, per segment `meta` (instance, first level, last
-    level) and `seg_off`, per level `lvl_row` / `lvl_node`, and `rows`,
-    `snodes`."""
+    level) and `seg_off`, per level `lvl_row` / `lvl_node`, `rows`, `snodes`,
+    and the forward long rows' chunks (`chunk_row`, `chunk_a`, `chunk_b`,
+    `chunk_level`, `row_chunk_off`)."""
     lib = load()
     ln = C.c_int64(0)
     _check(lib.hylu_export_solve_segments(h, int(bool(backward)), int(max_rows), None, C.byref(ln)),
@@ -286,11 +287,13 @@ def hylu_export_solve_segments(h: int, backward: bool, max_rows: int) -> dict:
     buf = np.zeros(ln.value, np.int32)
     _check(lib.hylu_export_solve_segments(h, int(bool(backward)), int(max_rows), buf.ctypes.data, C.byref(ln)),
            "hylu_export_solve_segments")
-    nt, ns, nl, nr, nn = (int(v) for v in buf[:5])
-    pos = 5
+    nt, ns, nl, nr, nn, nc = (int(v) for v in buf[:6])
+    pos = 6
+    n1 = len(buf) - pos - (nt + 3 * ns + ns + 1 + 2 * (nl + 1) + nr + nn + 4 * nc)   # n + 1
     out = {}
     for name, m in (("task", nt), ("meta", 3 * ns), ("seg_off", ns + 1), ("lvl_row", nl + 1),
-                    ("lvl_node", nl + 1), ("rows", nr), ("snodes", nn)):
+                    ("lvl_node", nl + 1), ("rows", nr), ("snodes", nn), ("chunk_row", nc), ("chunk_a", nc),
+                    ("chunk_b", nc), ("chunk_level", nc), ("row_chunk_off", n1)):
         out[name] = buf[pos:pos + m].copy()
         pos += m
     out["meta"] = out["meta"].reshape(-1, 3)

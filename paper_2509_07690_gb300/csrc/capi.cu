@@ -67,6 +67,9 @@ struct hylu_handle {
         const int32_t *fwd_task, *bwd_task;
         int32_t n_fwd_tasks, n_bwd_tasks, seq_blocks;
         hylu::SegTable fseg, bseg;
+        const int32_t *fch_row, *fch_a, *fch_b, *fch_level, *frow_chunk_off;
+        double* fch_part;
+        int32_t* fch_flag;
     };
     std::map<int, SeqTables> seq_tables;
 };
@@ -225,8 +228,29 @@ static int use_seq_segments(hylu_handle* h, int max_rows, cudaStream_t st) {
             TRY(upload(h, &sn, S.snodes, st));
             if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;   // S goes out of scope
             T.meta = meta; T.seg_off = so; T.lvl_row = lr; T.lvl_node = ln; T.rows = rows; T.snodes = sn;
-            if (dir == 0) { Q.fwd_task = task; Q.n_fwd_tasks = (int32_t)S.task.size(); Q.fseg = T; }
-            else { Q.bwd_task = task; Q.n_bwd_tasks = (int32_t)S.task.size(); Q.bseg = T; }
+            if (dir == 0) {
+                Q.fwd_task = task; Q.n_fwd_tasks = (int32_t)S.task.size(); Q.fseg = T;
+                // long rows' chunks (forward only)
+                const size_t nch = S.chunk_row.size();
+                for (std::vector<int32_t>* v : {&S.chunk_row, &S.chunk_a, &S.chunk_b, &S.chunk_level})
+                    if (v->empty()) v->push_back(0);
+                int32_t *cr, *ca, *cb, *cl, *rco, *cf;
+                double* cp;
+                TRY(upload(h, &cr, S.chunk_row, st));
+                TRY(upload(h, &ca, S.chunk_a, st));
+                TRY(upload(h, &cb, S.chunk_b, st));
+                TRY(upload(h, &cl, S.chunk_level, st));
+                TRY(upload(h, &rco, S.row_chunk_off, st));
+                TRY(dalloc(h, &cp, std::max<size_t>(1, nch)));
+                TRY(dalloc(h, &cf, std::max<size_t>(1, nch)));
+                if (cudaMemsetAsync(cf, 0, sizeof(int32_t) * std::max<size_t>(1, nch), st) != cudaSuccess)
+                    return HYLU_ERR_CUDA;
+                if (cudaStreamSynchronize(st) != cudaSuccess) return HYLU_ERR_CUDA;
+                Q.fch_row = cr; Q.fch_a = ca; Q.fch_b = cb; Q.fch_level = cl; Q.frow_chunk_off = rco;
+                Q.fch_part = cp; Q.fch_flag = cf;
+            } else {
+                Q.bwd_task = task; Q.n_bwd_tasks = (int32_t)S.task.size(); Q.bseg = T;
+            }
         }
         const bool batch = !h->P.node_inst.empty();
         Q.seq_blocks = nseg_max == 0 ? 0 : batch ? std::max(1, (nseg_max + 7) / 8) : 1;
@@ -236,6 +260,8 @@ static int use_seq_segments(hylu_handle* h, int max_rows, cudaStream_t st) {
     d.fwd_task = Q.fwd_task; d.n_fwd_tasks = Q.n_fwd_tasks; d.fseg = Q.fseg;
     d.bwd_task = Q.bwd_task; d.n_bwd_tasks = Q.n_bwd_tasks; d.bseg = Q.bseg;
     d.seq_blocks = Q.seq_blocks;
+    d.fch_row = Q.fch_row; d.fch_a = Q.fch_a; d.fch_b = Q.fch_b; d.fch_level = Q.fch_level;
+    d.frow_chunk_off = Q.frow_chunk_off; d.fch_part = Q.fch_part; d.fch_flag = Q.fch_flag;
     h->opt.solve_seq_rows = max_rows;
     return HYLU_OK;
 }
@@ -826,8 +852,10 @@ int hylu_export_solve_segments(hylu_handle* h, int backward, int max_rows, int32
         hylu::SeqSegments S;
         hylu::build_seq_segments(h->P, backward != 0, max_rows, S);
         std::vector<int32_t> out = {(int32_t)S.task.size(), (int32_t)(S.seg_off.size() - 1),
-                                    (int32_t)(S.lvl_row.size() - 1), (int32_t)S.rows.size(), (int32_t)S.snodes.size()};
-        for (const std::vector<int32_t>* v : {&S.task, &S.meta, &S.seg_off, &S.lvl_row, &S.lvl_node, &S.rows, &S.snodes})
+                                    (int32_t)(S.lvl_row.size() - 1), (int32_t)S.rows.size(), (int32_t)S.snodes.size(),
+                                    (int32_t)S.chunk_row.size()};
+        for (const std::vector<int32_t>* v : {&S.task, &S.meta, &S.seg_off, &S.lvl_row, &S.lvl_node, &S.rows, &S.snodes,
+                                              &S.chunk_row, &S.chunk_a, &S.chunk_b, &S.chunk_level, &S.row_chunk_off})
             out.insert(out.end(), v->begin(), v->end());
         const int64_t need = (int64_t)out.size();
         if (!buf) { *len = need; return HYLU_OK; }

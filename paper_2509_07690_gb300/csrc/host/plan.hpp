@@ -140,10 +140,20 @@ struct SymbolicRows {
 //   seg_off   segments + 1, into the level table
 //   lvl_row   level table + 1, into rows (a level's rows, node by node)
 //   lvl_node  level table + 1, into snodes (a level's nodes of more than one row)
+//   forward only: rows outside the segments with at least long_min L entries
+//   have their lists split into chunks of about chunk_len entries (entries
+//   [chunk_a, chunk_b) of row chunk_row); a chunk waits for level
+//   chunk_level (one past its entries' highest source level); row_chunk_off
+//   (n + 1) gives every row's chunks; the claim list holds chunk c as entry
+//   n + c, before the rows of its level
 struct SeqSegments {
     std::vector<int32_t> task, meta, seg_off, lvl_row, lvl_node, rows, snodes;
+    std::vector<int32_t> chunk_row, chunk_a, chunk_b, chunk_level, row_chunk_off;
 };
-void build_seq_segments(const Plan& P, bool backward, int32_t max_rows, SeqSegments& S);
+constexpr int32_t LONG_ROW_MIN = 2048;   // default long_min
+constexpr int32_t LONG_ROW_CHUNK = 1024; // default chunk_len
+void build_seq_segments(const Plan& P, bool backward, int32_t max_rows, SeqSegments& S,
+                        int32_t long_min = LONG_ROW_MIN, int32_t chunk_len = LONG_ROW_CHUNK);
 
 // Checkpoint of an analysis (serialize.cpp): the plan, the batch layout and
 // the options as one flat byte image with a checksum, and back.  load_plan

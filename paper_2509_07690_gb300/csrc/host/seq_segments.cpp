@@ -12,7 +12,8 @@
 
 namespace hylu {
 
-void build_seq_segments(const Plan& P, bool backward, int32_t max_rows, SeqSegments& S) {
+void build_seq_segments(const Plan& P, bool backward, int32_t max_rows, SeqSegments& S, int32_t long_min,
+                        int32_t chunk_len) {
     S = SeqSegments();
     const std::vector<int32_t>& order = backward ? P.bwd_order : P.fwd_order;
     const std::vector<int32_t>& level = backward ? P.bwd_level : P.fwd_level;
@@ -79,9 +80,50 @@ void build_seq_segments(const Plan& P, bool backward, int32_t max_rows, SeqSegme
             S.seg_off.push_back((int32_t)S.lvl_row.size() - 1);
         }
     }
-    S.task.reserve(order.size());
+    std::vector<int32_t> rows;
+    rows.reserve(order.size());
     for (int32_t i : order)
-        if (!in_seg[P.node_of[i]]) S.task.push_back(i);
+        if (!in_seg[P.node_of[i]]) rows.push_back(i);
+    // the forward solve's long rows: their L lists split into chunks of about
+    // chunk_len entries (the rectangular blocks of Sec. 2.3, nonzeros spread
+    // evenly over workers), each a claim entry n + c of its own that waits
+    // only for the levels its entries come from; the row then adds the
+    // chunks' sums in chunk order
+    S.row_chunk_off.assign((size_t)P.n + 1, 0);
+    if (!backward && long_min > 0) {
+        for (int32_t i : rows) {
+            const int64_t l0 = P.row_lptr[i], nl = P.row_lptr[i + 1] - l0;
+            if (nl < long_min) continue;
+            const int64_t nc = (nl + chunk_len - 1) / chunk_len;
+            for (int64_t c = 0; c < nc; ++c) {
+                const int32_t a = (int32_t)(c * nl / nc), b = (int32_t)((c + 1) * nl / nc);
+                int32_t lv = 0;
+                for (int64_t t = l0 + a; t < l0 + b; ++t) lv = std::max(lv, level[P.node_of[P.lcols[t]]] + 1);
+                S.chunk_row.push_back(i);
+                S.chunk_a.push_back(a);
+                S.chunk_b.push_back(b);
+                S.chunk_level.push_back(lv);
+            }
+            S.row_chunk_off[i + 1] = (int32_t)nc;
+        }
+        for (int32_t i = 0; i < P.n; ++i) S.row_chunk_off[i + 1] += S.row_chunk_off[i];
+    }
+    // claim list: at each level, the chunks waiting for it, then the rows
+    // of that level in their order (the rows' order is by level); a chunk's
+    // level is at most its row's, so it comes before its row
+    const int32_t nch = (int32_t)S.chunk_row.size();
+    std::vector<int32_t> corder(nch);
+    for (int32_t c = 0; c < nch; ++c) corder[c] = c;
+    std::stable_sort(corder.begin(), corder.end(),
+                     [&](int32_t x, int32_t y) { return S.chunk_level[x] < S.chunk_level[y]; });
+    S.task.reserve(rows.size() + nch);
+    size_t k = 0;
+    for (int32_t i : rows) {
+        const int32_t li = level[P.node_of[i]];
+        while (k < corder.size() && S.chunk_level[corder[k]] <= li) S.task.push_back(P.n + corder[k++]);
+        S.task.push_back(i);
+    }
+    while (k < corder.size()) S.task.push_back(P.n + corder[k++]);
 }
 
 }  // namespace hylu

@@ -1506,6 +1506,24 @@ fwd_kernel(DevPlan P, T* __restrict__ z, int nrhs, long long limit) {
         if (qi >= P.n_fwd_tasks) return;
         if (ld_relaxed(P.status + ST_ERR) != 0) return;
         const int i = P.fwd_task[qi];
+        if (i >= n) {
+            // a chunk of a long row's L list (the rectangular blocks of Sec.
+            // 2.3): summed as soon as the levels of its entries complete.  The
+            // several-right-hand-side variant sums whole rows instead.
+            if (!ONE) continue;
+            const int c = i - n;
+            const int ri = P.fch_row[c];
+            const int qc = P.node_inst ? P.node_inst[P.node_of[ri]] : 0;
+            if (qc != cq) { cq = qc; cached = 0; }
+            if (!__all_sync(FULL, wait_level(P.wm_f + qc, P.fch_level[c], cached, P.status, limit))) return;
+            const int64_t o = P.row_lptr[ri] + P.fch_a[c];
+            const T a = sparse_dot<T>(LV<T>(P) + o, P.lcols + o, P.fch_b[c] - P.fch_a[c], z, lane);
+            if (lane == 0) reinterpret_cast<T*>(P.fch_part)[c] = a;
+            __threadfence();
+            __syncwarp();
+            if (lane == 0) st_release(P.fch_flag + c, gen);
+            continue;
+        }
         const int D = P.node_of[i];
         const int L = P.fwd_level[D];
         const int r = P.sn_start[D], e = P.sn_start[D + 1] - 1, s = e - r + 1;
@@ -1525,7 +1543,22 @@ fwd_kernel(DevPlan P, T* __restrict__ z, int nrhs, long long limit) {
         // entries [0, sp) have sources at least two levels down: summed as
         // soon as those levels complete, before the level barrier
         const int sp = (P.fwd_split && L >= 1) ? P.fwd_split[i] : 0;
-        if (nrhs == 1) {
+        const int c0 = ONE ? P.frow_chunk_off[i] : 0, c1 = ONE ? P.frow_chunk_off[i + 1] : 0;
+        if (nrhs == 1 && c1 > c0) {
+            // a long row: the sums of its chunks, each once its warp has
+            // published it, added in chunk order (a fixed tree per 32 chunks)
+            T a = 0.0;
+            for (int cb = c0; cb < c1; cb += 32) {
+                const int c = cb + lane;
+                int ok = 1;
+                if (c < c1) ok = lane_wait(P.fch_flag + c, gen, P.status, c, limit);
+                if (!__all_sync(FULL, ok)) return;
+                T v = (c < c1) ? __ldcg(reinterpret_cast<const T*>(P.fch_part) + c) : T(0);
+                for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(FULL, v, off);
+                a += v;
+            }
+            if (lane == 0) z[i] -= a;
+        } else if (nrhs == 1) {
             T a = 0.0;
             if (sp > 0) {
                 if (!__all_sync(FULL, wait_level(P.wm_f + q, L - 1, cached, P.status, limit))) return;

@@ -107,6 +107,17 @@ struct DevPlan {
     int32_t n_fwd_tasks, n_bwd_tasks;
     SegTable fseg, bseg;
     int32_t seq_blocks;
+    // forward solve, long rows: chunk c sums entries [fch_a, fch_b) of row
+    // fch_row's L list once level fch_level is complete, writes fch_part[c]
+    // (the factors' type) and publishes fch_flag[c]; frow_chunk_off (n + 1)
+    // lists every row's chunks
+    const int32_t* fch_row;
+    const int32_t* fch_a;
+    const int32_t* fch_b;
+    const int32_t* fch_level;
+    const int32_t* frow_chunk_off;
+    double* fch_part;
+    int32_t* fch_flag;
     int32_t* fwd_row;              // per row of a supernode, solve generation
     int32_t* bwd_row;
     int32_t* tile_f;               // per 32-row tile of a supernode block (at its owner row):

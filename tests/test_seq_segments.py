@@ -106,10 +106,49 @@ def _check(S, segs, level, inst, sn, order):
             k += 1
     assert len(S["lvl_row"]) == k + 1
     # the bulk claim list: the rows outside the segments, in their claim order
+    # (entries from n on are the forward long rows' chunks)
     node_of = np.repeat(np.arange(len(sn) - 1), np.diff(sn))
+    n = len(node_of)
     want_task = [i for i in order if not in_seg[node_of[i]]]
-    assert S["task"].tolist() == want_task
-    assert len(S["task"]) + len(S["rows"]) == len(order)
+    rows_task = [int(t) for t in S["task"] if t < n]
+    assert rows_task == want_task
+    assert len(rows_task) + len(S["rows"]) == len(order)
+
+
+def _check_chunks(S, level, node_of, lptr, lcols, backward):
+    """Forward long rows (at least 2048 L entries, outside the segments): their
+    lists in ceil(nL / 1024) chunks of near-equal length, each waiting for one
+    past the highest level of its entries' sources and claimed before every
+    row of that level or later (after every row of a lower level)."""
+    n = len(node_of)
+    task = S["task"]
+    if backward:
+        assert len(S["chunk_row"]) == 0 and np.all(S["row_chunk_off"] == 0)
+        assert np.all(task < n)
+        return
+    want = []
+    for i in task[task < n]:
+        nl = lptr[i + 1] - lptr[i]
+        if nl < 2048:
+            continue
+        nc = -(-nl // 1024)
+        for c in range(nc):
+            a, b = c * nl // nc, (c + 1) * nl // nc
+            src = lcols[lptr[i] + a:lptr[i] + b]
+            want.append((int(i), int(a), int(b), int(level[node_of[src]].max() + 1)))
+    got = list(zip(S["chunk_row"].tolist(), S["chunk_a"].tolist(), S["chunk_b"].tolist(), S["chunk_level"].tolist()))
+    assert sorted(got) == sorted(want)
+    cnt = np.bincount(S["chunk_row"], minlength=n) if len(got) else np.zeros(n, np.int64)
+    assert np.array_equal(np.diff(S["row_chunk_off"]), cnt)
+    for c, (i, a, b, lv) in enumerate(got):
+        assert S["row_chunk_off"][i] <= c < S["row_chunk_off"][i + 1]
+    # placement: levels of the rows before / after each chunk entry
+    row_lv = [(k, int(level[node_of[t]])) for k, t in enumerate(task) if t < n]
+    for k, t in enumerate(task):
+        if t >= n:
+            lv = S["chunk_level"][t - n]
+            assert all(l < lv for kk, l in row_lv if kk < k)
+            assert all(l >= lv for kk, l in row_lv if kk > k)
 
 
 @pytest.mark.parametrize("max_rows", [0, 1, 4, 16, 64])
@@ -126,6 +165,20 @@ def test_segments_match_brute_force(name, A, opts, max_rows):
         S = capi.hylu_export_solve_segments(s.h, bwd, max_rows)
         segs = _brute_segments(level, B["size"], work, inst, max_rows)
         _check(S, segs, level, inst, B["sn"], order)
+        _check_chunks(S, level, B["node_of"], img.row_lptr, img.lcols, bwd)
+    s.close()
+
+
+def test_long_rows_split_into_chunks():
+    """A circuit matrix whose hub rows have more than 2048 L entries: the
+    forward partition splits them (the test above would pass without any)."""
+    A = synth.circuit(12000, seed=9)
+    s = Solver(A.n, A.rowptr, A.col, A.val)
+    img = PlanImage(capi.hylu_plan_save(s.h))
+    S = capi.hylu_export_solve_segments(s.h, 0, 8)
+    assert len(S["chunk_row"]) > 100
+    node_of = np.repeat(np.arange(len(img.sn_start) - 1), np.diff(img.sn_start))
+    _check_chunks(S, img.fwd_level, node_of, img.row_lptr, img.lcols, False)
     s.close()
 
 
@@ -159,4 +212,5 @@ def test_batch_segments_per_instance():
         segs = _brute_segments(level.astype(np.int64), size, work, inst, 16)
         assert len(segs) > 0 or bwd == 1
         _check(S, segs, level, inst, sn, order)
+        _check_chunks(S, level, node_of, img.row_lptr, img.lcols, bwd)
     bs.close()
