@@ -91,9 +91,12 @@ void build_seq_segments(const Plan& P, bool backward, int32_t max_rows, SeqSegme
     // chunks' sums in chunk order
     S.row_chunk_off.assign((size_t)P.n + 1, 0);
     if (!backward && long_min > 0) {
-        for (int32_t i : rows) {
+        // by row index, so that row_chunk_off lists every row's chunks
+        std::vector<char> bulk(P.n, 0);
+        for (int32_t i : rows) bulk[i] = 1;
+        for (int32_t i = 0; i < P.n; ++i) {
             const int64_t l0 = P.row_lptr[i], nl = P.row_lptr[i + 1] - l0;
-            if (nl < long_min) continue;
+            if (!bulk[i] || nl < long_min) continue;
             const int64_t nc = (nl + chunk_len - 1) / chunk_len;
             for (int64_t c = 0; c < nc; ++c) {
                 const int32_t a = (int32_t)(c * nl / nc), b = (int32_t)((c + 1) * nl / nc);

@@ -1546,7 +1546,11 @@ fwd_kernel(DevPlan P, T* __restrict__ z, int nrhs, long long limit) {
         const int c0 = ONE ? P.frow_chunk_off[i] : 0, c1 = ONE ? P.frow_chunk_off[i + 1] : 0;
         if (nrhs == 1 && c1 > c0) {
             // a long row: the sums of its chunks, each once its warp has
-            // published it, added in chunk order (a fixed tree per 32 chunks)
+            // published it, added in chunk order (a fixed tree per 32 chunks).
+            // The row still waits for its level: its node completing raises
+            // the watermark past its level, which must not happen before the
+            // lower levels complete (its chunks may all come from lower ones)
+            if (!__all_sync(FULL, wait_level(P.wm_f + q, L, cached, P.status, limit))) return;
             T a = 0.0;
             for (int cb = c0; cb < c1; cb += 32) {
                 const int c = cb + lane;

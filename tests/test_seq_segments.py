@@ -142,13 +142,16 @@ def _check_chunks(S, level, node_of, lptr, lcols, backward):
     assert np.array_equal(np.diff(S["row_chunk_off"]), cnt)
     for c, (i, a, b, lv) in enumerate(got):
         assert S["row_chunk_off"][i] <= c < S["row_chunk_off"][i + 1]
-    # placement: levels of the rows before / after each chunk entry
-    row_lv = [(k, int(level[node_of[t]])) for k, t in enumerate(task) if t < n]
-    for k, t in enumerate(task):
-        if t >= n:
-            lv = S["chunk_level"][t - n]
-            assert all(l < lv for kk, l in row_lv if kk < k)
-            assert all(l >= lv for kk, l in row_lv if kk > k)
+    # placement: the highest level of the rows before each chunk entry is below
+    # the chunk's level, the lowest level of the rows after it is not
+    is_row = task < n
+    lv_rows = np.where(is_row, level[node_of[np.where(is_row, task, 0)]], 0).astype(np.int64)
+    before = np.maximum.accumulate(np.where(is_row, lv_rows, -1))
+    after = np.minimum.accumulate(np.where(is_row, lv_rows, np.iinfo(np.int64).max)[::-1])[::-1]
+    for k in np.nonzero(~is_row)[0]:
+        lv = S["chunk_level"][task[k] - n]
+        assert k == 0 or before[k - 1] < lv
+        assert k == len(task) - 1 or after[k + 1] >= lv
 
 
 @pytest.mark.parametrize("max_rows", [0, 1, 4, 16, 64])
@@ -169,11 +172,15 @@ def test_segments_match_brute_force(name, A, opts, max_rows):
     s.close()
 
 
-def test_long_rows_split_into_chunks():
-    """A circuit matrix whose hub rows have more than 2048 L entries: the
-    forward partition splits them (the test above would pass without any)."""
-    A = synth.circuit(12000, seed=9)
-    s = Solver(A.n, A.rowptr, A.col, A.val)
+@pytest.mark.parametrize("name,A,opts", [("circuit_12000", synth.circuit(12000, seed=9), {}),
+                                         ("convdiff_40_nd", synth.convdiff3d(40), {"ordering": 1})],
+                         ids=["circuit_12000", "convdiff_40_nd"])
+def test_long_rows_split_into_chunks(name, A, opts):
+    """Matrices whose long rows have more than 2048 L entries (circuit hub
+    rows; a 3D grid's separators, whose claim order is not their index order):
+    the forward partition splits them (the test above would pass without any),
+    and every row's chunk range names its own chunks."""
+    s = Solver(A.n, A.rowptr, A.col, A.val, **opts)
     img = PlanImage(capi.hylu_plan_save(s.h))
     S = capi.hylu_export_solve_segments(s.h, 0, 8)
     assert len(S["chunk_row"]) > 100
