@@ -221,3 +221,22 @@ def test_batch_segments_per_instance():
         _check(S, segs, level, inst, sn, order)
         _check_chunks(S, level, node_of, img.row_lptr, img.lcols, bwd)
     bs.close()
+
+
+def test_export_length_protocol():
+    """hylu_export_solve_segments: a NULL buffer returns the length; a buffer
+    too short is refused with HYLU_ERR_ARG and the length needed."""
+    import ctypes as C
+    A = synth.circuit(3000, seed=2)
+    s = Solver(A.n, A.rowptr, A.col, A.val)
+    lib = capi.load()
+    need = C.c_int64(0)
+    assert lib.hylu_export_solve_segments(s.h, 0, 8, None, C.byref(need)) == 0
+    assert need.value > A.n
+    short = C.c_int64(need.value - 1)
+    buf = np.zeros(need.value, np.int32)
+    assert lib.hylu_export_solve_segments(s.h, 0, 8, buf.ctypes.data, C.byref(short)) == -1
+    assert short.value == need.value
+    full = capi.hylu_export_solve_segments(s.h, 0, 8)
+    assert len(full["row_chunk_off"]) == A.n + 1
+    s.close()
